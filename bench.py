@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Throughput of the DMR EM-plasma time step on GB300.
+
+Metric: fine-equivalent cell-updates/s = (r nx)(r ny)(r coarse steps) / time
+(the cost model of Sec. IV.C counts the uniform fine mesh's work N_f I_f).
+Workload: DMR r = 2, coarse 512 x 512 at lambda/32 (16 x 16 wavelengths), FP32
+fields with FP64 E^2 sums and totals, fine patch starting at 64 x 64 fine
+cells around the seed, air at 700 Torr, 110 GHz, E0 = 5 MV/m.
+
+A bench step is one EM period: 64 coarse steps with 2 fine sub-steps each,
+the continuity step, flags and the growth decision.  The timed run starts at
+t = 0 and advances --steps periods (2200 periods = the 20 ns of the workload);
+warm-up periods run on a separate run.  Each period is timed with CUDA events
+on the run's stream and the L2 is flushed (256 MB write) between periods,
+outside the timed intervals.
+
+--impl reference times the CPU oracle (test infrastructure, FP64 numpy) on the
+same workload: each step is one coarse step of the same run.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fine-equiv cell-updates/s, DMR vs uniform fine mesh, % of HBM BW roofline"
+UNIT = "fine-equiv cell-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def bytes_per_point(kclass, es, r=2):
+    """Algorithmic bytes per grid point of one launch of a kernel class (the
+    data the kernel must read and write once): H + E^2 sum: Ex, Ey read, Hz
+    read+write, S2 (fp64) read+write; E: Ex, Ey, vx, vy read+write, Hz and n
+    read; restriction: 2r fine reads and 2 coarse writes."""
+    return {"coarse_h": 4 * es + 16, "fine_h": 4 * es + 16,
+            "coarse_e": 10 * es, "fine_e": 10 * es,
+            "restrict": (2 * r + 2) * es}.get(kclass)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r_ in rows for q, v in enumerate(r_[3]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r_[0] for r_ in rows),
+                "sm_max_mhz": max(r_[1] for r_ in rows),
+                "power_w_max": max(r_[2] for r_ in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def gpu_index_for(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+def units_per_period(cfg):
+    r, nx, ny, NT = cfg["r"], cfg["nx"], cfg["ny"], cfg["steps_per_period"]
+    return (r * nx) * (r * ny) * (r * NT)
+
+
+def cpu_oracle_rate(w, budget_s=12.0, per_step_cap=None):
+    """Oracle (FP64 numpy, single thread) on the first coarse steps of the same
+    run: fine-equivalent cell-updates/s, steps done, seconds."""
+    from oracle import dmr_oracle as O
+    cfg = dict(w["cfg"])
+    cfg["precision"] = 0
+    sim = O.sim_from_workload(dict(w, cfg=cfg))
+    r, nx, ny = cfg["r"], cfg["nx"], cfg["ny"]
+    per_step = (r * nx) * (r * ny) * r
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        sim.coarse_step()
+        steps += 1
+        if time.perf_counter() - t0 >= budget_s or (per_step_cap and steps >= per_step_cap):
+            break
+    dt = time.perf_counter() - t0
+    return steps * per_step / dt, steps, dt
+
+
+def workload(name):
+    from paper_2105_13276_gb300 import workloads as W
+    if name == "dmr512":
+        return W.dmr_512_r2(precision=1)
+    if name == "dmr512_fp64":
+        return W.dmr_512_r2(precision=0)
+    if name == "uniform256":
+        return W.uniform_256(precision=1)
+    if name == "large_r2":
+        return W.large_dmr(r=2)
+    if name == "large_r4":
+        return W.large_dmr(r=4)
+    raise SystemExit("unknown workload " + name)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import dmr_oracle as O
+    w = workload(args.workload)
+    cfg = dict(w["cfg"])
+    sim = O.sim_from_workload(dict(w, cfg=dict(cfg, precision=0)))
+    r, nx, ny = cfg["r"], cfg["nx"], cfg["ny"]
+    per_step = (r * nx) * (r * ny) * r
+    for _ in range(args.warmup):
+        sim.coarse_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.coarse_step()
+    dt = time.perf_counter() - t0
+    value = args.steps * per_step / dt
+    sample = ("%d coarse steps of the %s run after %d warm-up steps (one coarse step per bench "
+              "step), FP64 numpy oracle" % (args.steps, w["name"], args.warmup))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(w, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def config_of(w, args):
+    c = w["cfg"]
+    return {"workload": w["name"], "model": "DMR EM-plasma (2D TE Yee + continuity)",
+            "nx": c["nx"], "ny": c["ny"], "r": c["r"], "n_lambda": c["n_lambda"],
+            "steps_per_period": c["steps_per_period"], "E0_V_per_m": c["E0"],
+            "p_torr": c["p_torr"], "freq_hz": c["freq"],
+            "precision": "fp32 fields + fp64 E^2 sums/totals" if c.get("precision") == 1 else "fp64",
+            "step": "one EM period (%d coarse steps x %d fine sub-steps + continuity + flags)"
+                    % (c["steps_per_period"], c["r"]),
+            "global_batch": 1, "seq_len": None, "parallelism": "replicas" if args.gpus > 1 else "single"}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import datetime
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl", timeout=datetime.timedelta(seconds=600))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2105_13276_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2105_13276_gb300 import dmr as D
+    from paper_2105_13276_gb300 import workloads as W
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    w = workload(args.workload)
+    cfg = w["cfg"]
+    NT = cfg["steps_per_period"]
+    upp = units_per_period(cfg)
+    es = 4 if cfg.get("precision") == 1 else 8
+    K, Wm = args.steps, args.warmup
+
+    # warm-up run: graphs captured, every kernel class timed to find the dominant one
+    warm = D.run_from_workload(w, device=dev)
+    warm.set_graphs(True)
+    warm.set_timing(True)
+    warm.advance(max(Wm, 1) * NT)
+    warm.sync()
+    kt = warm.kernel_times()
+    cand = {k: v for k, v in kt.items() if bytes_per_point(k, es, cfg["r"]) and v[1] > 0}
+    dominant = max(cand, key=lambda k: cand[k][0]) if cand else None
+    del warm
+
+    # timed run
+    run = D.run_from_workload(w, device=dev)
+    run.set_graphs(True)
+    if dominant:
+        run.set_timing(True, classes=[dominant])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    s = run.stream
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    l0 = run.launch_count()
+    sampler = ClockSampler(gpu_index_for(local)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter()
+    for k in range(K):
+        evs[k][0].record(s)
+        run.advance(NT)
+        evs[k][1].record(s)
+        with torch.cuda.stream(s):
+            flush.zero_()
+    torch.cuda.synchronize(dev)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop() if sampler else None
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    launches = run.launch_count() - l0
+    st = run.stats()
+    final_rect = list(run.get_patch())
+    kt = run.kernel_times()
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * K * upp / (ms / 1e3)
+
+    roof = None
+    if dominant and kt.get(dominant, (0, 0, 0))[1] > 0:
+        tms, n, pts = kt[dominant]
+        peak, src = measured_peak()
+        ach = bytes_per_point(dominant, es, cfg["r"]) * pts / (tms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dominant, "achieved": ach, "peak": peak,
+                "peak_source": src + " (burst copy)", "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "launches": n, "avg_launch_us": 1e3 * tms / n,
+                "bytes_per_point": bytes_per_point(dominant, es, cfg["r"]),
+                "points_per_launch": pts / n}
+    del run
+
+    # uniform fine mesh on the same GPU: the comparison the metric names
+    uni_rate = None
+    if not args.no_uniform:
+        u = W.uniform_fine_equivalent(w)
+        Ku = max(1, min(args.uniform_periods, K))
+        ur = D.run_from_workload(u, device=dev)
+        ur.set_graphs(True)
+        ur.advance(u["cfg"]["steps_per_period"])          # capture + warm
+        ur.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(Ku)]
+        for k in range(Ku):
+            ev[k][0].record(ur.stream)
+            ur.advance(u["cfg"]["steps_per_period"])
+            ev[k][1].record(ur.stream)
+            with torch.cuda.stream(ur.stream):
+                flush.zero_()
+        torch.cuda.synchronize(dev)
+        ums = sum(a.elapsed_time(b) for a, b in ev)
+        uni_rate = Ku * units_per_period(u["cfg"]) / (ums / 1e3)
+        del ur
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        er = D.run_from_workload(w, device=dev)
+        er.set_graphs(True)
+        (rc, cc), eb = er.shape("n", 0)
+        (rf, cf), _ = er.shape("n", 1)
+        dt_ = torch.float32 if es == 4 else torch.float64
+        h_nc = torch.empty((rc, cc), dtype=dt_, pin_memory=True)
+        h_nf = torch.empty((rf, cf), dtype=dt_, pin_memory=True)
+        er.read_to_host("n", 0, h_nc)
+        er.read_to_host("n", 1, h_nf)
+        h_out = torch.empty((rc, cc), dtype=dt_, pin_memory=True)
+        er2 = D.run_from_workload(dict(w, seeds=[(0.0, 0.5, 0.5, 0.1, 0.1)]), device=dev)
+        er2.set_graphs(True)
+        del er
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        er2.write_from_host("n", 1, h_nf)     # fine seed map (also sets coinciding coarse nodes)
+        er2.write_from_host("n", 0, h_nc)     # coarse seed map
+        for k in range(K):
+            er2.advance(NT)
+            er2.read_to_host("n", 0, h_out)   # the step's result: coarse density map
+        torch.cuda.synchronize(dev)
+        t_e = time.perf_counter() - t0
+        h2d = (h_nc.numel() + h_nf.numel()) * h_nc.element_size()
+        d2h = h_out.numel() * h_out.element_size() + 96
+        e2e = {"value": world * K * upp / t_e, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h,
+               "note": "initial density maps uploaded once (per-step share), coarse density read "
+                       "back every period, control block read every period"}
+        del er2
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        cr, csteps, csec = cpu_oracle_rate(w, budget_s=args.cpu_seconds)
+        cpu = {"value": cr, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first %d coarse steps (%.2f periods) of the same run, FP64 numpy oracle, "
+                         "%.1f s" % (csteps, csteps / NT, csec)}
+
+    if rank == 0:
+        c = config_of(w, args)
+        c.update({"periods_timed": K, "simulated_ns": K / cfg["freq"] * 1e9,
+                  "l2": "flushed (256 MB write) between timed periods",
+                  "final_rect": final_rect,
+                  "R_end": st["R"], "fine_cells_end": st["fine_cells"], "N_e_end": st["N_e"],
+                  "wall_s_timed_loop": t_wall})
+        if uni_rate:
+            c["uniform_fine_cell_updates_per_s"] = uni_rate
+            c["dmr_speedup_vs_uniform"] = (value / world) / uni_rate
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if es == 4 else "f64",
+                "data": "synthetic", "config": c, "roofline": roof, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2200, help="timed EM periods")
+    ap.add_argument("--warmup", type=int, default=3, help="warm-up periods (separate run)")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dmr512")
+    ap.add_argument("--uniform-periods", type=int, default=40)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-uniform", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        raise SystemExit("--steps >= 1 and --warmup >= 0")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

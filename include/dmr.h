@@ -1,0 +1,202 @@
+/*
+ * dmr.h -- C ABI of the GB300 dynamic-mesh-refinement (DMR) EM-plasma library.
+ *
+ * The library advances the 2D TE EM-plasma fluid model of Ghosh & Chaudhury
+ * (arXiv 2105.13276) on one coarse Yee mesh plus one growing fine rectangle:
+ *   - Eqs. 1-3 (Sec. II.A): Yee FDTD E/H update in scattered-field form with the
+ *     cold-plasma electron current J = -e n v, first-order Mur outer boundary
+ *     (Sec. II.B, Fig. 1 caption);
+ *   - Eq. 4 (Sec. II.A): electron continuity with nu_i(E_eff/p), effective
+ *     diffusion and recombination, once per EM period (Sec. III.C);
+ *   - Sec. III.C: r fine sub-steps per coarse step, coarse->fine transfer by
+ *     Eq. 5b (coarse-fine boundary) and Eq. 5a (new fine area), fine->coarse;
+ *   - Sec. III.A-III.D: threshold / gradient flags and rectangle growth.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a dmr_status (0 = success) and never aborts;
+ *     dmr_last_error() gives a message.
+ *   - The caller owns all device memory.  dmr_create() receives one device
+ *     buffer of dmr_workspace_bytes() bytes and carves every array out of it;
+ *     the library never calls cudaMalloc.  The fine arrays are sized for
+ *     patch_cap_cells fine cells up front; growth beyond that is DMR_ECAPACITY.
+ *   - Work is queued on the CUDA stream given to dmr_create().  Calls return
+ *     after queuing, except where stated (reads to host memory, dmr_stats, and
+ *     the once-per-period rectangle decision inside dmr_advance, which reads
+ *     16 bytes of flag bounding box back to the host).
+ *   - Units are SI; positions are metres from the lower-left domain corner.
+ *   - Arrays read or written through the ABI are dense, row-major with y as
+ *     the row index and x contiguous:
+ *       Ex, vx : (ny+1) rows x nx       at ((i+1/2)d, j d)
+ *       Ey, vy : ny rows x (nx+1)       at (i d, (j+1/2)d)
+ *       Hz     : ny rows x nx           at ((i+1/2)d, (j+1/2)d)
+ *       NE, S2 : (ny+1) rows x (nx+1)   at nodes (i d, j d)
+ *       MASK   : (ny+1) rows x (nx+1)   uint8 flags on the coarse nodes
+ *     with (nx, ny) the cell counts of the mesh read (coarse, or the current
+ *     fine rectangle).  Elements are double for precision 0 and float for
+ *     precision 1, except S2 (always double) and MASK (uint8).
+ */
+#ifndef DMR_H
+#define DMR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmr_ctx dmr_ctx;
+
+typedef enum {
+  DMR_OK = 0,
+  DMR_EINVAL = -1,     /* bad argument or configuration */
+  DMR_ECAPACITY = -2,  /* workspace too small or patch beyond patch_cap_cells */
+  DMR_ECUDA = -3,      /* a CUDA call failed (message has the CUDA error) */
+  DMR_EUNSTABLE = -4,  /* stability guard: Courant, diffusion number, NaN or w_p dt >= 2 */
+  DMR_ETIMEOUT = -5,   /* a bounded device wait gave up */
+  DMR_ESTATE = -6      /* call not valid in the current state */
+} dmr_status;
+
+typedef enum {
+  DMR_FIELD_EX = 0, DMR_FIELD_EY = 1, DMR_FIELD_HZ = 2, DMR_FIELD_VX = 3,
+  DMR_FIELD_VY = 4, DMR_FIELD_NE = 5, DMR_FIELD_S2 = 6, DMR_FIELD_MASK = 7
+} dmr_field;
+
+typedef enum {
+  DMR_STAT_T = 0,            /* simulated time (s) */
+  DMR_STAT_R = 1,            /* refinement region R(t) = fine cells / (r^2 coarse cells), Sec. III.C */
+  DMR_STAT_FINE_CELLS = 2,   /* fine cells of the rectangle */
+  DMR_STAT_NE = 3,           /* electrons per metre of depth (FP64 composite trapezoid total) */
+  DMR_STAT_PABS = 4,         /* period-mean absorbed power per metre of depth (W/m), FP64 */
+  DMR_STAT_WABS = 5,         /* absorbed energy per metre of depth since start (J/m), FP64 */
+  DMR_STAT_PERIODS = 6,      /* completed EM periods (continuity steps) */
+  DMR_STAT_COARSE_STEPS = 7, /* completed coarse EM steps */
+  DMR_STAT_NMAX = 8,         /* largest coarse-node density at the last period end */
+  DMR_STAT_FLAGS = 9,        /* flagged coarse nodes at the last period end */
+  DMR_NSTATS = 10
+} dmr_stat;
+
+/*
+ * Run description.  Negative values of De, Da, beta_rec, Te, nu_scale, n_th,
+ * g_th and patch_cap_cells select the defaults given in brackets.
+ */
+typedef struct dmr_config {
+  int32_t nx, ny;            /* coarse cells along x and y (>= 4 each) */
+  int32_t r;                 /* refinement factor (Sec. III.C); 1 = uniform mesh, no patch */
+  int32_t n_lambda;          /* coarse cells per wavelength: dx_c = lambda / n_lambda */
+  int32_t steps_per_period;  /* N_T coarse EM steps per period: dt_c = 1/(f N_T);
+                                Courant c dt/dx = n_lambda/N_T must be <= 1/sqrt(2) */
+  int32_t precision;         /* 0: FP64 everywhere; 1: FP32 fields, FP64 E^2 sums and totals */
+  int32_t buffer_cells;      /* growth buffer in coarse cells [4] */
+  int32_t growth;            /* 1: flags grow the rectangle; 0: it stays fixed */
+  int64_t patch_cap_cells;   /* fine-cell capacity [(r nx)(r ny)] */
+  double freq;               /* EM frequency f (Hz) */
+  double E0;                 /* incident amplitude (V/m), E along y, incident from the left */
+  double p_torr;             /* gas pressure (Torr); nu_m = 5.3e9 p (Sec. II.A) */
+  double De, Da;             /* free / ambipolar diffusion (m^2/s) [0.1*760/p, De/100] */
+  double beta_rec, Te;       /* r_ei = beta 1e-13 sqrt(300/Te) m^3/s (Sec. II.A) [1, 300 K] */
+  double nu_scale;           /* scale s_nu of the ionization frequency [1] */
+  double nu_a;               /* attachment frequency (1/s) [0] */
+  double n_th;               /* threshold density (m^-3) [1e-3 n_crit] (Sec. III.A) */
+  double g_th;               /* gradient threshold (m^-4) [n_th/(4 dx_c)] (Sec. III.B) */
+} dmr_config;
+
+/* Bytes of device workspace a run of this configuration needs; 0 if the
+ * configuration is invalid (dmr_last_error(NULL) says why). */
+size_t dmr_workspace_bytes(const dmr_config* cfg);
+
+/* Create a run.  dev_workspace: device buffer of at least
+ * dmr_workspace_bytes(cfg) bytes, 256-byte aligned, owned by the caller and
+ * kept alive until dmr_destroy.  cuda_stream: cudaStream_t (NULL = legacy
+ * default stream).  All fields start at zero and the density at zero; no
+ * fine rectangle exists until dmr_set_patch.  Errors: DMR_EINVAL (bad
+ * config), DMR_EUNSTABLE (stability guard), DMR_ECAPACITY (buffer too small),
+ * DMR_ECUDA. */
+int dmr_create(const dmr_config* cfg, void* dev_workspace, size_t bytes,
+               void* cuda_stream, dmr_ctx** out);
+
+/* Release host-side state (the workspace stays the caller's). NULL is ignored. */
+void dmr_destroy(dmr_ctx* ctx);
+
+/* Message of the last failed call on ctx (ctx NULL: of the calling thread's
+ * last failed dmr_workspace_bytes / dmr_create). Never NULL. */
+const char* dmr_last_error(const dmr_ctx* ctx);
+
+/* Gaussian seed n0 exp(-((x-x0)^2/sx^2 + (y-y0)^2/sy^2)) on the nodes of the
+ * coarse mesh and of the fine rectangle (Sec. IV), zero where the exponent is
+ * below -60; add != 0 adds it to the present density.  The fine density is
+ * then copied into the coinciding coarse nodes (Sec. III.C, direct copy). */
+int dmr_seed_gaussian(dmr_ctx* ctx, double n0, double x0, double y0, double sx, double sy,
+                      int add);
+
+/* Set the fine rectangle to coarse nodes [rect[0], rect[2]] x [rect[1], rect[3]]
+ * (i0, j0, i1, j1; i0 < i1 <= nx, j0 < j1 <= ny).  The first call creates the
+ * fine mesh with every field interpolated from the coarse mesh (Eq. 5a,
+ * frac = 1); later calls must contain the current rectangle and grow it as a
+ * flag-driven growth would (Sec. III.D).  Only at a period boundary.
+ * Errors: DMR_EINVAL, DMR_ECAPACITY, DMR_ESTATE (r = 1 or mid-period). */
+int dmr_set_patch(dmr_ctx* ctx, const int32_t rect[4]);
+
+/* Current rectangle (all -1 when there is none). */
+int dmr_get_patch(const dmr_ctx* ctx, int32_t rect[4]);
+
+/* Advance n_coarse_steps coarse EM steps (Sec. III.C sub-cycling; a
+ * continuity step, flags and growth at every period end).  Queued on the
+ * stream; each period end reads the flag bounding box back (one sync).
+ * Errors: DMR_ECAPACITY (growth beyond the cap; the run stops at that period
+ * end with the old rectangle), DMR_EUNSTABLE (NaN or w_p dt >= 2 detected at
+ * a period end), DMR_ECUDA. */
+int dmr_advance(dmr_ctx* ctx, int64_t n_coarse_steps);
+
+/* Checked mode: from the next period end on, the rectangle after period k is
+ * rects[4k .. 4k+3] instead of the growth policy (a recorded refinement log
+ * is replayed).  n_periods = 0 switches replay off. */
+int dmr_replay_log(dmr_ctx* ctx, const int32_t* rects, int64_t n_periods);
+
+/* Shape (rows, cols) and element size of a field at level 0 (coarse) or 1
+ * (fine rectangle). */
+int dmr_field_shape(const dmr_ctx* ctx, int field, int level, int32_t shape[2],
+                    int32_t* elem_bytes);
+
+/* Copy a field into dst (dense layout above).  dst_is_device != 0: dst is
+ * device memory and the copy is queued on the stream; otherwise dst is host
+ * memory and the call returns when the copy is done.  bytes must be at least
+ * rows*cols*elem_bytes (DMR_ECAPACITY otherwise). */
+int dmr_read(const dmr_ctx* ctx, int field, int level, void* dst, size_t bytes,
+             int dst_is_device);
+
+/* Overwrite a field (EX..NE, S2) from src (same layout).  Used to start from
+ * a given state or seed map.  src_is_device as in dmr_read. */
+int dmr_write(dmr_ctx* ctx, int field, int level, const void* src, size_t bytes,
+              int src_is_device);
+
+/* Statistics (dmr_stat indices) after waiting for the stream. */
+int dmr_stats(const dmr_ctx* ctx, double out[DMR_NSTATS]);
+
+/* Capture each full period (N_T coarse steps and the period-end kernels) in a
+ * CUDA graph and replay it while the rectangle is unchanged (enable = 1). */
+int dmr_set_graphs(dmr_ctx* ctx, int enable);
+
+/* Per-kernel timing with CUDA events recorded on the run's stream around each
+ * launch.  enable is a bit mask of the kernel classes to time (bit k for
+ * class k; -1 for all; 0 switches timing off); each call resets the sums.  dmr_kernel_time returns, for a kernel
+ * class, the summed device time in ms, the number of timed launches and the
+ * summed grid points (mesh nodes) those launches covered;
+ * dmr_kernel_class_name names a class (NULL past the last one).  Times are
+ * collected at period ends. */
+int dmr_set_timing(dmr_ctx* ctx, int enable);
+int dmr_kernel_time(const dmr_ctx* ctx, int kclass, double* ms, int64_t* launches,
+                    double* grid_points);
+const char* dmr_kernel_class_name(int kclass);
+
+/* Number of kernels the library has launched (graph replays count their
+ * kernel nodes). */
+int dmr_launch_count(const dmr_ctx* ctx, int64_t* launches);
+
+/* Wait for all work queued on the run's stream. */
+int dmr_sync(const dmr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMR_H */

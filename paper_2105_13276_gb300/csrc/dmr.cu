@@ -1,0 +1,945 @@
+// dmr.cu -- host side of the C ABI declared in include/dmr.h: configuration,
+// workspace layout, stream-ordered orchestration of the kernels in
+// dmr_kernels.cuh, per-period CUDA graphs and the growth decision.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dmr.h"
+#include "dmr_kernels.cuh"
+
+namespace {
+
+// CODATA 2018 (SI)
+constexpr double C0 = 299792458.0;
+constexpr double MU0 = 1.25663706212e-6;
+constexpr double EPS0 = 8.8541878128e-12;
+constexpr double QE = 1.602176634e-19;
+constexpr double ME = 9.1093837015e-31;
+constexpr double PI = 3.14159265358979323846;
+
+thread_local std::string g_err;
+
+std::string fmt(const char* f, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, f);
+  vsnprintf(buf, sizeof buf, f, ap);
+  va_end(ap);
+  return buf;
+}
+
+inline size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Physical set-up derived from a dmr_config (Sec. II.A readings).
+struct Derived {
+  double omega, lam, k, nu_m, dxc, dxf, dtc, dtf, De, Da, r_ei, nu_scale, nu_a, n_crit, n_th,
+      g_th, T;
+  int64_t cap;
+};
+
+int derive(const dmr_config* c, Derived* d, std::string* err) {
+  if (!c) { *err = "null config"; return DMR_EINVAL; }
+  if (c->nx < 4 || c->ny < 4) { *err = "nx and ny must be >= 4"; return DMR_EINVAL; }
+  if (c->r < 1 || c->r > 16) { *err = "r must be in [1, 16]"; return DMR_EINVAL; }
+  if (c->n_lambda < 1 || c->steps_per_period < 1) { *err = "n_lambda and steps_per_period must be >= 1"; return DMR_EINVAL; }
+  if (c->precision != 0 && c->precision != 1) { *err = "precision must be 0 (fp64) or 1 (fp32)"; return DMR_EINVAL; }
+  if (!(c->freq > 0) || !(c->p_torr > 0) || !std::isfinite(c->E0)) { *err = "freq and p_torr must be > 0, E0 finite"; return DMR_EINVAL; }
+  if (c->buffer_cells < 0) { *err = "buffer_cells must be >= 0"; return DMR_EINVAL; }
+  d->omega = 2.0 * PI * c->freq;
+  d->lam = C0 / c->freq;
+  d->k = d->omega / C0;
+  d->nu_m = 5.3e9 * c->p_torr;                       // Sec. II.A
+  d->dxc = d->lam / (double)c->n_lambda;
+  d->dxf = d->lam / ((double)c->r * (double)c->n_lambda);
+  d->dtc = 1.0 / (c->freq * (double)c->steps_per_period);
+  d->dtf = 1.0 / (c->freq * (double)((int64_t)c->r * c->steps_per_period));
+  d->De = c->De >= 0 ? c->De : 0.1 * 760.0 / c->p_torr;
+  d->Da = c->Da >= 0 ? c->Da : d->De / 100.0;
+  const double beta = c->beta_rec >= 0 ? c->beta_rec : 1.0;
+  const double Te = c->Te > 0 ? c->Te : 300.0;
+  d->r_ei = beta * 1e-13 * std::sqrt(300.0 / Te);   // Sec. II.A, m^3/s
+  d->nu_scale = c->nu_scale >= 0 ? c->nu_scale : 1.0;
+  d->nu_a = c->nu_a;
+  d->n_crit = ME * EPS0 * d->omega * d->omega / (QE * QE);
+  d->n_th = c->n_th >= 0 ? c->n_th : 1e-3 * d->n_crit;
+  d->g_th = c->g_th > 0 ? c->g_th : d->n_th / (4.0 * d->dxc);
+  d->T = 1.0 / c->freq;
+  const int64_t full = (int64_t)c->r * c->nx * (int64_t)c->r * c->ny;
+  d->cap = c->patch_cap_cells > 0 ? std::min<int64_t>(c->patch_cap_cells, full) : full;
+  // stability guard
+  const double courant = (double)c->n_lambda / (double)c->steps_per_period;
+  if (courant > 1.0 / std::sqrt(2.0)) {
+    *err = fmt("Courant number %.4f > 1/sqrt(2)", courant);
+    return DMR_EUNSTABLE;
+  }
+  const double dmax = std::max(d->De, d->Da);
+  if (dmax * d->T / (d->dxf * d->dxf) > 0.25) {
+    *err = fmt("diffusion number %.4f > 1/4", dmax * d->T / (d->dxf * d->dxf));
+    return DMR_EUNSTABLE;
+  }
+  return DMR_OK;
+}
+
+constexpr int BX = 32, BY = 8;
+
+struct Layout {
+  size_t es = 8;       // bytes per field element
+  int pc = 0;          // coarse pitch (elements)
+  size_t cplane = 0;   // coarse elements per array
+  size_t fplane = 0;   // fine elements per array (capacity)
+  int nblk_c = 0, nblk_f = 0;
+  size_t off_c[9] = {}, off_cS2 = 0;      // Ex Ey Hz vx vy n ntmp D nu
+  size_t off_f[2][6] = {}, off_fS2[2] = {};
+  size_t off_ftmp[3] = {};                // ntmp D nu
+  size_t off_strip[4] = {};
+  size_t off_tab[4] = {};                 // ckx_c skx_c ckx_f skx_f
+  size_t off_mask = 0, off_part[4] = {}, off_ctl = 0, off_view = 0;
+  size_t total = 0;
+};
+
+int64_t fine_pitch(int64_t nfx) { return (int64_t)up((size_t)nfx + 1, 64); }
+
+int make_layout(const dmr_config* c, const Derived& d, Layout* L, std::string* err) {
+  L->es = c->precision == 1 ? 4 : 8;
+  const int64_t nx = c->nx, ny = c->ny, r = c->r;
+  L->pc = (int)up((size_t)nx + 1, 64);
+  L->cplane = (size_t)(ny + 1) * L->pc;
+  if (r > 1) {
+    // any rectangle with nfx*nfy <= cap fits (nfy+1) * roundup(nfx+1, 64) elements
+    const int64_t bound = d.cap + r * nx + 64 * (r * ny + 1) + 64;
+    const int64_t full = (r * ny + 1) * fine_pitch(r * nx);
+    L->fplane = (size_t)std::min(bound, full);
+  }
+  if ((int64_t)L->cplane >= (1ll << 31) || (int64_t)L->fplane >= (1ll << 31)) {
+    *err = "mesh too large for 32-bit element indices";
+    return DMR_EINVAL;
+  }
+  L->nblk_c = (int)(((nx + 1 + BX - 1) / BX) * ((ny + 1 + BY - 1) / BY));
+  L->nblk_f = r > 1 ? (int)(((r * nx + 1 + BX - 1) / BX) * ((r * ny + 1 + BY - 1) / BY)) : 0;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = up(o + bytes, 256); return at; };
+  for (int q = 0; q < 9; ++q) L->off_c[q] = take(L->cplane * L->es);
+  L->off_cS2 = take(L->cplane * 8);
+  if (r > 1) {
+    for (int s = 0; s < 2; ++s) {
+      for (int q = 0; q < 6; ++q) L->off_f[s][q] = take(L->fplane * L->es);
+      L->off_fS2[s] = take(L->fplane * 8);
+    }
+    for (int q = 0; q < 3; ++q) L->off_ftmp[q] = take(L->fplane * L->es);
+    const size_t sl = (size_t)std::max(nx, ny) + 1;
+    for (int q = 0; q < 4; ++q) L->off_strip[q] = take(sl * L->es);
+  }
+  L->off_tab[0] = take((size_t)(nx + 1) * L->es);
+  L->off_tab[1] = take((size_t)(nx + 1) * L->es);
+  L->off_tab[2] = take((size_t)(r * nx + 1) * L->es);
+  L->off_tab[3] = take((size_t)(r * nx + 1) * L->es);
+  L->off_mask = take((size_t)(nx + 1) * (ny + 1));
+  L->off_part[0] = take((size_t)L->nblk_c * 8);
+  L->off_part[1] = take((size_t)std::max(L->nblk_f, 1) * 8);
+  L->off_part[2] = take((size_t)L->nblk_c * 8);
+  L->off_part[3] = take((size_t)std::max(L->nblk_f, 1) * 8);
+  L->off_ctl = take(sizeof(dmr::Ctl));
+  L->off_view = take(std::max(L->cplane, L->fplane) * 8);
+  L->total = o;
+  return DMR_OK;
+}
+
+// --------------------------------------------------------------------------
+struct Base {
+  dmr_config cfg{};
+  Derived d{};
+  Layout L{};
+  char* ws = nullptr;
+  cudaStream_t st = nullptr;
+  std::string err;
+  int64_t m = 0;            // coarse steps done (time level of coarse E)
+  int64_t launches = 0;
+  bool capturing = false;
+  int64_t graph_nodes = 0;
+  bool graphs = false;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<int32_t> replay;
+  size_t replay_pos = 0;
+  bool has_fine = false;
+  int rect[4] = {-1, -1, -1, -1};
+  // timing: event pairs around launches; direct launches use a pool that is
+  // recycled every period, a captured graph owns its events until dropped
+  bool timing = false;
+  std::vector<cudaEvent_t> evd, evg;
+  size_t evd_used = 0;
+  struct Pend { int cls; int a, b; double units; };
+  std::vector<Pend> pend, gpend;
+  double kt_ms[8] = {};
+  int64_t kt_n[8] = {};
+  double kt_units[8] = {};
+
+  virtual ~Base() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    for (auto e : evd) cudaEventDestroy(e);
+    for (auto e : evg) cudaEventDestroy(e);
+  }
+  int fail(int code, const std::string& msg) { err = msg; return code; }
+  int ck(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return DMR_OK;
+    return fail(DMR_ECUDA, fmt("%s: %s", what, cudaGetErrorString(e)));
+  }
+  void drop_graph() {
+    if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+    gpend.clear();
+    for (auto e : evg) cudaEventDestroy(e);
+    evg.clear();
+  }
+  int ev_get() {
+    if (capturing) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      evg.push_back(e);
+      return (int)evg.size() - 1;
+    }
+    if (evd_used >= evd.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      evd.push_back(e);
+    }
+    return (int)evd_used++;
+  }
+  cudaEvent_t ev_at(int idx, bool graph) const { return graph ? evg[idx] : evd[idx]; }
+  // inside a stream capture a plain record only orders work; the external
+  // flag turns it into an event-record node that fires on every replay
+  void record(cudaEvent_t e) {
+    if (capturing) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
+  }
+  unsigned timing_mask = 0xffffffffu;
+  // units: grid points (nodes) the timed launch covers
+  int tbeg(int cls, double units) {
+    if (!timing || !((timing_mask >> cls) & 1u)) return -1;
+    int a = ev_get();
+    if (a < 0) return -1;
+    record(ev_at(a, capturing));
+    auto& v = capturing ? gpend : pend;
+    v.push_back({cls, a, -1, units});
+    return (int)v.size() - 1;
+  }
+  void tend(int h) {
+    if (h < 0) return;
+    auto& v = capturing ? gpend : pend;
+    int b = ev_get();
+    if (b < 0) { v[h].cls = -1; return; }
+    record(ev_at(b, capturing));
+    v[h].b = b;
+  }
+  void harvest(const std::vector<Pend>& v, bool graph) {
+    for (const auto& p : v) {
+      if (p.cls < 0 || p.b < 0) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev_at(p.a, graph), ev_at(p.b, graph)) == cudaSuccess) {
+        kt_ms[p.cls] += ms;
+        kt_n[p.cls] += 1;
+        kt_units[p.cls] += p.units;
+      }
+    }
+  }
+  void harvest_period(bool graph_ran) {
+    if (!timing) return;
+    harvest(pend, false);
+    pend.clear();
+    evd_used = 0;
+    if (graph_ran) harvest(gpend, true);
+  }
+  void counted(int k) {
+    if (capturing) graph_nodes += k; else launches += k;
+  }
+
+  virtual int init() = 0;
+  virtual int seed(double n0, double x0, double y0, double sx, double sy, int add) = 0;
+  virtual int set_patch(const int32_t* r4) = 0;
+  virtual int advance(int64_t n) = 0;
+  virtual int shape(int field, int level, int32_t* s, int32_t* eb) const = 0;
+  virtual int read(int field, int level, void* dst, size_t bytes, int dev) = 0;
+  virtual int write(int field, int level, const void* src, size_t bytes, int dev) = 0;
+  virtual int stats(double* out) = 0;
+};
+
+template <class T>
+struct Engine final : Base {
+  dmr::Mesh<T> C{};
+  T *c_ntmp = nullptr, *c_D = nullptr, *c_nu = nullptr;
+  dmr::Mesh<T> F[2]{};
+  T* fptr[2][6] = {};
+  double* fS2[2] = {};
+  int cur = 0;
+  T *f_ntmp = nullptr, *f_D = nullptr, *f_nu = nullptr;
+  T* strip[4] = {};
+  T *ckx_c = nullptr, *skx_c = nullptr, *ckx_f = nullptr, *skx_f = nullptr;
+  uint8_t* mask = nullptr;
+  double* part[4] = {};
+  dmr::Ctl* ctl = nullptr;
+  double* view = nullptr;
+  int nblk_f_cur = 0;
+
+  template <class P>
+  P* at(size_t off) { return reinterpret_cast<P*>(ws + off); }
+
+  int init() override {
+    C.Ex = at<T>(L.off_c[0]); C.Ey = at<T>(L.off_c[1]); C.Hz = at<T>(L.off_c[2]);
+    C.vx = at<T>(L.off_c[3]); C.vy = at<T>(L.off_c[4]); C.n = at<T>(L.off_c[5]);
+    c_ntmp = at<T>(L.off_c[6]); c_D = at<T>(L.off_c[7]); c_nu = at<T>(L.off_c[8]);
+    C.S2 = at<double>(L.off_cS2);
+    C.nx = cfg.nx; C.ny = cfg.ny; C.p = L.pc;
+    if (cfg.r > 1) {
+      for (int s = 0; s < 2; ++s) {
+        for (int q = 0; q < 6; ++q) fptr[s][q] = at<T>(L.off_f[s][q]);
+        fS2[s] = at<double>(L.off_fS2[s]);
+      }
+      f_ntmp = at<T>(L.off_ftmp[0]); f_D = at<T>(L.off_ftmp[1]); f_nu = at<T>(L.off_ftmp[2]);
+      for (int q = 0; q < 4; ++q) strip[q] = at<T>(L.off_strip[q]);
+    }
+    ckx_c = at<T>(L.off_tab[0]); skx_c = at<T>(L.off_tab[1]);
+    ckx_f = at<T>(L.off_tab[2]); skx_f = at<T>(L.off_tab[3]);
+    mask = at<uint8_t>(L.off_mask);
+    for (int q = 0; q < 4; ++q) part[q] = at<double>(L.off_part[q]);
+    ctl = at<dmr::Ctl>(L.off_ctl);
+    view = at<double>(L.off_view);
+    int s = ck(cudaMemsetAsync(ws, 0, L.total, st), "cudaMemsetAsync(workspace)");
+    if (s) return s;
+    // incident-wave column tables: cos(k x), sin(k x) at the node columns
+    std::vector<T> tc(cfg.nx + 1), ts(cfg.nx + 1);
+    for (int g = 0; g <= cfg.nx; ++g) {
+      double x = (double)g * d.dxc;
+      tc[g] = (T)std::cos(d.k * x);
+      ts[g] = (T)std::sin(d.k * x);
+    }
+    if ((s = ck(cudaMemcpyAsync(ckx_c, tc.data(), tc.size() * sizeof(T), cudaMemcpyHostToDevice, st), "upload tables"))) return s;
+    if ((s = ck(cudaMemcpyAsync(skx_c, ts.data(), ts.size() * sizeof(T), cudaMemcpyHostToDevice, st), "upload tables"))) return s;
+    const int nf = cfg.r * cfg.nx;
+    std::vector<T> fc(nf + 1), fs(nf + 1);
+    for (int g = 0; g <= nf; ++g) {
+      double x = (double)g * d.dxf;
+      fc[g] = (T)std::cos(d.k * x);
+      fs[g] = (T)std::sin(d.k * x);
+    }
+    if ((s = ck(cudaMemcpyAsync(ckx_f, fc.data(), fc.size() * sizeof(T), cudaMemcpyHostToDevice, st), "upload tables"))) return s;
+    if ((s = ck(cudaMemcpyAsync(skx_f, fs.data(), fs.size() * sizeof(T), cudaMemcpyHostToDevice, st), "upload tables"))) return s;
+    return ck(cudaStreamSynchronize(st), "init sync");
+  }
+
+  static dim3 nodes_grid(int nx, int ny) { return dim3((nx + 1 + BX - 1) / BX, (ny + 1 + BY - 1) / BY); }
+
+  dmr::Mesh<T> fine_view(int set, const int* rc) const {
+    dmr::Mesh<T> f;
+    f.Ex = fptr[set][0]; f.Ey = fptr[set][1]; f.Hz = fptr[set][2];
+    f.vx = fptr[set][3]; f.vy = fptr[set][4]; f.n = fptr[set][5]; f.S2 = fS2[set];
+    f.nx = cfg.r * (rc[2] - rc[0]);
+    f.ny = cfg.r * (rc[3] - rc[1]);
+    f.p = (int)fine_pitch(f.nx);
+    return f;
+  }
+
+  bool side_on_edge(int sd) const {
+    switch (sd) {
+      case dmr::SIDE_LEFT: return rect[0] == 0;
+      case dmr::SIDE_RIGHT: return rect[2] == cfg.nx;
+      case dmr::SIDE_BOTTOM: return rect[1] == 0;
+      default: return rect[3] == cfg.ny;
+    }
+  }
+
+  dmr::Step<T> make_step(int rr, int64_t level, bool accum) const {
+    const double dx = d.lam / ((double)rr * (double)cfg.n_lambda);
+    const double dt = 1.0 / (cfg.freq * (double)((int64_t)rr * cfg.steps_per_period));
+    const double h = 0.5 * d.nu_m * dt;
+    dmr::Step<T> s;
+    s.ch = (T)(dt / (MU0 * dx));
+    s.ce = (T)(dt / (EPS0 * dx));
+    s.cj = (T)(dt * QE / (2.0 * EPS0));
+    s.va = (T)((1.0 - h) / (1.0 + h));
+    s.vb = (T)((QE * dt / ME) / (1.0 + h));
+    s.mur = (T)((C0 * dt - dx) / (C0 * dt + dx));
+    const int64_t N = (int64_t)rr * cfg.steps_per_period;
+    const double phase = 2.0 * PI * (double)(level % N) / (double)N;
+    s.E0 = (T)cfg.E0;
+    s.sphi = (T)std::sin(phase);
+    s.cphi = (T)std::cos(phase);
+    if (rr == 1) { s.ckx = ckx_c; s.skx = skx_c; }
+    else { s.ckx = ckx_f + (size_t)rr * rect[0]; s.skx = skx_f + (size_t)rr * rect[0]; }
+    s.accum = accum ? 1 : 0;
+    return s;
+  }
+
+  dmr::Dens make_dens(int rr) const {
+    dmr::Dens q;
+    q.N = (double)((int64_t)rr * cfg.steps_per_period);
+    const double w = d.omega / d.nu_m;
+    q.g = 1.0 + w * w;
+    q.hp = 100.0 * cfg.p_torr;
+    q.A = d.nu_scale * 5.14e11 * cfg.p_torr;
+    q.nu_m = d.nu_m; q.nu_a = d.nu_a; q.De = d.De; q.Da = d.Da;
+    q.wp2c = QE * QE / (ME * EPS0);
+    q.heat = QE * QE / (ME * d.nu_m);
+    q.T = d.T;
+    const double dx = rr == 1 ? d.dxc : d.dxf;
+    q.dx2 = dx * dx;
+    q.r_ei = d.r_ei;
+    return q;
+  }
+
+  int launched(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(DMR_ECUDA, fmt("launch %s: %s", what, cudaGetErrorString(e)));
+    return DMR_OK;
+  }
+
+  // one coarse step from level mlev: coarse H, E; r fine sub-steps; restriction
+  int launch_coarse_step(int64_t mlev) {
+    const int NT = cfg.steps_per_period, r = cfg.r;
+    dmr::Step<T> sc = make_step(1, mlev, (mlev % NT) != 0);
+    dmr::Bnd<T> bc{};
+    for (int q = 0; q < 4; ++q) bc.mode[q] = dmr::BC_MUR;
+    bc.r = 1;
+    if (has_fine) {
+      const int at_[4] = {rect[0], rect[2], rect[1], rect[3]};
+      for (int q = 0; q < 4; ++q)
+        if (!side_on_edge(q)) { bc.save[q] = strip[q]; bc.save_at[q] = at_[q]; }
+    }
+    const dim3 blk(BX, BY);
+    const double cn = (double)(C.nx + 1) * (C.ny + 1);
+    int h = tbeg(0, cn);
+    dmr::k_h<T><<<nodes_grid(C.nx, C.ny), blk, 0, st>>>(C, sc);
+    tend(h);
+    counted(1);
+    h = tbeg(1, cn);
+    dmr::k_e<T><<<nodes_grid(C.nx, C.ny), blk, 0, st>>>(C, sc, bc);
+    tend(h);
+    counted(1);
+    if (int s = launched("coarse EM")) return s;
+    if (!has_fine) return DMR_OK;
+    dmr::Mesh<T> f = F[cur];
+    dmr::Bnd<T> bf{};
+    bf.r = r;
+    for (int q = 0; q < 4; ++q) {
+      if (side_on_edge(q)) { bf.mode[q] = dmr::BC_MUR; continue; }
+      bf.mode[q] = dmr::BC_CFB;
+      bf.old_line[q] = strip[q];
+      if (q == dmr::SIDE_BOTTOM || q == dmr::SIDE_TOP) {
+        const int jl = q == dmr::SIDE_BOTTOM ? rect[1] : rect[3];
+        bf.new_line[q] = C.Ex + (size_t)jl * C.p;
+        bf.new_stride[q] = 1;
+        bf.len[q] = cfg.nx;
+        bf.start[q] = rect[0];
+      } else {
+        const int il = q == dmr::SIDE_LEFT ? rect[0] : rect[2];
+        bf.new_line[q] = C.Ey + il;
+        bf.new_stride[q] = C.p;
+        bf.len[q] = cfg.ny;
+        bf.start[q] = rect[1];
+      }
+    }
+    const dim3 gf = nodes_grid(f.nx, f.ny);
+    const double fn = (double)(f.nx + 1) * (f.ny + 1);
+    for (int k = 1; k <= r; ++k) {
+      const int64_t mf = (int64_t)r * mlev + (k - 1);
+      dmr::Step<T> sf = make_step(r, mf, (mf % ((int64_t)r * NT)) != 0);
+      bf.frac = (T)((double)k / (double)r);
+      h = tbeg(2, fn);
+      dmr::k_h<T><<<gf, blk, 0, st>>>(f, sf);
+      tend(h);
+      h = tbeg(3, fn);
+      dmr::k_e<T><<<gf, blk, 0, st>>>(f, sf, bf);
+      tend(h);
+      counted(2);
+    }
+    const int jlo = side_on_edge(dmr::SIDE_BOTTOM) ? rect[1] : rect[1] + 1;
+    const int jhi = side_on_edge(dmr::SIDE_TOP) ? rect[3] : rect[3] - 1;
+    const int ilo = side_on_edge(dmr::SIDE_LEFT) ? rect[0] : rect[0] + 1;
+    const int ihi = side_on_edge(dmr::SIDE_RIGHT) ? rect[2] : rect[2] - 1;
+    const dim3 gr((rect[2] - rect[0] + 1 + BX - 1) / BX, (rect[3] - rect[1] + 1 + BY - 1) / BY);
+    h = tbeg(4, (double)(rect[2] - rect[0] + 1) * (rect[3] - rect[1] + 1));
+    dmr::k_restrict<T><<<gr, blk, 0, st>>>(C, f, rect[0], rect[1], rect[2], rect[3], r, jlo, jhi, ilo, ihi);
+    tend(h);
+    counted(1);
+    return launched("fine EM / restrict");
+  }
+
+  // continuity step, totals and flags at the end of a period (coarse level mlev)
+  int launch_period_end(int64_t mlev) {
+    const int r = cfg.r;
+    const dim3 blk(BX, BY);
+    int h = tbeg(5, (double)(C.nx + 1) * (C.ny + 1) +
+                        (has_fine ? (double)(F[cur].nx + 1) * (F[cur].ny + 1) : 0.0));
+    dmr::Wts wc{cfg.nx, cfg.ny, has_fine ? 1 : 0, rect[0], rect[1], rect[2], rect[3]};
+    dmr::Dens dc = make_dens(1);
+    dmr::Step<T> sc = make_step(1, mlev, true);
+    const dim3 gc = nodes_grid(C.nx, C.ny);
+    dmr::k_rates<T><<<gc, blk, 0, st>>>(C, sc, dc, wc, c_D, c_nu, part[0], ctl);
+    dmr::Mesh<T> f{};
+    dmr::Dens df{};
+    dmr::Wts wf{};
+    dim3 gf(1, 1);
+    int nbf = 0;
+    int n_launch = 1;
+    if (has_fine) {
+      f = F[cur];
+      df = make_dens(r);
+      wf = dmr::Wts{f.nx, f.ny, 0, 0, 0, 0, 0};
+      gf = nodes_grid(f.nx, f.ny);
+      nbf = (int)(gf.x * gf.y);
+      dmr::Step<T> sf = make_step(r, (int64_t)r * mlev, true);
+      dmr::k_rates<T><<<gf, blk, 0, st>>>(f, sf, df, wf, f_D, f_nu, part[1], nullptr);
+      ++n_launch;
+    }
+    dmr::Dir<T> none{};
+    dmr::k_density<T><<<gc, blk, 0, st>>>(C, c_D, c_nu, c_ntmp, dc, none);
+    ++n_launch;
+    if (has_fine) {
+      dmr::Dir<T> dir{};
+      dir.r = r;
+      for (int q = 0; q < 4; ++q) {
+        if (side_on_edge(q)) continue;
+        dir.on[q] = 1;
+        if (q == dmr::SIDE_BOTTOM || q == dmr::SIDE_TOP) {
+          const int jl = q == dmr::SIDE_BOTTOM ? rect[1] : rect[3];
+          dir.line[q] = c_ntmp + (size_t)jl * C.p;
+          dir.stride[q] = 1;
+          dir.len[q] = cfg.nx + 1;
+          dir.start[q] = rect[0];
+        } else {
+          const int il = q == dmr::SIDE_LEFT ? rect[0] : rect[2];
+          dir.line[q] = c_ntmp + il;
+          dir.stride[q] = C.p;
+          dir.len[q] = cfg.ny + 1;
+          dir.start[q] = rect[1];
+        }
+      }
+      dmr::k_density<T><<<gf, blk, 0, st>>>(f, f_D, f_nu, f_ntmp, df, dir);
+      ++n_launch;
+    }
+    dmr::k_commit<T><<<gc, blk, 0, st>>>(C, c_ntmp, wc, has_fine ? f_ntmp : nullptr,
+                                          has_fine ? f.p : 0, r, part[2]);
+    ++n_launch;
+    if (has_fine) {
+      dmr::k_commit<T><<<gf, blk, 0, st>>>(f, f_ntmp, wf, nullptr, 0, r, part[3]);
+      const double gs = 1.0 / (2.0 * d.dxc * d.g_th);
+      dmr::k_flags<T><<<gc, blk, 0, st>>>(C, (T)d.n_th, (T)gs, mask, ctl);
+      n_launch += 2;
+    }
+    dmr::k_finalize<<<1, 1024, 0, st>>>(part[0], (int)(gc.x * gc.y), part[1], nbf, part[2],
+                                         (int)(gc.x * gc.y), part[3], nbf, d.dxc * d.dxc,
+                                         d.dxf * d.dxf, d.T, ctl);
+    ++n_launch;
+    tend(h);
+    counted(n_launch);
+    return launched("period end");
+  }
+
+  // host side of the period end: read the control block, stability guard,
+  // growth policy (or replay), expansion
+  int period_end_host(bool graph_ran = false) {
+    dmr::Ctl hc;
+    if (int s = ck(cudaMemcpyAsync(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, st), "read control block")) return s;
+    if (int s = ck(cudaStreamSynchronize(st), "period sync")) return s;
+    harvest_period(graph_ran);
+    if (hc.err) return fail(DMR_EUNSTABLE, "NaN in the density or totals at a period end");
+    const double wp_lim = (2.0 / (has_fine ? d.dtf : d.dtc));
+    const double n_lim = wp_lim * wp_lim * ME * EPS0 / (QE * QE);
+    if (hc.st[4] >= n_lim)
+      return fail(DMR_EUNSTABLE, fmt("density %.3e reaches w_p dt >= 2", hc.st[4]));
+    if (!has_fine) return DMR_OK;
+    int nr[4] = {rect[0], rect[1], rect[2], rect[3]};
+    if (!replay.empty()) {
+      if (replay_pos * 4 + 3 < replay.size()) {
+        for (int q = 0; q < 4; ++q) nr[q] = replay[replay_pos * 4 + q];
+        ++replay_pos;
+      }
+    } else if (cfg.growth && hc.nflag > 0) {
+      const int b = cfg.buffer_cells;
+      const int c4[4] = {std::max(hc.bbox[0] - b, 0), std::max(hc.bbox[1] - b, 0),
+                         std::min(hc.bbox[2] + b, cfg.nx), std::min(hc.bbox[3] + b, cfg.ny)};
+      nr[0] = std::min(rect[0], c4[0]);
+      nr[1] = std::min(rect[1], c4[1]);
+      nr[2] = std::max(rect[2], c4[2]);
+      nr[3] = std::max(rect[3], c4[3]);
+    }
+    if (nr[0] == rect[0] && nr[1] == rect[1] && nr[2] == rect[2] && nr[3] == rect[3]) return DMR_OK;
+    return expand(nr);
+  }
+
+  int check_rect(const int* nr) {
+    if (!(0 <= nr[0] && nr[0] < nr[2] && nr[2] <= cfg.nx && 0 <= nr[1] && nr[1] < nr[3] &&
+          nr[3] <= cfg.ny))
+      return fail(DMR_EINVAL, fmt("bad rectangle (%d,%d,%d,%d)", nr[0], nr[1], nr[2], nr[3]));
+    if (has_fine && !(nr[0] <= rect[0] && nr[1] <= rect[1] && nr[2] >= rect[2] && nr[3] >= rect[3]))
+      return fail(DMR_EINVAL, "the rectangle can only grow");
+    const int64_t cells = (int64_t)cfg.r * (nr[2] - nr[0]) * (int64_t)cfg.r * (nr[3] - nr[1]);
+    if (cells > d.cap)
+      return fail(DMR_ECAPACITY, fmt("rectangle of %lld fine cells exceeds the capacity %lld",
+                                     (long long)cells, (long long)d.cap));
+    return DMR_OK;
+  }
+
+  int expand(const int* nr) {
+    if (int s = check_rect(nr)) return s;
+    const int nxt = has_fine ? 1 - cur : cur;
+    dmr::Mesh<T> nf = fine_view(nxt, nr);
+    if ((size_t)(nf.ny + 1) * nf.p > L.fplane) return fail(DMR_ECAPACITY, "fine arrays exceed the workspace");
+    dmr::Mesh<T> of = has_fine ? F[cur] : nf;
+    const int oI0 = has_fine ? rect[0] : nr[0], oJ0 = has_fine ? rect[1] : nr[1];
+    int h = tbeg(6, (double)(nf.nx + 1) * (nf.ny + 1));
+    dmr::k_expand<T><<<nodes_grid(nf.nx, nf.ny), dim3(BX, BY), 0, st>>>(
+        nf, of, C, nr[0], nr[1], oI0, oJ0, has_fine ? 1 : 0, cfg.r);
+    tend(h);
+    counted(1);
+    if (int s = launched("expand")) return s;
+    cur = nxt;
+    F[cur] = nf;
+    for (int q = 0; q < 4; ++q) rect[q] = nr[q];
+    has_fine = true;
+    drop_graph();
+    return DMR_OK;
+  }
+
+  int seed(double n0, double x0, double y0, double sx, double sy, int add) override {
+    if (!(sx > 0) || !(sy > 0)) return fail(DMR_EINVAL, "seed widths must be > 0");
+    const dim3 blk(BX, BY);
+    dmr::k_seed<T><<<nodes_grid(C.nx, C.ny), blk, 0, st>>>(C, 0, 0, d.dxc, n0, x0, y0, sx, sy, add);
+    counted(1);
+    if (has_fine) {
+      dmr::Mesh<T> f = F[cur];
+      dmr::k_seed<T><<<nodes_grid(f.nx, f.ny), blk, 0, st>>>(f, cfg.r * rect[0], cfg.r * rect[1],
+                                                             d.dxf, n0, x0, y0, sx, sy, add);
+      inject();
+      counted(1);
+    }
+    return launched("seed");
+  }
+
+  void inject() {
+    const dim3 g((rect[2] - rect[0] + 1 + BX - 1) / BX, (rect[3] - rect[1] + 1 + BY - 1) / BY);
+    dmr::k_inject<T><<<g, dim3(BX, BY), 0, st>>>(C, F[cur], rect[0], rect[1], rect[2], rect[3], cfg.r);
+    counted(1);
+  }
+
+  int set_patch(const int32_t* r4) override {
+    if (cfg.r == 1) return fail(DMR_ESTATE, "r = 1: a uniform mesh has no fine rectangle");
+    if (m % cfg.steps_per_period != 0) return fail(DMR_ESTATE, "the rectangle changes only at a period boundary");
+    int nr[4] = {r4[0], r4[1], r4[2], r4[3]};
+    if (has_fine && nr[0] == rect[0] && nr[1] == rect[1] && nr[2] == rect[2] && nr[3] == rect[3]) return DMR_OK;
+    return expand(nr);
+  }
+
+  int advance(int64_t n) override {
+    if (n < 0) return fail(DMR_EINVAL, "negative step count");
+    const int NT = cfg.steps_per_period;
+    while (n > 0) {
+      if (graphs && m % NT == 0 && n >= NT) {
+        if (!gexec) {
+          if (int s = capture()) return s;
+        }
+        if (int s = ck(cudaGraphLaunch(gexec, st), "cudaGraphLaunch")) return s;
+        launches += graph_nodes;
+        m += NT;
+        n -= NT;
+        if (int s = period_end_host(true)) return s;
+        continue;
+      }
+      if (int s = launch_coarse_step(m)) return s;
+      ++m;
+      --n;
+      if (m % NT == 0) {
+        if (int s = launch_period_end(m)) return s;
+        if (int s = period_end_host()) return s;
+      }
+    }
+    return DMR_OK;
+  }
+
+  int capture() {
+    drop_graph();
+    const int NT = cfg.steps_per_period;
+    cudaGraph_t g = nullptr;
+    if (int s = ck(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture")) return s;
+    capturing = true;
+    graph_nodes = 0;
+    int s = DMR_OK;
+    for (int q = 0; q < NT && !s; ++q) s = launch_coarse_step(m + q);
+    if (!s) s = launch_period_end(m + NT);
+    capturing = false;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (s) { if (g) cudaGraphDestroy(g); gpend.clear(); return s; }
+    if (e != cudaSuccess) { gpend.clear(); return ck(e, "end capture"); }
+    e = cudaGraphInstantiate(&gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { gexec = nullptr; gpend.clear(); return ck(e, "graph instantiate"); }
+    return DMR_OK;
+  }
+
+  int dims(int field, int level, int* rows, int* cols, int* es) const {
+    int nx, ny;
+    if (level == 0) { nx = C.nx; ny = C.ny; }
+    else if (level == 1 && has_fine) { nx = F[cur].nx; ny = F[cur].ny; }
+    else return DMR_ESTATE;
+    *es = (int)L.es;
+    switch (field) {
+      case DMR_FIELD_EX: case DMR_FIELD_VX: *rows = ny + 1; *cols = nx; break;
+      case DMR_FIELD_EY: case DMR_FIELD_VY: *rows = ny; *cols = nx + 1; break;
+      case DMR_FIELD_HZ: *rows = ny; *cols = nx; break;
+      case DMR_FIELD_NE: *rows = ny + 1; *cols = nx + 1; break;
+      case DMR_FIELD_S2: *rows = ny + 1; *cols = nx + 1; *es = 8; break;
+      case DMR_FIELD_MASK:
+        if (level != 0 || cfg.r == 1) return DMR_ESTATE;
+        *rows = ny + 1; *cols = nx + 1; *es = 1; break;
+      default: return DMR_EINVAL;
+    }
+    return DMR_OK;
+  }
+
+  int shape(int field, int level, int32_t* s, int32_t* eb) const override {
+    int rows, cols, es;
+    int st_ = dims(field, level, &rows, &cols, &es);
+    if (st_) return st_;
+    s[0] = rows; s[1] = cols;
+    if (eb) *eb = es;
+    return DMR_OK;
+  }
+
+  void* field_ptr(int field, int level) {
+    const dmr::Mesh<T>& mm = level == 0 ? C : F[cur];
+    switch (field) {
+      case DMR_FIELD_EX: return mm.Ex;
+      case DMR_FIELD_EY: return mm.Ey;
+      case DMR_FIELD_HZ: return mm.Hz;
+      case DMR_FIELD_VX: return mm.vx;
+      case DMR_FIELD_VY: return mm.vy;
+      case DMR_FIELD_NE: return mm.n;
+      case DMR_FIELD_S2: return mm.S2;
+      default: return mask;
+    }
+  }
+
+  int read(int field, int level, void* dst, size_t bytes, int dev) override {
+    int rows, cols, es;
+    if (int s = dims(field, level, &rows, &cols, &es)) return fail(s, "no such field / level");
+    if (bytes < (size_t)rows * cols * es) return fail(DMR_ECAPACITY, "destination too small");
+    const int p = field == DMR_FIELD_MASK ? cols : (level == 0 ? C.p : F[cur].p);
+    const void* src = field_ptr(field, level);
+    if (field == DMR_FIELD_S2 && m % cfg.steps_per_period != 0) {
+      // S2 holds the levels before the current one; add the current level so
+      // the result is the running sum through the present E level
+      const int rr = level == 0 ? 1 : cfg.r;
+      const int64_t lev = level == 0 ? m : (int64_t)cfg.r * m;
+      dmr::Step<T> s = make_step(rr, lev, true);
+      const dmr::Mesh<T>& mm = level == 0 ? C : F[cur];
+      dmr::k_s2_view<T><<<nodes_grid(mm.nx, mm.ny), dim3(BX, BY), 0, st>>>(mm, s, view);
+      counted(1);
+      if (int e = launched("S2 view")) return e;
+      src = view;
+    }
+    const size_t wb = (size_t)cols * es;
+    cudaError_t e = cudaMemcpy2DAsync(dst, wb, src, (size_t)p * es, wb, rows,
+                                      dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    if (int s = ck(e, "cudaMemcpy2DAsync(read)")) return s;
+    if (!dev) return ck(cudaStreamSynchronize(st), "read sync");
+    return DMR_OK;
+  }
+
+  int write(int field, int level, const void* src, size_t bytes, int dev) override {
+    if (field == DMR_FIELD_MASK) return fail(DMR_EINVAL, "the mask is not writable");
+    int rows, cols, es;
+    if (int s = dims(field, level, &rows, &cols, &es)) return fail(s, "no such field / level");
+    if (bytes < (size_t)rows * cols * es) return fail(DMR_ECAPACITY, "source too small");
+    const int p = level == 0 ? C.p : F[cur].p;
+    const size_t wb = (size_t)cols * es;
+    cudaError_t e = cudaMemcpy2DAsync(field_ptr(field, level), (size_t)p * es, src, wb, wb, rows,
+                                      dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (int s = ck(e, "cudaMemcpy2DAsync(write)")) return s;
+    if (field == DMR_FIELD_NE && level == 1) inject();
+    if (!dev) return ck(cudaStreamSynchronize(st), "write sync");
+    return launched("write");
+  }
+
+  int stats(double* out) override {
+    dmr::Ctl hc;
+    if (int s = ck(cudaMemcpyAsync(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, st), "stats")) return s;
+    if (int s = ck(cudaStreamSynchronize(st), "stats sync")) return s;
+    const double fine_cells = has_fine ? (double)F[cur].nx * (double)F[cur].ny : 0.0;
+    out[DMR_STAT_T] = (double)m * d.dtc;
+    out[DMR_STAT_R] = has_fine ? fine_cells / ((double)cfg.r * cfg.r * (double)cfg.nx * cfg.ny) : 0.0;
+    out[DMR_STAT_FINE_CELLS] = fine_cells;
+    out[DMR_STAT_NE] = hc.st[0];
+    out[DMR_STAT_PABS] = hc.st[1];
+    out[DMR_STAT_WABS] = hc.st[2];
+    out[DMR_STAT_PERIODS] = hc.st[3];
+    out[DMR_STAT_COARSE_STEPS] = (double)m;
+    out[DMR_STAT_NMAX] = hc.st[4];
+    out[DMR_STAT_FLAGS] = (double)hc.nflag;
+    return DMR_OK;
+  }
+};
+
+}  // namespace
+
+struct dmr_ctx {
+  Base* e;
+};
+
+extern "C" {
+
+size_t dmr_workspace_bytes(const dmr_config* cfg) {
+  Derived d;
+  Layout L;
+  std::string err;
+  if (derive(cfg, &d, &err) || make_layout(cfg, d, &L, &err)) {
+    g_err = err;
+    return 0;
+  }
+  return L.total;
+}
+
+int dmr_create(const dmr_config* cfg, void* ws, size_t bytes, void* stream, dmr_ctx** out) {
+  if (!out) { g_err = "null output pointer"; return DMR_EINVAL; }
+  *out = nullptr;
+  Derived d;
+  Layout L;
+  std::string err;
+  if (int s = derive(cfg, &d, &err)) { g_err = err; return s; }
+  if (int s = make_layout(cfg, d, &L, &err)) { g_err = err; return s; }
+  if (!ws || ((uintptr_t)ws & 255u)) { g_err = "workspace must be a 256-byte aligned device pointer"; return DMR_EINVAL; }
+  if (bytes < L.total) { g_err = fmt("workspace too small: %zu < %zu bytes", bytes, L.total); return DMR_ECAPACITY; }
+  Base* e = cfg->precision == 1 ? (Base*)new (std::nothrow) Engine<float>()
+                                : (Base*)new (std::nothrow) Engine<double>();
+  if (!e) { g_err = "out of host memory"; return DMR_EINVAL; }
+  e->cfg = *cfg;
+  e->d = d;
+  e->L = L;
+  e->ws = (char*)ws;
+  e->st = (cudaStream_t)stream;
+  if (int s = e->init()) { g_err = e->err; delete e; return s; }
+  dmr_ctx* c = new (std::nothrow) dmr_ctx{e};
+  if (!c) { delete e; g_err = "out of host memory"; return DMR_EINVAL; }
+  *out = c;
+  return DMR_OK;
+}
+
+void dmr_destroy(dmr_ctx* ctx) {
+  if (!ctx) return;
+  delete ctx->e;
+  delete ctx;
+}
+
+const char* dmr_last_error(const dmr_ctx* ctx) {
+  if (!ctx) return g_err.c_str();
+  return ctx->e->err.c_str();
+}
+
+#define CTX_OR_FAIL(c)               \
+  if (!(c)) {                        \
+    g_err = "null context";          \
+    return DMR_EINVAL;               \
+  }
+
+int dmr_seed_gaussian(dmr_ctx* ctx, double n0, double x0, double y0, double sx, double sy, int add) {
+  CTX_OR_FAIL(ctx);
+  return ctx->e->seed(n0, x0, y0, sx, sy, add);
+}
+
+int dmr_set_patch(dmr_ctx* ctx, const int32_t rect[4]) {
+  CTX_OR_FAIL(ctx);
+  if (!rect) return ctx->e->fail(DMR_EINVAL, "null rectangle");
+  return ctx->e->set_patch(rect);
+}
+
+int dmr_get_patch(const dmr_ctx* ctx, int32_t rect[4]) {
+  CTX_OR_FAIL(ctx);
+  for (int q = 0; q < 4; ++q) rect[q] = ctx->e->has_fine ? ctx->e->rect[q] : -1;
+  return DMR_OK;
+}
+
+int dmr_advance(dmr_ctx* ctx, int64_t n) {
+  CTX_OR_FAIL(ctx);
+  return ctx->e->advance(n);
+}
+
+int dmr_replay_log(dmr_ctx* ctx, const int32_t* rects, int64_t n_periods) {
+  CTX_OR_FAIL(ctx);
+  if (n_periods < 0 || (n_periods > 0 && !rects)) return ctx->e->fail(DMR_EINVAL, "bad replay log");
+  ctx->e->replay.assign(rects, rects + 4 * n_periods);
+  ctx->e->replay_pos = 0;
+  return DMR_OK;
+}
+
+int dmr_field_shape(const dmr_ctx* ctx, int field, int level, int32_t shape[2], int32_t* eb) {
+  CTX_OR_FAIL(ctx);
+  return ctx->e->shape(field, level, shape, eb);
+}
+
+int dmr_read(const dmr_ctx* ctx, int field, int level, void* dst, size_t bytes, int dev) {
+  CTX_OR_FAIL(ctx);
+  if (!dst) return ctx->e->fail(DMR_EINVAL, "null destination");
+  return ctx->e->read(field, level, dst, bytes, dev);
+}
+
+int dmr_write(dmr_ctx* ctx, int field, int level, const void* src, size_t bytes, int dev) {
+  CTX_OR_FAIL(ctx);
+  if (!src) return ctx->e->fail(DMR_EINVAL, "null source");
+  return ctx->e->write(field, level, src, bytes, dev);
+}
+
+int dmr_stats(const dmr_ctx* ctx, double out[DMR_NSTATS]) {
+  CTX_OR_FAIL(ctx);
+  return ctx->e->stats(out);
+}
+
+int dmr_set_graphs(dmr_ctx* ctx, int enable) {
+  CTX_OR_FAIL(ctx);
+  ctx->e->graphs = enable != 0;
+  if (!enable) ctx->e->drop_graph();
+  return DMR_OK;
+}
+
+int dmr_set_timing(dmr_ctx* ctx, int enable) {
+  CTX_OR_FAIL(ctx);
+  ctx->e->timing = enable != 0;
+  ctx->e->timing_mask = (unsigned)enable;
+  ctx->e->drop_graph();
+  ctx->e->pend.clear();
+  ctx->e->evd_used = 0;
+  for (int q = 0; q < 8; ++q) { ctx->e->kt_ms[q] = 0; ctx->e->kt_n[q] = 0; ctx->e->kt_units[q] = 0; }
+  return DMR_OK;
+}
+
+int dmr_kernel_time(const dmr_ctx* ctx, int kclass, double* ms, int64_t* n, double* units) {
+  CTX_OR_FAIL(ctx);
+  if (kclass < 0 || kclass >= 8) return DMR_EINVAL;
+  if (ms) *ms = ctx->e->kt_ms[kclass];
+  if (n) *n = ctx->e->kt_n[kclass];
+  if (units) *units = ctx->e->kt_units[kclass];
+  return DMR_OK;
+}
+
+const char* dmr_kernel_class_name(int kclass) {
+  static const char* names[] = {"coarse_h", "coarse_e", "fine_h", "fine_e",
+                                "restrict", "period_end", "expand"};
+  if (kclass < 0 || kclass >= 7) return nullptr;
+  return names[kclass];
+}
+
+int dmr_launch_count(const dmr_ctx* ctx, int64_t* n) {
+  CTX_OR_FAIL(ctx);
+  *n = ctx->e->launches;
+  return DMR_OK;
+}
+
+int dmr_sync(const dmr_ctx* ctx) {
+  CTX_OR_FAIL(ctx);
+  return ctx->e->ck(cudaStreamSynchronize(ctx->e->st), "sync");
+}
+
+}  // extern "C"

@@ -1,0 +1,563 @@
+// dmr_kernels.cuh -- sm_103a kernels of the DMR EM-plasma time step.
+//
+// Layout in HBM: every mesh array is row-major with y as the row index and a
+// row pitch p (elements, a multiple of 64) shared by all arrays of the mesh:
+//   Ex, vx [j*p + i], i < nx, j <= ny      Ey, vy [j*p + i], i <= nx, j < ny
+//   Hz     [j*p + i], i < nx, j < ny       n, S2  [j*p + i], i <= nx, j <= ny
+// Threads map x to threadIdx.x so each warp reads 32 consecutive elements.
+//
+// The stencils are HBM-bound (~0.7 flop/byte): no tensor cores.  Arithmetic
+// is compiled without FMA contraction so that the FP64 path repeats the
+// rounding of a plain unfused evaluation.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dmr {
+
+enum { SIDE_LEFT = 0, SIDE_RIGHT = 1, SIDE_BOTTOM = 2, SIDE_TOP = 3 };
+enum { BC_MUR = 0, BC_CFB = 1 };
+
+template <class T>
+struct Mesh {
+  T *Ex, *Ey, *Hz, *vx, *vy, *n;
+  double* S2;
+  int nx, ny;  // cells
+  int p;       // row pitch (elements)
+};
+
+// Coefficients of one EM step on one mesh (Eqs. 1-3).
+template <class T>
+struct Step {
+  T ch;        // dt / (mu0 dx)                 Faraday (Eq. 2)
+  T ce;        // dt / (eps0 dx)                Ampere  (Eq. 1)
+  T cj;        // dt e / (2 eps0): -J dt/eps0 = cj (n_a + n_b) v
+  T va, vb;    // Crank-Nicolson momentum (Eq. 3): v' = va v - vb E
+  T mur;       // (c dt - dx) / (c dt + dx)     first-order Mur
+  T E0, sphi, cphi;      // incident amplitude and sin/cos of w t at this E level
+  const T *ckx, *skx;    // cos(k x_i), sin(k x_i) of this mesh's node columns
+  int accum;             // add |E_total|^2 of this level to S2
+};
+
+// Coarse-fine boundary (Eq. 5b) for the fine mesh, and the coarse lines it
+// reads.  For the coarse mesh, `save` receives the pre-update tangential E
+// of the rectangle's interior sides.
+template <class T>
+struct Bnd {
+  int mode[4];              // BC_MUR or BC_CFB per side
+  const T* old_line[4];     // coarse tangential E before the coarse step
+  const T* new_line[4];     // coarse tangential E after it (strided)
+  int new_stride[4];
+  int len[4];               // coarse samples along the line
+  int start[4];             // coarse index of the rectangle corner along the line
+  int r;
+  T frac;                   // k / r of the fine sub-step
+  T* save[4];               // coarse only: where to keep the old line (or null)
+  int save_at[4];           // coarse row / column of that line
+};
+
+template <class T>
+__device__ __forceinline__ T incident(const Step<T>& c, int i) {
+  return c.E0 * (c.sphi * c.ckx[i] - c.cphi * c.skx[i]);
+}
+
+// Squared total field at node (i, j): mean of the existing Ex^2 edges along x
+// plus mean of the existing Ey^2 edges along y (incident added to Ey).
+template <class T>
+__device__ __forceinline__ T node_e2(const Mesh<T>& m, const Step<T>& c, int i, int j) {
+  const int p = m.p;
+  T sx, sy;
+  if (i > 0 && i < m.nx) {
+    T a = m.Ex[j * p + i - 1], b = m.Ex[j * p + i];
+    sx = T(0.5) * (a * a + b * b);
+  } else if (i > 0) {
+    T a = m.Ex[j * p + i - 1];
+    sx = a * a;
+  } else {
+    T b = m.Ex[j * p + i];
+    sx = b * b;
+  }
+  T inc = incident(c, i);
+  if (j > 0 && j < m.ny) {
+    T e = m.Ey[(j - 1) * p + i] + inc, f = m.Ey[j * p + i] + inc;
+    sy = T(0.5) * (e * e + f * f);
+  } else if (j > 0) {
+    T e = m.Ey[(j - 1) * p + i] + inc;
+    sy = e * e;
+  } else {
+    T f = m.Ey[j * p + i] + inc;
+    sy = f * f;
+  }
+  return sx + sy;
+}
+
+// Eq. 5b for tangential sample q of side sd of the fine rectangle.
+template <class T>
+__device__ __forceinline__ T cfb_value(const Bnd<T>& b, int sd, int q) {
+  double pos = ((double)b.start[sd] + ((double)q + 0.5) / (double)b.r) - 0.5;
+  int i0 = (int)floor(pos);
+  double w = pos - (double)i0;
+  if (i0 < 0) { i0 = 0; w = 0.0; }
+  if (i0 > b.len[sd] - 2) { i0 = b.len[sd] - 2; w = 1.0; }
+  const T xp = (T)w, one = T(1);
+  const T* o = b.old_line[sd];
+  const T* nw = b.new_line[sd];
+  const int s = b.new_stride[sd];
+  T lo = o[i0] * (one - xp) + o[i0 + 1] * xp;
+  T ln = nw[i0 * s] * (one - xp) + nw[(i0 + 1) * s] * xp;
+  return (one - b.frac) * lo + b.frac * ln;
+}
+
+// a1 (Eq. 2) + a5 for the level being left: Hz^{n+1/2} from E^n, and S2 += |E^n|^2
+// at the nodes when c.accum.  Grid covers the (nx+1) x (ny+1) nodes.
+template <class T>
+__global__ void k_h(Mesh<T> m, Step<T> c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > m.nx || j > m.ny) return;
+  const int p = m.p;
+  if (c.accum) m.S2[j * p + i] += (double)node_e2(m, c, i, j);
+  if (i < m.nx && j < m.ny) {
+    const int id = j * p + i;
+    T ey0 = m.Ey[id], ey1 = m.Ey[id + 1];
+    T ex0 = m.Ex[id], ex1 = m.Ex[id + p];
+    m.Hz[id] = m.Hz[id] - c.ch * ((ey1 - ey0) - (ex1 - ex0));
+  }
+}
+
+// a2 + a3 + a4 (+ a6 on the fine mesh): v^{n+1/2} (Eq. 3), E^{n+1} on interior
+// edges (Eq. 1), Mur on domain sides, Eq. 5b on coarse-fine sides.
+// A Mur side's boundary edge (v and E) is advanced by the thread owning the
+// adjacent interior edge, which holds both E levels that Mur needs.
+template <class T>
+__global__ void k_e(Mesh<T> m, Step<T> c, Bnd<T> b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > m.nx || j > m.ny) return;
+  const int p = m.p;
+  const int nx = m.nx, ny = m.ny;
+  // ---- x edges (i < nx, j <= ny)
+  if (i < nx) {
+    const int id = j * p + i;
+    if (j > 0 && j < ny) {
+      T ex = m.Ex[id];
+      T v = c.va * m.vx[id] - c.vb * ex;
+      m.vx[id] = v;
+      if (b.save[SIDE_BOTTOM] && j == b.save_at[SIDE_BOTTOM]) b.save[SIDE_BOTTOM][i] = ex;
+      if (b.save[SIDE_TOP] && j == b.save_at[SIDE_TOP]) b.save[SIDE_TOP][i] = ex;
+      T en = ex + c.ce * (m.Hz[id] - m.Hz[id - p]) + c.cj * (m.n[id] + m.n[id + 1]) * v;
+      m.Ex[id] = en;
+      if (j == 1 && b.mode[SIDE_BOTTOM] == BC_MUR) {
+        const int ib = i;
+        T eb = m.Ex[ib];
+        m.vx[ib] = c.va * m.vx[ib] - c.vb * eb;
+        m.Ex[ib] = ex + c.mur * (en - eb);
+      }
+      if (j == ny - 1 && b.mode[SIDE_TOP] == BC_MUR) {
+        const int ib = ny * p + i;
+        T eb = m.Ex[ib];
+        m.vx[ib] = c.va * m.vx[ib] - c.vb * eb;
+        m.Ex[ib] = ex + c.mur * (en - eb);
+      }
+    } else {
+      const int sd = (j == 0) ? SIDE_BOTTOM : SIDE_TOP;
+      if (b.mode[sd] == BC_CFB) {
+        m.vx[id] = c.va * m.vx[id] - c.vb * m.Ex[id];
+        m.Ex[id] = cfb_value(b, sd, i);
+      }
+    }
+  }
+  // ---- y edges (i <= nx, j < ny)
+  if (j < ny) {
+    const int id = j * p + i;
+    const T inc = incident(c, i);
+    if (i > 0 && i < nx) {
+      T ey = m.Ey[id];
+      T v = c.va * m.vy[id] - c.vb * (ey + inc);
+      m.vy[id] = v;
+      if (b.save[SIDE_LEFT] && i == b.save_at[SIDE_LEFT]) b.save[SIDE_LEFT][j] = ey;
+      if (b.save[SIDE_RIGHT] && i == b.save_at[SIDE_RIGHT]) b.save[SIDE_RIGHT][j] = ey;
+      T en = ey - c.ce * (m.Hz[id] - m.Hz[id - 1]) + c.cj * (m.n[id] + m.n[id + p]) * v;
+      m.Ey[id] = en;
+      if (i == 1 && b.mode[SIDE_LEFT] == BC_MUR) {
+        const int ib = j * p;
+        T eb = m.Ey[ib];
+        m.vy[ib] = c.va * m.vy[ib] - c.vb * (eb + incident(c, 0));
+        m.Ey[ib] = ey + c.mur * (en - eb);
+      }
+      if (i == nx - 1 && b.mode[SIDE_RIGHT] == BC_MUR) {
+        const int ib = j * p + nx;
+        T eb = m.Ey[ib];
+        m.vy[ib] = c.va * m.vy[ib] - c.vb * (eb + incident(c, nx));
+        m.Ey[ib] = ey + c.mur * (en - eb);
+      }
+    } else {
+      const int sd = (i == 0) ? SIDE_LEFT : SIDE_RIGHT;
+      if (b.mode[sd] == BC_CFB) {
+        m.vy[id] = c.va * m.vy[id] - c.vb * (m.Ey[id] + inc);
+        m.Ey[id] = cfb_value(b, sd, j);
+      }
+    }
+  }
+}
+
+// a8: coarse E edges of the closed rectangle (except tangential edges of
+// interior sides) = mean of the r collinear fine edges.  Grid over the
+// rectangle's coarse nodes.
+template <class T>
+__global__ void k_restrict(Mesh<T> c, Mesh<T> f, int I0, int J0, int I1, int J1, int r,
+                           int jlo, int jhi, int ilo, int ihi) {
+  const int i = I0 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = J0 + blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > I1 || j > J1) return;
+  const int fa = r * (i - I0), fb = r * (j - J0);
+  if (i < I1 && j >= jlo && j <= jhi) {
+    const T* s = f.Ex + (size_t)fb * f.p + fa;
+    T acc = s[0];
+    for (int q = 1; q < r; ++q) acc = acc + s[q];
+    c.Ex[j * c.p + i] = acc / (T)r;
+  }
+  if (j < J1 && i >= ilo && i <= ihi) {
+    const T* s = f.Ey + (size_t)fb * f.p + fa;
+    T acc = s[0];
+    for (int q = 1; q < r; ++q) acc = acc + s[(size_t)q * f.p];
+    c.Ey[j * c.p + i] = acc / (T)r;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Period end: E_eff, rates, continuity step, totals, flags (a9-a11, a13)
+// ----------------------------------------------------------------------------
+struct Dens {
+  double N;          // EM samples per period on this mesh
+  double g;          // 1 + (w/nu_m)^2
+  double hp;         // 100 p: E_eff/p in V/(cm Torr)
+  double A;          // s_nu 5.14e11 p
+  double nu_m, nu_a, De, Da;
+  double wp2c;       // e^2/(m eps0)
+  double heat;       // e^2/(m nu_m): period-mean J.E = n heat E_eff^2
+  double T;          // period
+  double dx2;        // dx^2
+  double r_ei;
+};
+
+// composite trapezoid weight of node (i, j): coarse mesh outside the
+// rectangle, fine mesh inside it
+struct Wts {
+  int nx, ny;               // cells of this mesh
+  int has_rect;             // coarse mesh with a fine rectangle
+  int I0, J0, I1, J1;
+};
+
+__device__ __forceinline__ double trap_w(const Wts& w, int i, int j) {
+  double wx = (i == 0 || i == w.nx) ? 0.5 : 1.0;
+  double wy = (j == 0 || j == w.ny) ? 0.5 : 1.0;
+  double v = wx * wy;
+  if (w.has_rect) {
+    double px = (i < w.I0 || i > w.I1) ? 0.0 : ((i == w.I0 || i == w.I1) ? 0.5 : 1.0);
+    double py = (j < w.J0 || j > w.J1) ? 0.0 : ((j == w.J0 || j == w.J1) ? 0.5 : 1.0);
+    v = v - px * py;
+  }
+  return v;
+}
+
+// deterministic block sum of a double (blockDim.x*blockDim.y threads, <= 1024)
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[32];
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nt = blockDim.x * blockDim.y;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((t & 31) == 0) sh[t >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (t < 32) {
+    s = (t < (nt + 31) / 32) ? sh[t] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  __syncthreads();
+  return s;  // valid in thread 0
+}
+
+struct Ctl {           // device control block
+  double st[8];        // 0 N_e, 1 P_abs, 2 W_abs, 3 periods, 4 n_max
+  int bbox[4];         // imin, jmin, imax, jmax of the flags
+  int nflag;
+  int err;
+};
+
+// a9 first pass: finish the period's S2 with the last level, E_eff, nu_net,
+// D_eff; period-mean absorbed power partial; reset S2.
+template <class T>
+__global__ void k_rates(Mesh<T> m, Step<T> c, Dens d, Wts w, T* D, T* nu, double* partP,
+                        Ctl* ctl) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (ctl && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+    ctl->bbox[0] = 0x7fffffff; ctl->bbox[1] = 0x7fffffff;
+    ctl->bbox[2] = -1; ctl->bbox[3] = -1;
+    ctl->nflag = 0; ctl->st[4] = 0.0;
+  }
+  double contrib = 0.0;
+  if (i <= m.nx && j <= m.ny) {
+    const int id = j * m.p + i;
+    double s2 = m.S2[id] + (double)node_e2(m, c, i, j);
+    double erms2 = s2 / d.N;
+    double eeff = sqrt(erms2 / d.g);
+    T x = (T)(eeff / d.hp);
+    T nui = (x > T(0)) ? (T)d.A * exp(T(-73.0) * pow(x, T(-0.44))) : T(0);
+    T n = m.n[id];
+    T wp2 = n * (T)d.wp2c;
+    T num = nui * (T)d.nu_m * (T)d.De + wp2 * (T)d.Da;
+    T den = nui * (T)d.nu_m + wp2;
+    D[id] = (den == T(0)) ? (T)d.De : num / den;
+    nu[id] = nui - (T)d.nu_a;
+    contrib = trap_w(w, i, j) * (double)n * d.heat * eeff * eeff;
+    m.S2[id] = 0.0;
+  }
+  double s = block_sum(contrib);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partP[blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+// Dirichlet (coarse-fine) sides of the fine density step: new coarse density
+// interpolated along the side (Eq. 5b, frac = 1).
+template <class T>
+struct Dir {
+  int on[4];            // side is a coarse-fine boundary
+  const T* line[4];     // new coarse density along the side (strided)
+  int stride[4];
+  int len[4];
+  int start[4];
+  int r;
+};
+
+template <class T>
+__device__ __forceinline__ T dir_value(const Dir<T>& d, int sd, int q) {
+  double pos = (double)d.start[sd] + (double)q / (double)d.r;
+  int i0 = (int)floor(pos);
+  double w = pos - (double)i0;
+  if (i0 < 0) { i0 = 0; w = 0.0; }
+  if (i0 > d.len[sd] - 2) { i0 = d.len[sd] - 2; w = 1.0; }
+  const T xp = (T)w;
+  const T* l = d.line[sd];
+  const int s = d.stride[sd];
+  return l[i0 * s] * (T(1) - xp) + l[(i0 + 1) * s] * xp;
+}
+
+// a9 second pass (+ a10 on the fine mesh): forward-Euler continuity step over
+// one period with face-mean D_eff, zero flux through the domain edges.
+template <class T>
+__global__ void k_density(Mesh<T> m, const T* D, const T* nu, T* nout, Dens d, Dir<T> dir) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > m.nx || j > m.ny) return;
+  const int p = m.p;
+  const int id = j * p + i;
+  if (dir.on[SIDE_BOTTOM] && j == 0) { nout[id] = dir_value(dir, SIDE_BOTTOM, i); return; }
+  if (dir.on[SIDE_TOP] && j == m.ny) { nout[id] = dir_value(dir, SIDE_TOP, i); return; }
+  if (dir.on[SIDE_LEFT] && i == 0) { nout[id] = dir_value(dir, SIDE_LEFT, j); return; }
+  if (dir.on[SIDE_RIGHT] && i == m.nx) { nout[id] = dir_value(dir, SIDE_RIGHT, j); return; }
+  const T n = m.n[id];
+  const T Di = D[id];
+  T lap = T(0);
+  if (i < m.nx) lap = lap + T(0.5) * (Di + D[id + 1]) * (m.n[id + 1] - n);
+  if (i > 0) lap = lap + T(0.5) * (Di + D[id - 1]) * (m.n[id - 1] - n);
+  if (j < m.ny) lap = lap + T(0.5) * (Di + D[id + p]) * (m.n[id + p] - n);
+  if (j > 0) lap = lap + T(0.5) * (Di + D[id - p]) * (m.n[id - p] - n);
+  const T rate = lap / (T)d.dx2 + nu[id] * n - (T)d.r_ei * n * n;
+  nout[id] = n + (T)d.T * rate;
+}
+
+// commit the new density: coarse nodes of the closed rectangle take the fine
+// value (direct copy, Sec. III.C); electron-total partial.
+template <class T>
+__global__ void k_commit(Mesh<T> m, const T* nnew, Wts w, const T* fine_n, int fine_p, int r,
+                         double* partN) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  double contrib = 0.0;
+  if (i <= m.nx && j <= m.ny) {
+    const int id = j * m.p + i;
+    T v = nnew[id];
+    if (fine_n && i >= w.I0 && i <= w.I1 && j >= w.J0 && j <= w.J1)
+      v = fine_n[(size_t)(r * (j - w.J0)) * fine_p + r * (i - w.I0)];
+    m.n[id] = v;
+    contrib = trap_w(w, i, j) * (double)v;
+  }
+  double s = block_sum(contrib);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partN[blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+// a11: flags on the coarse nodes (threshold OR central gradient, the latter
+// as (dn_x s)^2 + (dn_y s)^2 > 1 with s = 1/(2 dx g_th)); uint8 mask, flag
+// bounding box and count, largest density.
+template <class T>
+__global__ void k_flags(Mesh<T> m, T n_th, T gs, uint8_t* mask, Ctl* ctl) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > m.nx || j > m.ny) return;
+  const int p = m.p;
+  const T n = m.n[j * p + i];
+  bool f = n > n_th;
+  if (i > 0 && i < m.nx && j > 0 && j < m.ny) {
+    T gx = (m.n[j * p + i + 1] - m.n[j * p + i - 1]) * gs;
+    T gy = (m.n[(j + 1) * p + i] - m.n[(j - 1) * p + i]) * gs;
+    f = f || (gx * gx + gy * gy > T(1));
+  }
+  mask[(size_t)j * (m.nx + 1) + i] = f ? 1 : 0;
+  // largest density (non-negative doubles order like their bit patterns)
+  const double dn = (double)n;
+  if (dn != dn) {
+    atomicOr(&ctl->err, 1);
+  } else if (dn > 0.0) {
+    atomicMax((unsigned long long*)&ctl->st[4], (unsigned long long)__double_as_longlong(dn));
+  }
+  if (f) {
+    atomicMin(&ctl->bbox[0], i);
+    atomicMin(&ctl->bbox[1], j);
+    atomicMax(&ctl->bbox[2], i);
+    atomicMax(&ctl->bbox[3], j);
+    atomicAdd(&ctl->nflag, 1);
+  }
+}
+
+// sum the partials in a fixed order (deterministic), update the totals.
+__global__ void k_finalize(const double* pPc, int nPc, const double* pPf, int nPf,
+                           const double* pNc, int nNc, const double* pNf, int nNf,
+                           double dxc2, double dxf2, double T, Ctl* ctl) {
+  __shared__ double sh[4][32];
+  const int t = threadIdx.x;  // 1024 threads
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int q = t; q < nPc; q += blockDim.x) a[0] += pPc[q];
+  for (int q = t; q < nPf; q += blockDim.x) a[1] += pPf[q];
+  for (int q = t; q < nNc; q += blockDim.x) a[2] += pNc[q];
+  for (int q = t; q < nNf; q += blockDim.x) a[3] += pNf[q];
+  for (int k = 0; k < 4; ++k) {
+    double v = a[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((t & 31) == 0) sh[k][t >> 5] = v;
+  }
+  __syncthreads();
+  if (t < 32) {
+    for (int k = 0; k < 4; ++k) {
+      double v = sh[k][t];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (t == 0) a[k] = v;
+    }
+    if (t == 0) {
+      double P = dxc2 * a[0] + dxf2 * a[1];
+      double N = dxc2 * a[2] + dxf2 * a[3];
+      ctl->st[0] = N;
+      ctl->st[1] = P;
+      ctl->st[2] = ctl->st[2] + P * T;
+      ctl->st[3] = ctl->st[3] + 1.0;
+      if (!(N == N) || !(P == P)) ctl->err |= 1;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Growth (a12) and set-up
+// ----------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T bilin(const T* F, int p, int Lx, int Ly, double u, double v) {
+  int i0 = (int)floor(u);
+  double fu = u - (double)i0;
+  if (i0 < 0) { i0 = 0; fu = 0.0; }
+  if (i0 > Lx - 2) { i0 = Lx - 2; fu = 1.0; }
+  int j0 = (int)floor(v);
+  double fv = v - (double)j0;
+  if (j0 < 0) { j0 = 0; fv = 0.0; }
+  if (j0 > Ly - 2) { j0 = Ly - 2; fv = 1.0; }
+  const T a = (T)((1.0 - fu) * (1.0 - fv)), b = (T)(fu * (1.0 - fv));
+  const T cc = (T)((1.0 - fu) * fv), dd = (T)(fu * fv);
+  const T* r0 = F + (size_t)j0 * p;
+  const T* r1 = r0 + p;
+  return r0[i0] * a + r0[i0 + 1] * b + r1[i0] * cc + r1[i0 + 1] * dd;
+}
+
+// New fine arrays of rectangle (I0, J0) with (nf.nx, nf.ny) cells: values of
+// the old rectangle are copied, the rest bilinear from coarse (Eq. 5a).
+template <class T>
+__global__ void k_expand(Mesh<T> nf, Mesh<T> of, Mesh<T> c, int I0, int J0, int oI0, int oJ0,
+                         int has_old, int r) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y * blockDim.y + threadIdx.y;
+  if (a > nf.nx || b > nf.ny) return;
+  const int sa = a - r * (oI0 - I0), sb = b - r * (oJ0 - J0);
+  const int id = b * nf.p + a;
+  const double rr = (double)r;
+  const double xn = (double)I0 + (double)a / rr, yn = (double)J0 + (double)b / rr;
+  const double xh = ((double)I0 + ((double)a + 0.5) / rr) - 0.5;
+  const double yh = ((double)J0 + ((double)b + 0.5) / rr) - 0.5;
+  const bool in_x = has_old && sa >= 0 && sa < of.nx;
+  const bool in_xn = has_old && sa >= 0 && sa <= of.nx;
+  const bool in_y = has_old && sb >= 0 && sb < of.ny;
+  const bool in_yn = has_old && sb >= 0 && sb <= of.ny;
+  const int oid = sb * of.p + sa;
+  if (a < nf.nx) {  // Ex, vx at (i+1/2, j)
+    if (in_x && in_yn) {
+      nf.Ex[id] = of.Ex[oid];
+      nf.vx[id] = of.vx[oid];
+    } else {
+      nf.Ex[id] = bilin(c.Ex, c.p, c.nx, c.ny + 1, xh, yn);
+      nf.vx[id] = bilin(c.vx, c.p, c.nx, c.ny + 1, xh, yn);
+    }
+  }
+  if (b < nf.ny) {  // Ey, vy at (i, j+1/2)
+    if (in_xn && in_y) {
+      nf.Ey[id] = of.Ey[oid];
+      nf.vy[id] = of.vy[oid];
+    } else {
+      nf.Ey[id] = bilin(c.Ey, c.p, c.nx + 1, c.ny, xn, yh);
+      nf.vy[id] = bilin(c.vy, c.p, c.nx + 1, c.ny, xn, yh);
+    }
+  }
+  if (a < nf.nx && b < nf.ny) {
+    nf.Hz[id] = (in_x && in_y) ? of.Hz[oid] : bilin(c.Hz, c.p, c.nx, c.ny, xh, yh);
+  }
+  nf.n[id] = (in_xn && in_yn) ? of.n[oid] : bilin(c.n, c.p, c.nx + 1, c.ny + 1, xn, yn);
+  nf.S2[id] = 0.0;
+}
+
+template <class T>
+__global__ void k_seed(Mesh<T> m, int gi0, int gj0, double dx, double n0, double x0, double y0,
+                       double sx, double sy, int add) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > m.nx || j > m.ny) return;
+  const double x = (double)(gi0 + i) * dx, y = (double)(gj0 + j) * dx;
+  const double ux = x - x0, uy = y - y0;
+  const double arg = ux * ux / (sx * sx) + uy * uy / (sy * sy);
+  const double g = (arg <= 60.0) ? n0 * exp(-fmin(arg, 60.0)) : 0.0;
+  const int id = j * m.p + i;
+  m.n[id] = add ? (T)((double)m.n[id] + g) : (T)g;
+}
+
+// direct copy of the fine density into the coinciding coarse nodes
+template <class T>
+__global__ void k_inject(Mesh<T> c, Mesh<T> f, int I0, int J0, int I1, int J1, int r) {
+  const int i = I0 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = J0 + blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > I1 || j > J1) return;
+  c.n[j * c.p + i] = f.n[(size_t)(r * (j - J0)) * f.p + r * (i - I0)];
+}
+
+// running S2 through the present E level (S2 holds the levels before it)
+template <class T>
+__global__ void k_s2_view(Mesh<T> m, Step<T> c, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > m.nx || j > m.ny) return;
+  out[j * m.p + i] = m.S2[j * m.p + i] + (double)node_e2(m, c, i, j);
+}
+
+// strided 2-D copy between a dense buffer and a pitched array (device side)
+template <class E>
+__global__ void k_copy2d(E* dst, int dp, const E* src, int sp, int cols, int rows) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= cols || j >= rows) return;
+  dst[(size_t)j * dp + i] = src[(size_t)j * sp + i];
+}
+
+}  // namespace dmr

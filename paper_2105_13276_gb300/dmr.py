@@ -1,0 +1,298 @@
+"""Thin ctypes binding of ``libdmr.so`` (the C ABI in include/dmr.h).
+
+Argument marshalling only: every step of the time stepping runs in the CUDA
+kernels of the library.  PyTorch provides the device workspace and the
+stream.  If the library is missing this module raises; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_int32, c_int64, c_size_t, c_void_p
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libdmr.so")
+
+# status codes
+OK, EINVAL, ECAPACITY, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "DMR_OK", -1: "DMR_EINVAL", -2: "DMR_ECAPACITY", -3: "DMR_ECUDA",
+                -4: "DMR_EUNSTABLE", -5: "DMR_ETIMEOUT", -6: "DMR_ESTATE"}
+
+FIELDS = {"Ex": 0, "Ey": 1, "Hz": 2, "vx": 3, "vy": 4, "n": 5, "S2": 6, "mask": 7}
+STATS = ["t", "R", "fine_cells", "N_e", "P_abs", "W_abs", "periods", "coarse_steps", "n_max",
+         "flags"]
+
+C0 = 299792458.0
+
+
+class DmrConfig(ctypes.Structure):
+    _fields_ = [("nx", c_int32), ("ny", c_int32), ("r", c_int32), ("n_lambda", c_int32),
+                ("steps_per_period", c_int32), ("precision", c_int32),
+                ("buffer_cells", c_int32), ("growth", c_int32), ("patch_cap_cells", c_int64),
+                ("freq", c_double), ("E0", c_double), ("p_torr", c_double),
+                ("De", c_double), ("Da", c_double), ("beta_rec", c_double), ("Te", c_double),
+                ("nu_scale", c_double), ("nu_a", c_double), ("n_th", c_double),
+                ("g_th", c_double)]
+
+
+class DMRError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, code), msg))
+        self.code = code
+
+
+_LIB = None
+
+
+def load():
+    """Load libdmr.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libdmr.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P = c_void_p
+    sig = {
+        "dmr_workspace_bytes": (c_size_t, [POINTER(DmrConfig)]),
+        "dmr_create": (c_int, [POINTER(DmrConfig), P, c_size_t, P, POINTER(P)]),
+        "dmr_destroy": (None, [P]),
+        "dmr_last_error": (c_char_p, [P]),
+        "dmr_seed_gaussian": (c_int, [P, c_double, c_double, c_double, c_double, c_double, c_int]),
+        "dmr_set_patch": (c_int, [P, POINTER(c_int32)]),
+        "dmr_get_patch": (c_int, [P, POINTER(c_int32)]),
+        "dmr_advance": (c_int, [P, c_int64]),
+        "dmr_replay_log": (c_int, [P, POINTER(c_int32), c_int64]),
+        "dmr_field_shape": (c_int, [P, c_int, c_int, POINTER(c_int32), POINTER(c_int32)]),
+        "dmr_read": (c_int, [P, c_int, c_int, P, c_size_t, c_int]),
+        "dmr_write": (c_int, [P, c_int, c_int, P, c_size_t, c_int]),
+        "dmr_stats": (c_int, [P, POINTER(c_double)]),
+        "dmr_set_graphs": (c_int, [P, c_int]),
+        "dmr_set_timing": (c_int, [P, c_int]),
+        "dmr_kernel_time": (c_int, [P, c_int, POINTER(c_double), POINTER(c_int64),
+                                    POINTER(c_double)]),
+        "dmr_kernel_class_name": (c_char_p, [c_int]),
+        "dmr_launch_count": (c_int, [P, POINTER(c_int64)]),
+        "dmr_sync": (c_int, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def make_config(cfg: dict) -> DmrConfig:
+    """dmr_config from a plain parameter dict (None selects a default)."""
+    def d(key, default=-1.0):
+        v = cfg.get(key)
+        return float(default if v is None else v)
+    c = DmrConfig()
+    c.nx, c.ny = int(cfg["nx"]), int(cfg["ny"])
+    c.r = int(cfg.get("r") or 1)
+    c.n_lambda = int(cfg["n_lambda"])
+    c.steps_per_period = int(cfg["steps_per_period"])
+    c.precision = int(cfg.get("precision") or 0)
+    c.buffer_cells = int(4 if cfg.get("buffer_cells") is None else cfg["buffer_cells"])
+    c.growth = int(1 if cfg.get("growth") is None else bool(cfg["growth"]))
+    c.patch_cap_cells = int(-1 if cfg.get("patch_cap_cells") is None else cfg["patch_cap_cells"])
+    c.freq, c.E0, c.p_torr = float(cfg["freq"]), float(cfg["E0"]), float(cfg["p_torr"])
+    c.De, c.Da = d("De"), d("Da")
+    c.beta_rec, c.Te = d("beta_rec"), d("Te")
+    c.nu_scale = d("nu_scale")
+    c.nu_a = d("nu_a", 0.0)
+    c.n_th, c.g_th = d("n_th"), d("g_th")
+    return c
+
+
+def workspace_bytes(cfg: dict) -> int:
+    lib = load()
+    c = make_config(cfg)
+    n = lib.dmr_workspace_bytes(byref(c))
+    if n == 0:
+        raise DMRError(EINVAL, lib.dmr_last_error(None).decode())
+    return int(n)
+
+
+class Run:
+    """One DMR (or uniform, r = 1) run on a CUDA device."""
+
+    def __init__(self, cfg: dict, device=None, stream=None):
+        import torch
+        self.lib = lib = load()
+        self.cfg = dict(cfg)
+        self._c = make_config(cfg)
+        nbytes = lib.dmr_workspace_bytes(byref(self._c))
+        if nbytes == 0:
+            raise DMRError(EINVAL, lib.dmr_last_error(None).decode())
+        self.device = torch.device(device if device is not None else "cuda")
+        self.ws = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        # a dedicated stream: CUDA graphs cannot be captured on the legacy default stream
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        ctx = c_void_p()
+        st = lib.dmr_create(byref(self._c), c_void_p(self.ws.data_ptr()), c_size_t(nbytes),
+                            c_void_p(self.stream.cuda_stream), byref(ctx))
+        if st != OK:
+            raise DMRError(st, lib.dmr_last_error(None).decode())
+        self.ctx = ctx
+        self.fdtype = np.float32 if self._c.precision == 1 else np.float64
+        self.lam = C0 / self._c.freq
+        self.dxc = self.lam / self._c.n_lambda
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.dmr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != OK:
+            raise DMRError(st, self.lib.dmr_last_error(self.ctx).decode())
+
+    # -- set-up ---------------------------------------------------------------
+    def seed_gaussian(self, n0, x0, y0, sx, sy, add=False):
+        self._check(self.lib.dmr_seed_gaussian(self.ctx, n0, x0, y0, sx, sy, int(add)))
+
+    def seed_workload(self, seeds):
+        """Seeds given as (n0, x0/Lx, y0/Ly, sx/lambda, sy/lambda)."""
+        Lx, Ly = self._c.nx * self.dxc, self._c.ny * self.dxc
+        for q, (n0, fx, fy, sxl, syl) in enumerate(seeds):
+            self.seed_gaussian(n0, fx * Lx, fy * Ly, sxl * self.lam, syl * self.lam, add=q > 0)
+
+    def set_patch(self, rect):
+        arr = (c_int32 * 4)(*[int(v) for v in rect])
+        self._check(self.lib.dmr_set_patch(self.ctx, arr))
+
+    def get_patch(self):
+        arr = (c_int32 * 4)()
+        self._check(self.lib.dmr_get_patch(self.ctx, arr))
+        return tuple(arr)
+
+    def replay_log(self, rects):
+        flat = np.ascontiguousarray(np.asarray(rects, dtype=np.int32).reshape(-1))
+        n = flat.size // 4
+        ptr = flat.ctypes.data_as(POINTER(c_int32)) if n else None
+        self._replay_keep = flat
+        self._check(self.lib.dmr_replay_log(self.ctx, ptr, n))
+
+    # -- stepping ---------------------------------------------------------------
+    def advance(self, n_coarse_steps):
+        self._check(self.lib.dmr_advance(self.ctx, int(n_coarse_steps)))
+
+    def set_graphs(self, on=True):
+        self._check(self.lib.dmr_set_graphs(self.ctx, int(bool(on))))
+
+    def set_timing(self, on=True, classes=None):
+        """Time every kernel class (on=True), none (on=False) or the named
+        classes (``classes``: iterable of class names)."""
+        mask = -1 if on else 0
+        if on and classes is not None:
+            names = [self.lib.dmr_kernel_class_name(k) for k in range(32)]
+            names = [n.decode() for n in names if n]
+            mask = 0
+            for c in classes:
+                mask |= 1 << names.index(c)
+        self._check(self.lib.dmr_set_timing(self.ctx, mask))
+
+    def kernel_times(self):
+        out = {}
+        k = 0
+        while True:
+            name = self.lib.dmr_kernel_class_name(k)
+            if not name:
+                break
+            ms, n, u = c_double(), c_int64(), c_double()
+            self._check(self.lib.dmr_kernel_time(self.ctx, k, byref(ms), byref(n), byref(u)))
+            out[name.decode()] = (ms.value, n.value, u.value)
+            k += 1
+        return out
+
+    def launch_count(self):
+        n = c_int64()
+        self._check(self.lib.dmr_launch_count(self.ctx, byref(n)))
+        return n.value
+
+    def sync(self):
+        self._check(self.lib.dmr_sync(self.ctx))
+
+    # -- outputs ---------------------------------------------------------------
+    def shape(self, field, level=0):
+        s = (c_int32 * 2)()
+        eb = c_int32()
+        self._check(self.lib.dmr_field_shape(self.ctx, FIELDS[field], level, s, byref(eb)))
+        return (s[0], s[1]), eb.value
+
+    def _dtype(self, field):
+        if field == "S2":
+            return np.float64
+        if field == "mask":
+            return np.uint8
+        return self.fdtype
+
+    def read(self, field, level=0):
+        """Field as a numpy array of shape (rows, cols) = (y, x)."""
+        (rows, cols), eb = self.shape(field, level)
+        out = np.empty((rows, cols), dtype=self._dtype(field))
+        self._check(self.lib.dmr_read(self.ctx, FIELDS[field], level,
+                                      c_void_p(out.ctypes.data), out.nbytes, 0))
+        return out
+
+    def read_into(self, field, level, dst_tensor):
+        """Queue a device-to-device copy of a field into a torch tensor."""
+        self._check(self.lib.dmr_read(self.ctx, FIELDS[field], level,
+                                      c_void_p(dst_tensor.data_ptr()),
+                                      dst_tensor.numel() * dst_tensor.element_size(), 1))
+
+    def write(self, field, level, arr):
+        (rows, cols), eb = self.shape(field, level)
+        a = np.ascontiguousarray(np.asarray(arr, dtype=self._dtype(field)))
+        if a.shape != (rows, cols):
+            raise ValueError("expected shape %r, got %r" % ((rows, cols), a.shape))
+        self._check(self.lib.dmr_write(self.ctx, FIELDS[field], level,
+                                       c_void_p(a.ctypes.data), a.nbytes, 0))
+
+    def read_to_host(self, field, level, host_tensor):
+        """Copy a field into a (pinned) host torch tensor; returns after the copy."""
+        self._check(self.lib.dmr_read(self.ctx, FIELDS[field], level,
+                                      c_void_p(host_tensor.data_ptr()),
+                                      host_tensor.numel() * host_tensor.element_size(), 0))
+
+    def write_from_host(self, field, level, host_tensor):
+        """Overwrite a field from a (pinned) host torch tensor."""
+        self._check(self.lib.dmr_write(self.ctx, FIELDS[field], level,
+                                       c_void_p(host_tensor.data_ptr()),
+                                       host_tensor.numel() * host_tensor.element_size(), 0))
+
+    def write_from(self, field, level, src_tensor):
+        self._check(self.lib.dmr_write(self.ctx, FIELDS[field], level,
+                                       c_void_p(src_tensor.data_ptr()),
+                                       src_tensor.numel() * src_tensor.element_size(), 1))
+
+    def stats(self):
+        out = (c_double * len(STATS))()
+        self._check(self.lib.dmr_stats(self.ctx, out))
+        return dict(zip(STATS, list(out)))
+
+
+def run_from_workload(w, device=None, precision=None, cfg_overrides=None, rect=None):
+    """Create, patch and seed a run from a workload dict."""
+    cfg = dict(w["cfg"])
+    if precision is not None:
+        cfg["precision"] = precision
+    if cfg_overrides:
+        cfg.update(cfg_overrides)
+    run = Run(cfg, device=device)
+    rect = rect if rect is not None else w.get("rect")
+    if cfg.get("r", 1) > 1 and rect is not None:
+        run.set_patch(rect)
+    run.seed_workload(w["seeds"])
+    return run

@@ -1,0 +1,72 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/dmr.h; host-only calls (configuration checks) behave.  No kernel runs."""
+import os
+import re
+import shutil
+
+import pytest
+
+from paper_2105_13276_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "dmr.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(dmr_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2105_13276_gb300 import build as B
+    B.build()
+    from paper_2105_13276_gb300 import dmr as D
+    return D.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 18
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_config_validation_host_only(lib):
+    from paper_2105_13276_gb300 import dmr as D
+    assert D.workspace_bytes(W.dmr_512_r2()["cfg"]) > 0
+    assert D.workspace_bytes(W.uniform_256()["cfg"]) > 0
+    with pytest.raises(D.DMRError, match="Courant"):
+        D.workspace_bytes(W.base_cfg(n_lambda=32, steps_per_period=32))
+    with pytest.raises(D.DMRError, match="nx and ny"):
+        D.workspace_bytes(W.base_cfg(nx=2))
+    with pytest.raises(D.DMRError, match="precision"):
+        D.workspace_bytes(W.base_cfg(precision=3))
+    with pytest.raises(D.DMRError, match="diffusion number"):
+        D.workspace_bytes(W.base_cfg(De=1e4))
+
+
+def test_workspace_grows_with_capacity_and_precision(lib):
+    from paper_2105_13276_gb300 import dmr as D
+    c = W.dmr_512_r2()["cfg"]
+    small = D.workspace_bytes(dict(c, patch_cap_cells=64 * 64))
+    full = D.workspace_bytes(c)
+    f64 = D.workspace_bytes(dict(c, precision=0))
+    assert small < full < f64
+
+
+def test_create_rejects_bad_arguments_without_gpu(lib):
+    import ctypes
+    from paper_2105_13276_gb300 import dmr as D
+    c = D.make_config(W.small_dmr()["cfg"])
+    ctx = ctypes.c_void_p()
+    # misaligned workspace pointer is rejected before any CUDA call
+    st = lib.dmr_create(ctypes.byref(c), ctypes.c_void_p(8), 1 << 30, None, ctypes.byref(ctx))
+    assert st == D.EINVAL
+    assert b"aligned" in lib.dmr_last_error(None)
+    st = lib.dmr_create(ctypes.byref(c), ctypes.c_void_p(256), 16, None, ctypes.byref(ctx))
+    assert st == D.ECAPACITY
+    assert lib.dmr_kernel_class_name(0) == b"coarse_h"
+    assert lib.dmr_kernel_class_name(99) is None

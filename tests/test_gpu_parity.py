@@ -1,0 +1,220 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.
+
+Tolerances (the run's precision decides):
+  FP64 path : relative L2 <= 1e-12 per field, FP64 totals <= 1e-12, masks and
+              rectangle logs bit-exact;
+  FP32 path : relative L2 <= 1e-4 per field against the FP64 oracle on a
+              bounded horizon with the oracle's rectangle log replayed; the
+              FP32 mask equals the oracle's flag rule applied to the GPU's own
+              density in FP32 (same precision decides the integer).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from oracle import dmr_oracle as O  # noqa: E402
+from paper_2105_13276_gb300 import dmr as D  # noqa: E402
+from paper_2105_13276_gb300 import workloads as W  # noqa: E402
+
+FIELDS = ("Ex", "Ey", "Hz", "vx", "vy", "n")
+TOL64 = 1e-12
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2105_13276_gb300 import build as B
+    B.build()
+    D.load()
+
+
+def rel_l2(g, o):
+    no = np.linalg.norm(o)
+    if no == 0:
+        return float(np.linalg.norm(g))
+    return float(np.linalg.norm(g.astype(np.float64) - o) / no)
+
+
+def compare(run, sim, tol, fields=FIELDS, levels=(0, 1), s2=True):
+    worst = {}
+    for level in levels:
+        mesh = sim.coarse if level == 0 else sim.fine
+        if mesh is None:
+            continue
+        for name in fields + (("S2",) if s2 else ()):
+            g = run.read(name, level).T
+            o = getattr(mesh, name)
+            assert g.shape == o.shape, (name, level, g.shape, o.shape)
+            e = rel_l2(g, o)
+            worst[(level, name)] = e
+            assert e <= tol, (level, name, e)
+    return worst
+
+
+def test_uniform_fp64_matches_oracle():
+    w = W.small_dmr(nx=70, ny=50, r=1, rect=None)
+    sim = O.sim_from_workload(w)
+    run = D.run_from_workload(w)
+    steps = 2 * 32 + 7
+    sim.advance(steps)
+    run.advance(steps)
+    compare(run, sim, TOL64)
+    st = run.stats()
+    assert abs(st["N_e"] / sim.N_e - 1) < TOL64
+    assert abs(st["P_abs"] / sim.P_abs - 1) < TOL64
+    assert abs(st["W_abs"] / sim.W_abs - 1) < TOL64
+    assert st["periods"] == 2 and st["coarse_steps"] == steps
+
+
+def test_uniform_fp64_several_tiles_ragged():
+    """150 x 90 cells: 5 x 12 thread blocks with ragged last tiles."""
+    w = W.small_dmr(nx=150, ny=90, r=1, rect=None)
+    sim = O.sim_from_workload(w)
+    run = D.run_from_workload(w)
+    sim.advance(40)
+    run.advance(40)
+    compare(run, sim, TOL64)
+
+
+@pytest.mark.parametrize("rect", [(12, 10, 24, 20), (0, 0, 10, 9), (28, 20, 40, 32), (3, 0, 30, 6)])
+def test_dmr_fp64_growth_matches_oracle(rect):
+    """Free-running growth policy on both sides: identical rectangle after
+    every period, bit-exact masks, fields within 1e-12."""
+    w = W.small_dmr(rect=rect)
+    sim = O.sim_from_workload(w)
+    run = D.run_from_workload(w)
+    NT = w["cfg"]["steps_per_period"]
+    for p in range(4):
+        sim.advance(NT)
+        run.advance(NT)
+        assert run.get_patch() == tuple(sim.rect), (p, run.get_patch(), sim.rect)
+        mask = run.read("mask").T.astype(bool)
+        assert np.array_equal(mask, sim.masks[-1]), p
+    sim.advance(5)
+    run.advance(5)
+    compare(run, sim, TOL64)
+    st = run.stats()
+    assert abs(st["N_e"] / sim.N_e - 1) < TOL64
+    assert abs(st["P_abs"] / sim.P_abs - 1) < TOL64
+    assert sim.log[-1] != tuple(rect) or rect == (0, 0, 10, 9)
+
+
+def test_fp32_against_fp64_oracle_with_replay():
+    w = W.small_dmr(precision=1)
+    sim = O.sim_from_workload(w)
+    NT = w["cfg"]["steps_per_period"]
+    sim.advance(3 * NT + 9)
+    run = D.run_from_workload(w)
+    run.replay_log(sim.log)
+    run.advance(3 * NT + 9)
+    assert run.get_patch() == tuple(sim.rect)
+    worst = compare(run, sim, TOL32)
+    assert max(worst.values()) > 1e-9  # it really is FP32
+    # FP32 flags: the oracle's rule applied to the GPU's density in FP32
+    n32 = run.read("n").T
+    ref = O.flag_mask(n32, sim.P.n_th, sim.P.g_th, sim.P.dxc, dtype=np.float32)
+    run2 = D.run_from_workload(w)
+    run2.replay_log(sim.log)
+    run2.advance(3 * NT)
+    n32 = run2.read("n").T
+    ref = O.flag_mask(n32, sim.P.n_th, sim.P.g_th, sim.P.dxc, dtype=np.float32)
+    assert np.array_equal(run2.read("mask").T.astype(bool), ref)
+
+
+def test_full_patch_equals_uniform_fine_on_gpu():
+    """A rectangle covering the whole domain makes the fine mesh a uniform
+    fine run: bit-identical on the GPU too."""
+    w = W.small_dmr(nx=24, ny=20, r=2, rect=(0, 0, 24, 20))
+    dmr = D.run_from_workload(w)
+    uni = D.run_from_workload(W.uniform_fine_equivalent(w))
+    dmr.advance(2 * 32 + 3)
+    uni.advance(2 * (2 * 32 + 3))
+    for name in FIELDS:
+        assert np.array_equal(dmr.read(name, 1), uni.read(name, 0)), name
+    assert dmr.stats()["N_e"] == uni.stats()["N_e"]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graphs_equal_direct_launches(precision):
+    w = W.small_dmr(precision=precision)
+    a = D.run_from_workload(w)
+    b = D.run_from_workload(w)
+    b.set_graphs(True)
+    a.advance(5 * 32 + 4)
+    b.advance(5 * 32 + 4)
+    assert a.get_patch() == b.get_patch()
+    for level in (0, 1):
+        for name in FIELDS:
+            assert np.array_equal(a.read(name, level), b.read(name, level)), (level, name)
+    assert b.launch_count() > 0
+
+
+def test_vacuum_stays_exactly_zero():
+    w = W.small_dmr()
+    w = dict(w, seeds=[(0.0, 0.5, 0.5, 0.1, 0.1)])
+    run = D.run_from_workload(w)
+    run.advance(70)
+    for level in (0, 1):
+        for name in ("Ex", "Ey", "Hz", "vx", "n"):
+            assert not np.any(run.read(name, level)), (level, name)
+
+
+def test_full_size_dmr_512_fp32_graphs():
+    """The benchmark workload (coarse 512^2 at lambda/32, r = 2, FP32, CUDA
+    graphs as timed) against the FP64 oracle for two periods."""
+    w = W.dmr_512_r2(precision=1)
+    sim = O.sim_from_workload(w)
+    NT = w["cfg"]["steps_per_period"]
+    sim.advance(2 * NT)
+    run = D.run_from_workload(w)
+    run.set_graphs(True)
+    run.replay_log(sim.log)
+    run.advance(2 * NT)
+    compare(run, sim, TOL32, s2=False)
+    st = run.stats()
+    assert abs(st["N_e"] / sim.N_e - 1) < TOL32
+
+
+def test_capacity_error_and_state_errors():
+    w = W.small_dmr()
+    cfg = dict(w["cfg"], patch_cap_cells=4 * 12 * 10)
+    run = D.Run(cfg)
+    run.set_patch(w["rect"])
+    run.seed_workload(w["seeds"])
+    with pytest.raises(D.DMRError) as e:
+        run.advance(3 * 32)
+    assert e.value.code == D.ECAPACITY
+    uni = D.Run(dict(w["cfg"], r=1))
+    with pytest.raises(D.DMRError) as e:
+        uni.set_patch((1, 1, 5, 5))
+    assert e.value.code == D.ESTATE
+    run2 = D.run_from_workload(w)
+    run2.advance(3)
+    with pytest.raises(D.DMRError) as e:
+        run2.set_patch((0, 0, 40, 32))
+    assert e.value.code == D.ESTATE
+    run3 = D.run_from_workload(w)
+    with pytest.raises(D.DMRError) as e:
+        run3.set_patch((13, 10, 24, 20))
+    assert e.value.code == D.EINVAL
+
+
+def test_timing_counts_launches():
+    w = W.small_dmr(precision=1)
+    run = D.run_from_workload(w)
+    run.set_timing(True)
+    run.advance(32)
+    kt = run.kernel_times()
+    assert kt["coarse_h"][1] == 32 and kt["fine_e"][1] == 64
+    assert all(v[0] > 0 for k, v in kt.items() if v[1] > 0)
+    run.set_graphs(True)
+    run.set_timing(True)
+    run.advance(64)
+    kt = run.kernel_times()
+    assert kt["fine_e"][1] == 128 and kt["fine_e"][0] > 0
