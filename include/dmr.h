@@ -196,6 +196,30 @@ int dmr_launch_count(const dmr_ctx* ctx, int64_t* launches);
 /* Wait for all work queued on the run's stream. */
 int dmr_sync(const dmr_ctx* ctx);
 
+/* Electron total (per metre of depth) of one density map, without any
+ * allocation.  The paper has no counterpart to this call: it exists for
+ * callers that cannot allocate device memory at all -- a host application
+ * that gives all GPU memory to its own pool and lets no plug-in call
+ * cudaMalloc, code where an allocation (which synchronises the device) is not
+ * allowed, or a caller with no workspace to hand over.  It computes the same
+ * composite trapezoid sum as the run totals of a uniform mesh,
+ *   total = dx^2 * sum_{i,j} w_i w_j n[j][i],  w = 1/2 on the first and last
+ * node of each axis, 1 elsewhere,
+ * for a dense (ny+1) x (nx+1) node map n_dev (double for precision 0, float
+ * for precision 1) in device memory, and writes one double to total_dev
+ * (device memory).  Work is queued on cuda_stream (NULL = legacy default).
+ * Its scratch is a fixed array inside the library (16384 doubles, 128 KiB,
+ * held on every GPU that loads the library until the process exits), so maps
+ * above 67108864 nodes are rejected with DMR_ECAPACITY.  The first call on a
+ * device looks the array's device address up (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  Every call shares the array:
+ * calls that overlap on the GPU (other streams, other threads) race; calls
+ * on one stream are ordered and each rewrites the scratch it reads.  Errors:
+ * DMR_EINVAL, DMR_ECAPACITY, DMR_ECUDA; dmr_noalloc_last_error() explains. */
+int dmr_electron_total_noalloc(const void* n_dev, int32_t nx, int32_t ny, int32_t precision,
+                               double dx, void* cuda_stream, double* total_dev);
+const char* dmr_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libdmr.so")
 
-SOURCES = ["dmr.cu"]
+SOURCES = ["dmr.cu", "dmr_noalloc.cu"]
 HEADERS = ["dmr_kernels.cuh"]
 
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"

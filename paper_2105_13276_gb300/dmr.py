@@ -77,6 +77,8 @@ def load():
         "dmr_kernel_class_name": (c_char_p, [c_int]),
         "dmr_launch_count": (c_int, [P, POINTER(c_int64)]),
         "dmr_sync": (c_int, [P]),
+        "dmr_electron_total_noalloc": (c_int, [P, c_int32, c_int32, c_int32, c_double, P, P]),
+        "dmr_noalloc_last_error": (c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
