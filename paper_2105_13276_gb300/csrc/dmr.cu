@@ -88,7 +88,7 @@ int derive(const dmr_config* c, Derived* d, std::string* err) {
   return DMR_OK;
 }
 
-constexpr int BX = 32, BY = 8;
+constexpr int BX = dmr::TX, BY = dmr::TY;
 
 struct Layout {
   size_t es = 8;       // bytes per field element
@@ -96,10 +96,9 @@ struct Layout {
   size_t cplane = 0;   // coarse elements per array
   size_t fplane = 0;   // fine elements per array (capacity)
   int nblk_c = 0, nblk_f = 0;
-  size_t off_c[9] = {}, off_cS2 = 0;      // Ex Ey Hz vx vy n ntmp D nu
-  size_t off_f[2][6] = {}, off_fS2[2] = {};
+  size_t off_c[12] = {}, off_cS2 = 0;     // Ex Ey Hz vx vy n ntmp D nu, then Ex' Ey' Hz'
+  size_t off_f[2][9] = {}, off_fS2[2] = {};  // Ex Ey Hz vx vy n, then Ex' Ey' Hz'
   size_t off_ftmp[3] = {};                // ntmp D nu
-  size_t off_strip[4] = {};
   size_t off_tab[4] = {};                 // ckx_c skx_c ckx_f skx_f
   size_t off_mask = 0, off_part[4] = {}, off_ctl = 0, off_view = 0;
   size_t total = 0;
@@ -126,16 +125,14 @@ int make_layout(const dmr_config* c, const Derived& d, Layout* L, std::string* e
   L->nblk_f = r > 1 ? (int)(((r * nx + 1 + BX - 1) / BX) * ((r * ny + 1 + BY - 1) / BY)) : 0;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t at = o; o = up(o + bytes, 256); return at; };
-  for (int q = 0; q < 9; ++q) L->off_c[q] = take(L->cplane * L->es);
+  for (int q = 0; q < 12; ++q) L->off_c[q] = take(L->cplane * L->es);
   L->off_cS2 = take(L->cplane * 8);
   if (r > 1) {
     for (int s = 0; s < 2; ++s) {
-      for (int q = 0; q < 6; ++q) L->off_f[s][q] = take(L->fplane * L->es);
+      for (int q = 0; q < 9; ++q) L->off_f[s][q] = take(L->fplane * L->es);
       L->off_fS2[s] = take(L->fplane * 8);
     }
     for (int q = 0; q < 3; ++q) L->off_ftmp[q] = take(L->fplane * L->es);
-    const size_t sl = (size_t)std::max(nx, ny) + 1;
-    for (int q = 0; q < 4; ++q) L->off_strip[q] = take(sl * L->es);
   }
   L->off_tab[0] = take((size_t)(nx + 1) * L->es);
   L->off_tab[1] = take((size_t)(nx + 1) * L->es);
@@ -161,11 +158,13 @@ struct Base {
   cudaStream_t st = nullptr;
   std::string err;
   int64_t m = 0;            // coarse steps done (time level of coarse E)
+  int num_sms = 152;
   int64_t launches = 0;
   bool capturing = false;
   int64_t graph_nodes = 0;
   bool graphs = false;
   cudaGraphExec_t gexec = nullptr;
+  int g_cpar = 0, g_fpar = 0, g_rvalid = 0;   // state the graph was captured in
   std::vector<int32_t> replay;
   size_t replay_pos = 0;
   bool has_fine = false;
@@ -219,7 +218,7 @@ struct Base {
     else cudaEventRecord(e, st);
   }
   unsigned timing_mask = 0xffffffffu;
-  // units: grid points (nodes) the timed launch covers
+  // units: algorithmic bytes the timed launch must move (0: not a bandwidth kernel)
   int tbeg(int cls, double units) {
     if (!timing || !((timing_mask >> cls) & 1u)) return -1;
     int a = ev_get();
@@ -271,14 +270,21 @@ struct Base {
 
 template <class T>
 struct Engine final : Base {
+  // C and F[cur] always point at the current (level n) E/H buffers; the
+  // other buffer of each pair receives the next level (double buffering).
   dmr::Mesh<T> C{};
+  T* cE[2][3] = {};          // [parity][Ex, Ey, Hz]
+  int cpar = 0;
   T *c_ntmp = nullptr, *c_D = nullptr, *c_nu = nullptr;
   dmr::Mesh<T> F[2]{};
-  T* fptr[2][6] = {};
+  T* fptr[2][6] = {};        // [set][Ex, Ey, Hz, vx, vy, n] (parity 0)
+  T* fE1[2][3] = {};         // [set][Ex', Ey', Hz'] (parity 1)
   double* fS2[2] = {};
-  int cur = 0;
+  int cur = 0, fpar = 0;
+  // the fine arrays hold the result of sub-steps for the current rectangle, so
+  // the coarse E under it is their mean (false at start and after growth)
+  bool rvalid = false;
   T *f_ntmp = nullptr, *f_D = nullptr, *f_nu = nullptr;
-  T* strip[4] = {};
   T *ckx_c = nullptr, *skx_c = nullptr, *ckx_f = nullptr, *skx_f = nullptr;
   uint8_t* mask = nullptr;
   double* part[4] = {};
@@ -290,7 +296,8 @@ struct Engine final : Base {
   P* at(size_t off) { return reinterpret_cast<P*>(ws + off); }
 
   int init() override {
-    C.Ex = at<T>(L.off_c[0]); C.Ey = at<T>(L.off_c[1]); C.Hz = at<T>(L.off_c[2]);
+    for (int q = 0; q < 3; ++q) { cE[0][q] = at<T>(L.off_c[q]); cE[1][q] = at<T>(L.off_c[9 + q]); }
+    C.Ex = cE[0][0]; C.Ey = cE[0][1]; C.Hz = cE[0][2];
     C.vx = at<T>(L.off_c[3]); C.vy = at<T>(L.off_c[4]); C.n = at<T>(L.off_c[5]);
     c_ntmp = at<T>(L.off_c[6]); c_D = at<T>(L.off_c[7]); c_nu = at<T>(L.off_c[8]);
     C.S2 = at<double>(L.off_cS2);
@@ -298,10 +305,10 @@ struct Engine final : Base {
     if (cfg.r > 1) {
       for (int s = 0; s < 2; ++s) {
         for (int q = 0; q < 6; ++q) fptr[s][q] = at<T>(L.off_f[s][q]);
+        for (int q = 0; q < 3; ++q) fE1[s][q] = at<T>(L.off_f[s][6 + q]);
         fS2[s] = at<double>(L.off_fS2[s]);
       }
       f_ntmp = at<T>(L.off_ftmp[0]); f_D = at<T>(L.off_ftmp[1]); f_nu = at<T>(L.off_ftmp[2]);
-      for (int q = 0; q < 4; ++q) strip[q] = at<T>(L.off_strip[q]);
     }
     ckx_c = at<T>(L.off_tab[0]); skx_c = at<T>(L.off_tab[1]);
     ckx_f = at<T>(L.off_tab[2]); skx_f = at<T>(L.off_tab[3]);
@@ -311,6 +318,11 @@ struct Engine final : Base {
     view = at<double>(L.off_view);
     int s = ck(cudaMemsetAsync(ws, 0, L.total, st), "cudaMemsetAsync(workspace)");
     if (s) return s;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+      int v = 0;
+      if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) num_sms = v;
+    }
     // incident-wave column tables: cos(k x), sin(k x) at the node columns
     std::vector<T> tc(cfg.nx + 1), ts(cfg.nx + 1);
     for (int g = 0; g <= cfg.nx; ++g) {
@@ -333,6 +345,31 @@ struct Engine final : Base {
   }
 
   static dim3 nodes_grid(int nx, int ny) { return dim3((nx + 1 + BX - 1) / BX, (ny + 1 + BY - 1) / BY); }
+
+  // node rows per warp of the strip EM kernel: enough warps to fill the GPU
+  // (about 48 per SM); small meshes get 1-2 rows per warp so a launch costs
+  // about one memory latency, large ones up to 64 (the warm-up row is 1/rows)
+  int em_rows(int nx, int ny) const {
+    const long long sx = (nx + 1 + dmr::STRIP_W - 1) / dmr::STRIP_W;
+    const long long target = (long long)num_sms * 48;
+    long long rows = (sx * (ny + 1) + target - 1) / target;
+    return (int)std::min<long long>(64, std::max<long long>(1, rows));
+  }
+  dim3 em_grid(int nx, int ny, int rows) const {
+    const int sy = (ny + 1 + rows - 1) / rows;
+    return dim3((nx + 1 + dmr::STRIP_W - 1) / dmr::STRIP_W, (sy + dmr::EM_WARPS - 1) / dmr::EM_WARPS);
+  }
+
+  T* fineE(int set, int par, int q) const { return par ? fE1[set][q] : fptr[set][q]; }
+
+  void flip_coarse() {
+    cpar ^= 1;
+    C.Ex = cE[cpar][0]; C.Ey = cE[cpar][1]; C.Hz = cE[cpar][2];
+  }
+  void flip_fine() {
+    fpar ^= 1;
+    F[cur].Ex = fineE(cur, fpar, 0); F[cur].Ey = fineE(cur, fpar, 1); F[cur].Hz = fineE(cur, fpar, 2);
+  }
 
   dmr::Mesh<T> fine_view(int set, const int* rc) const {
     dmr::Mesh<T> f;
@@ -398,83 +435,112 @@ struct Engine final : Base {
     return DMR_OK;
   }
 
-  // one coarse step from level mlev: coarse H, E; r fine sub-steps; restriction
+  // rows / columns of the fine->coarse E transfer (a8)
+  void restr_bounds(int* jlo, int* jhi, int* ilo, int* ihi) const {
+    *jlo = side_on_edge(dmr::SIDE_BOTTOM) ? rect[1] : rect[1] + 1;
+    *jhi = side_on_edge(dmr::SIDE_TOP) ? rect[3] : rect[3] - 1;
+    *ilo = side_on_edge(dmr::SIDE_LEFT) ? rect[0] : rect[0] + 1;
+    *ihi = side_on_edge(dmr::SIDE_RIGHT) ? rect[2] : rect[2] - 1;
+  }
+
+  // algorithmic bytes of one fused EM launch over `pts` grid points: Ex, Ey,
+  // Hz, vx, vy read and written, n read, S2 (fp64) read and written if summed
+  double em_bytes(double pts, bool accum) const {
+    return pts * (11.0 * (double)L.es + (accum ? 16.0 : 0.0));
+  }
+
+  // one coarse step from level mlev: fused coarse EM step (reading the
+  // restricted E of the previous step on the fly), then r fused fine sub-steps
   int launch_coarse_step(int64_t mlev) {
     const int NT = cfg.steps_per_period, r = cfg.r;
-    dmr::Step<T> sc = make_step(1, mlev, (mlev % NT) != 0);
+    const bool acc_c = (mlev % NT) != 0;
+    dmr::Step<T> sc = make_step(1, mlev, acc_c);
     dmr::Bnd<T> bc{};
     for (int q = 0; q < 4; ++q) bc.mode[q] = dmr::BC_MUR;
     bc.r = 1;
-    if (has_fine) {
-      const int at_[4] = {rect[0], rect[2], rect[1], rect[3]};
-      for (int q = 0; q < 4; ++q)
-        if (!side_on_edge(q)) { bc.save[q] = strip[q]; bc.save_at[q] = at_[q]; }
+    dmr::Restr<T> R{};
+    if (has_fine && rvalid) {
+      R.on = 1;
+      R.I0 = rect[0]; R.J0 = rect[1]; R.I1 = rect[2]; R.J1 = rect[3]; R.r = r;
+      restr_bounds(&R.jlo, &R.jhi, &R.ilo, &R.ihi);
+      R.fEx = F[cur].Ex; R.fEy = F[cur].Ey; R.fp = F[cur].p;
     }
     const dim3 blk(BX, BY);
-    const double cn = (double)(C.nx + 1) * (C.ny + 1);
-    int h = tbeg(0, cn);
-    dmr::k_h<T><<<nodes_grid(C.nx, C.ny), blk, 0, st>>>(C, sc);
+    const dmr::Mesh<T> src = C;
+    T** dst = cE[cpar ^ 1];
+    const int rc = em_rows(C.nx, C.ny);
+    int h = tbeg(0, em_bytes((double)(C.nx + 1) * (C.ny + 1), acc_c));
+    dmr::k_em<T><<<em_grid(C.nx, C.ny, rc), 32 * dmr::EM_WARPS, 0, st>>>(src, dst[0], dst[1], dst[2],
+                                                                          sc, bc, R, rc);
     tend(h);
     counted(1);
-    h = tbeg(1, cn);
-    dmr::k_e<T><<<nodes_grid(C.nx, C.ny), blk, 0, st>>>(C, sc, bc);
-    tend(h);
-    counted(1);
+    flip_coarse();
     if (int s = launched("coarse EM")) return s;
     if (!has_fine) return DMR_OK;
-    dmr::Mesh<T> f = F[cur];
+    // Eq. 5b lines: coarse tangential E before (src) and after (C) the coarse step
     dmr::Bnd<T> bf{};
     bf.r = r;
     for (int q = 0; q < 4; ++q) {
       if (side_on_edge(q)) { bf.mode[q] = dmr::BC_MUR; continue; }
       bf.mode[q] = dmr::BC_CFB;
-      bf.old_line[q] = strip[q];
       if (q == dmr::SIDE_BOTTOM || q == dmr::SIDE_TOP) {
-        const int jl = q == dmr::SIDE_BOTTOM ? rect[1] : rect[3];
-        bf.new_line[q] = C.Ex + (size_t)jl * C.p;
-        bf.new_stride[q] = 1;
+        const size_t off = (size_t)(q == dmr::SIDE_BOTTOM ? rect[1] : rect[3]) * C.p;
+        bf.old_line[q] = src.Ex + off;
+        bf.new_line[q] = C.Ex + off;
+        bf.stride[q] = 1;
         bf.len[q] = cfg.nx;
         bf.start[q] = rect[0];
       } else {
-        const int il = q == dmr::SIDE_LEFT ? rect[0] : rect[2];
-        bf.new_line[q] = C.Ey + il;
-        bf.new_stride[q] = C.p;
+        const size_t off = (size_t)(q == dmr::SIDE_LEFT ? rect[0] : rect[2]);
+        bf.old_line[q] = src.Ey + off;
+        bf.new_line[q] = C.Ey + off;
+        bf.stride[q] = C.p;
         bf.len[q] = cfg.ny;
         bf.start[q] = rect[1];
       }
     }
-    const dim3 gf = nodes_grid(f.nx, f.ny);
-    const double fn = (double)(f.nx + 1) * (f.ny + 1);
+    const dmr::Restr<T> none{};
+    const int rf = em_rows(F[cur].nx, F[cur].ny);
+    const dim3 gf = em_grid(F[cur].nx, F[cur].ny, rf);
+    const double fn = (double)(F[cur].nx + 1) * (F[cur].ny + 1);
     for (int k = 1; k <= r; ++k) {
       const int64_t mf = (int64_t)r * mlev + (k - 1);
-      dmr::Step<T> sf = make_step(r, mf, (mf % ((int64_t)r * NT)) != 0);
+      const bool acc_f = (mf % ((int64_t)r * NT)) != 0;
+      dmr::Step<T> sf = make_step(r, mf, acc_f);
       bf.frac = (T)((double)k / (double)r);
-      h = tbeg(2, fn);
-      dmr::k_h<T><<<gf, blk, 0, st>>>(f, sf);
+      const dmr::Mesh<T> fs = F[cur];
+      h = tbeg(1, em_bytes(fn, acc_f));
+      dmr::k_em<T><<<gf, 32 * dmr::EM_WARPS, 0, st>>>(fs, fineE(cur, fpar ^ 1, 0), fineE(cur, fpar ^ 1, 1),
+                                                      fineE(cur, fpar ^ 1, 2), sf, bf, none, rf);
       tend(h);
-      h = tbeg(3, fn);
-      dmr::k_e<T><<<gf, blk, 0, st>>>(f, sf, bf);
-      tend(h);
-      counted(2);
+      counted(1);
+      flip_fine();
     }
-    const int jlo = side_on_edge(dmr::SIDE_BOTTOM) ? rect[1] : rect[1] + 1;
-    const int jhi = side_on_edge(dmr::SIDE_TOP) ? rect[3] : rect[3] - 1;
-    const int ilo = side_on_edge(dmr::SIDE_LEFT) ? rect[0] : rect[0] + 1;
-    const int ihi = side_on_edge(dmr::SIDE_RIGHT) ? rect[2] : rect[2] - 1;
+    rvalid = true;
+    return launched("fine EM");
+  }
+
+  // write the fine->coarse E transfer into the coarse arrays (the EM kernel
+  // reads it on the fly; the period end, reads and growth need it stored)
+  void materialize_restriction() {
+    if (!has_fine || !rvalid) return;
+    int jlo, jhi, ilo, ihi;
+    restr_bounds(&jlo, &jhi, &ilo, &ihi);
     const dim3 gr((rect[2] - rect[0] + 1 + BX - 1) / BX, (rect[3] - rect[1] + 1 + BY - 1) / BY);
-    h = tbeg(4, (double)(rect[2] - rect[0] + 1) * (rect[3] - rect[1] + 1));
-    dmr::k_restrict<T><<<gr, blk, 0, st>>>(C, f, rect[0], rect[1], rect[2], rect[3], r, jlo, jhi, ilo, ihi);
+    const int h = tbeg(2, (double)(rect[2] - rect[0] + 1) * (rect[3] - rect[1] + 1) *
+                              (double)(2 * cfg.r + 2) * (double)L.es);
+    dmr::k_restrict<T><<<gr, dim3(BX, BY), 0, st>>>(C, F[cur], rect[0], rect[1], rect[2], rect[3],
+                                                    cfg.r, jlo, jhi, ilo, ihi);
     tend(h);
     counted(1);
-    return launched("fine EM / restrict");
   }
 
   // continuity step, totals and flags at the end of a period (coarse level mlev)
   int launch_period_end(int64_t mlev) {
     const int r = cfg.r;
     const dim3 blk(BX, BY);
-    int h = tbeg(5, (double)(C.nx + 1) * (C.ny + 1) +
-                        (has_fine ? (double)(F[cur].nx + 1) * (F[cur].ny + 1) : 0.0));
+    materialize_restriction();
+    int h = tbeg(3, 0.0);
     dmr::Wts wc{cfg.nx, cfg.ny, has_fine ? 1 : 0, rect[0], rect[1], rect[2], rect[3]};
     dmr::Dens dc = make_dens(1);
     dmr::Step<T> sc = make_step(1, mlev, true);
@@ -592,7 +658,7 @@ struct Engine final : Base {
     if ((size_t)(nf.ny + 1) * nf.p > L.fplane) return fail(DMR_ECAPACITY, "fine arrays exceed the workspace");
     dmr::Mesh<T> of = has_fine ? F[cur] : nf;
     const int oI0 = has_fine ? rect[0] : nr[0], oJ0 = has_fine ? rect[1] : nr[1];
-    int h = tbeg(6, (double)(nf.nx + 1) * (nf.ny + 1));
+    int h = tbeg(4, 0.0);
     dmr::k_expand<T><<<nodes_grid(nf.nx, nf.ny), dim3(BX, BY), 0, st>>>(
         nf, of, C, nr[0], nr[1], oI0, oJ0, has_fine ? 1 : 0, cfg.r);
     tend(h);
@@ -600,6 +666,8 @@ struct Engine final : Base {
     if (int s = launched("expand")) return s;
     cur = nxt;
     F[cur] = nf;
+    fpar = 0;
+    rvalid = false;
     for (int q = 0; q < 4; ++q) rect[q] = nr[q];
     has_fine = true;
     drop_graph();
@@ -640,6 +708,8 @@ struct Engine final : Base {
     const int NT = cfg.steps_per_period;
     while (n > 0) {
       if (graphs && m % NT == 0 && n >= NT) {
+        // a graph holds the buffer parities it was captured with
+        if (gexec && (g_cpar != cpar || g_fpar != fpar || g_rvalid != (int)rvalid)) drop_graph();
         if (!gexec) {
           if (int s = capture()) return s;
         }
@@ -647,6 +717,9 @@ struct Engine final : Base {
         launches += graph_nodes;
         m += NT;
         n -= NT;
+        if (NT & 1) flip_coarse();
+        if (has_fine && (((int64_t)cfg.r * NT) & 1)) flip_fine();
+        if (has_fine) rvalid = true;
         if (int s = period_end_host(true)) return s;
         continue;
       }
@@ -668,10 +741,19 @@ struct Engine final : Base {
     if (int s = ck(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture")) return s;
     capturing = true;
     graph_nodes = 0;
+    // capturing advances the host-side buffer parities; put them back after
+    const int c0 = cpar, f0 = fpar;
+    const bool rv0 = rvalid;
     int s = DMR_OK;
     for (int q = 0; q < NT && !s; ++q) s = launch_coarse_step(m + q);
     if (!s) s = launch_period_end(m + NT);
     capturing = false;
+    if (cpar != c0) flip_coarse();
+    if (has_fine && fpar != f0) flip_fine();
+    rvalid = rv0;
+    g_cpar = c0;
+    g_fpar = f0;
+    g_rvalid = (int)rv0;
     cudaError_t e = cudaStreamEndCapture(st, &g);
     if (s) { if (g) cudaGraphDestroy(g); gpend.clear(); return s; }
     if (e != cudaSuccess) { gpend.clear(); return ck(e, "end capture"); }
@@ -729,6 +811,10 @@ struct Engine final : Base {
     if (int s = dims(field, level, &rows, &cols, &es)) return fail(s, "no such field / level");
     if (bytes < (size_t)rows * cols * es) return fail(DMR_ECAPACITY, "destination too small");
     const int p = field == DMR_FIELD_MASK ? cols : (level == 0 ? C.p : F[cur].p);
+    if (level == 0 && field != DMR_FIELD_MASK) {
+      materialize_restriction();
+      if (int e = launched("restriction")) return e;
+    }
     const void* src = field_ptr(field, level);
     if (field == DMR_FIELD_S2 && m % cfg.steps_per_period != 0) {
       // S2 holds the levels before the current one; add the current level so
@@ -925,9 +1011,8 @@ int dmr_kernel_time(const dmr_ctx* ctx, int kclass, double* ms, int64_t* n, doub
 }
 
 const char* dmr_kernel_class_name(int kclass) {
-  static const char* names[] = {"coarse_h", "coarse_e", "fine_h", "fine_e",
-                                "restrict", "period_end", "expand"};
-  if (kclass < 0 || kclass >= 7) return nullptr;
+  static const char* names[] = {"coarse_em", "fine_em", "restrict", "period_end", "expand"};
+  if (kclass < 0 || kclass >= 5) return nullptr;
   return names[kclass];
 }
 

@@ -39,21 +39,30 @@ struct Step {
   int accum;             // add |E_total|^2 of this level to S2
 };
 
-// Coarse-fine boundary (Eq. 5b) for the fine mesh, and the coarse lines it
-// reads.  For the coarse mesh, `save` receives the pre-update tangential E
-// of the rectangle's interior sides.
+// Coarse-fine boundary (Eq. 5b) for the fine mesh: per side, Mur or the
+// coarse tangential-E line before (old) and after (new) the coarse step.
 template <class T>
 struct Bnd {
   int mode[4];              // BC_MUR or BC_CFB per side
-  const T* old_line[4];     // coarse tangential E before the coarse step
-  const T* new_line[4];     // coarse tangential E after it (strided)
-  int new_stride[4];
+  const T* old_line[4];     // coarse tangential E at level n (strided)
+  const T* new_line[4];     // coarse tangential E at level n+1 (strided)
+  int stride[4];
   int len[4];               // coarse samples along the line
   int start[4];             // coarse index of the rectangle corner along the line
   int r;
   T frac;                   // k / r of the fine sub-step
-  T* save[4];               // coarse only: where to keep the old line (or null)
-  int save_at[4];           // coarse row / column of that line
+};
+
+// Fine -> coarse transfer read on the fly (a8): while a coarse tile loads its
+// E^n, each coarse edge of the restriction set takes the mean of its r
+// collinear fine edges (the fine arrays hold level n after the sub-steps).
+template <class T>
+struct Restr {
+  int on;
+  int I0, J0, I1, J1, r;
+  int jlo, jhi, ilo, ihi;   // Ex rows [jlo, jhi], Ey columns [ilo, ihi]
+  const T *fEx, *fEy;
+  int fp;
 };
 
 template <class T>
@@ -102,102 +111,194 @@ __device__ __forceinline__ T cfb_value(const Bnd<T>& b, int sd, int q) {
   const T xp = (T)w, one = T(1);
   const T* o = b.old_line[sd];
   const T* nw = b.new_line[sd];
-  const int s = b.new_stride[sd];
-  T lo = o[i0] * (one - xp) + o[i0 + 1] * xp;
+  const int s = b.stride[sd];
+  T lo = o[i0 * s] * (one - xp) + o[(i0 + 1) * s] * xp;
   T ln = nw[i0 * s] * (one - xp) + nw[(i0 + 1) * s] * xp;
   return (one - b.frac) * lo + b.frac * ln;
 }
 
-// a1 (Eq. 2) + a5 for the level being left: Hz^{n+1/2} from E^n, and S2 += |E^n|^2
-// at the nodes when c.accum.  Grid covers the (nx+1) x (ny+1) nodes.
+constexpr int TX = 32, TY = 8;   // 2-D thread block of the node-wise kernels
+
 template <class T>
-__global__ void k_h(Mesh<T> m, Step<T> c) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i > m.nx || j > m.ny) return;
-  const int p = m.p;
-  if (c.accum) m.S2[j * p + i] += (double)node_e2(m, c, i, j);
-  if (i < m.nx && j < m.ny) {
-    const int id = j * p + i;
-    T ey0 = m.Ey[id], ey1 = m.Ey[id + 1];
-    T ex0 = m.Ex[id], ex1 = m.Ex[id + p];
-    m.Hz[id] = m.Hz[id] - c.ch * ((ey1 - ey0) - (ex1 - ex0));
-  }
+__device__ __forceinline__ T restricted_ex(const Restr<T>& R, int i, int j) {
+  const T* f = R.fEx + (size_t)(R.r * (j - R.J0)) * R.fp + R.r * (i - R.I0);
+  T acc = f[0];
+  for (int q = 1; q < R.r; ++q) acc = acc + f[q];
+  return acc / (T)R.r;
 }
 
-// a2 + a3 + a4 (+ a6 on the fine mesh): v^{n+1/2} (Eq. 3), E^{n+1} on interior
-// edges (Eq. 1), Mur on domain sides, Eq. 5b on coarse-fine sides.
-// A Mur side's boundary edge (v and E) is advanced by the thread owning the
-// adjacent interior edge, which holds both E levels that Mur needs.
 template <class T>
-__global__ void k_e(Mesh<T> m, Step<T> c, Bnd<T> b) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i > m.nx || j > m.ny) return;
-  const int p = m.p;
-  const int nx = m.nx, ny = m.ny;
-  // ---- x edges (i < nx, j <= ny)
-  if (i < nx) {
-    const int id = j * p + i;
-    if (j > 0 && j < ny) {
-      T ex = m.Ex[id];
-      T v = c.va * m.vx[id] - c.vb * ex;
-      m.vx[id] = v;
-      if (b.save[SIDE_BOTTOM] && j == b.save_at[SIDE_BOTTOM]) b.save[SIDE_BOTTOM][i] = ex;
-      if (b.save[SIDE_TOP] && j == b.save_at[SIDE_TOP]) b.save[SIDE_TOP][i] = ex;
-      T en = ex + c.ce * (m.Hz[id] - m.Hz[id - p]) + c.cj * (m.n[id] + m.n[id + 1]) * v;
-      m.Ex[id] = en;
-      if (j == 1 && b.mode[SIDE_BOTTOM] == BC_MUR) {
-        const int ib = i;
-        T eb = m.Ex[ib];
-        m.vx[ib] = c.va * m.vx[ib] - c.vb * eb;
-        m.Ex[ib] = ex + c.mur * (en - eb);
-      }
-      if (j == ny - 1 && b.mode[SIDE_TOP] == BC_MUR) {
-        const int ib = ny * p + i;
-        T eb = m.Ex[ib];
-        m.vx[ib] = c.va * m.vx[ib] - c.vb * eb;
-        m.Ex[ib] = ex + c.mur * (en - eb);
-      }
-    } else {
-      const int sd = (j == 0) ? SIDE_BOTTOM : SIDE_TOP;
-      if (b.mode[sd] == BC_CFB) {
-        m.vx[id] = c.va * m.vx[id] - c.vb * m.Ex[id];
-        m.Ex[id] = cfb_value(b, sd, i);
-      }
-    }
+__device__ __forceinline__ T restricted_ey(const Restr<T>& R, int i, int j) {
+  const T* f = R.fEy + (size_t)(R.r * (j - R.J0)) * R.fp + R.r * (i - R.I0);
+  T acc = f[0];
+  for (int q = 1; q < R.r; ++q) acc = acc + f[(size_t)q * R.fp];
+  return acc / (T)R.r;
+}
+
+template <class T>
+__device__ __forceinline__ T load_ex(const Mesh<T>& m, const Restr<T>& R, int i, int j) {
+  if (i < 0 || i >= m.nx || j < 0 || j > m.ny) return T(0);
+  if (R.on && i >= R.I0 && i < R.I1 && j >= R.jlo && j <= R.jhi) return restricted_ex(R, i, j);
+  return m.Ex[j * m.p + i];
+}
+
+template <class T>
+__device__ __forceinline__ T load_ey(const Mesh<T>& m, const Restr<T>& R, int i, int j) {
+  if (i < 0 || i > m.nx || j < 0 || j >= m.ny) return T(0);
+  if (R.on && i >= R.ilo && i <= R.ihi && j >= R.J0 && j < R.J1) return restricted_ey(R, i, j);
+  return m.Ey[j * m.p + i];
+}
+
+// One EM step on one mesh, fused (a1-a6 + a5 of the level being left):
+//   Hz^{n+1/2} from E^n (Eq. 2); S2 += |E^n_total|^2 at the nodes when c.accum;
+//   v^{n+1/2} (Eq. 3); E^{n+1} on interior edges (Eq. 1); Mur on domain sides;
+//   Eq. 5b on coarse-fine sides.
+// E and H are double-buffered (read m.Ex/Ey/Hz, write dEx/dEy/dHz), so strips
+// may read neighbouring E^n and H^{n-1/2} while those are being advanced.
+//
+// Warp strips: lane L of a warp holds node column i = c0 - 1 + L with
+// c0 = STRIP_W * strip; lanes 1..STRIP_W own their columns, lane 0 and lane 31
+// are halo columns that only load and (lane 0) compute H for their neighbour.
+// The warp marches up `rows` node rows, carrying the previous row's E^n, new
+// H, density and Ey^n in registers; every x-neighbour comes by shuffle, so
+// there is no shared memory and no block barrier.  A Mur side's boundary edge
+// is advanced by the owner of the adjacent interior edge, which holds both E
+// levels.  Each element is read once and written once: 60 B per cell (FP32).
+constexpr int STRIP_W = 30;
+constexpr int EM_WARPS = 4;   // warps per block (consecutive strips in y)
+
+template <class T>
+__global__ void __launch_bounds__(32 * EM_WARPS) k_em(Mesh<T> m, T* __restrict__ dEx, T* __restrict__ dEy,
+                                                      T* __restrict__ dHz, Step<T> c, Bnd<T> b,
+                                                      Restr<T> R, int rows) {
+  const int lane = threadIdx.x & 31;
+  const int sy = blockIdx.y * EM_WARPS + (threadIdx.x >> 5);
+  const int p = m.p, nx = m.nx, ny = m.ny;
+  const int i = blockIdx.x * STRIP_W - 1 + lane;
+  const int j0 = sy * rows;
+  if (j0 > ny) return;                       // whole warp leaves together
+  const int j1 = min(j0 + rows, ny + 1);     // node rows [j0, j1)
+  const bool own = lane >= 1 && lane <= STRIP_W && i <= nx;
+  const bool xcol = i >= 0 && i < nx;        // column has Ex / Hz
+  const bool ycol = i >= 0 && i <= nx;       // column has Ey / n
+  const T inc = ycol ? incident(c, i) : T(0);
+  const T inc0 = incident(c, 0), incn = incident(c, nx);
+  // ---- carried state for row j: Ex^n(j), Ex^n(j-1), Ey^n(j-1), Hz^{n+1/2}(j-1), n(j)
+  T exc = T(0), exp_ = T(0), eyp = T(0), hzp = T(0), nc = T(0);
+  if (xcol) exc = load_ex(m, R, i, j0);
+  if (ycol) nc = m.n[j0 * p + i];
+  if (j0 > 0) {
+    // H of row j0-1, needed by the Ex update of row j0
+    const int jm = j0 - 1;
+    const T exm = xcol ? load_ex(m, R, i, jm) : T(0);
+    const T eym = ycol ? load_ey(m, R, i, jm) : T(0);
+    const T hzo = xcol ? m.Hz[jm * p + i] : T(0);
+    const T eyr = __shfl_down_sync(0xffffffffu, eym, 1);
+    if (xcol) hzp = hzo - c.ch * ((eyr - eym) - (exc - exm));
+    exp_ = exm;
+    eyp = eym;
   }
-  // ---- y edges (i <= nx, j < ny)
-  if (j < ny) {
+  // row loads, software-pipelined: row j+1 is loaded before row j is stored
+  struct Row { T exn, eyc, hzo, vxo, vyo, nn; double s2; };
+  auto load_row = [&](int j) {
+    Row q;
     const int id = j * p + i;
-    const T inc = incident(c, i);
-    if (i > 0 && i < nx) {
-      T ey = m.Ey[id];
-      T v = c.va * m.vy[id] - c.vb * (ey + inc);
-      m.vy[id] = v;
-      if (b.save[SIDE_LEFT] && i == b.save_at[SIDE_LEFT]) b.save[SIDE_LEFT][j] = ey;
-      if (b.save[SIDE_RIGHT] && i == b.save_at[SIDE_RIGHT]) b.save[SIDE_RIGHT][j] = ey;
-      T en = ey - c.ce * (m.Hz[id] - m.Hz[id - 1]) + c.cj * (m.n[id] + m.n[id + p]) * v;
-      m.Ey[id] = en;
-      if (i == 1 && b.mode[SIDE_LEFT] == BC_MUR) {
-        const int ib = j * p;
-        T eb = m.Ey[ib];
-        m.vy[ib] = c.va * m.vy[ib] - c.vb * (eb + incident(c, 0));
-        m.Ey[ib] = ey + c.mur * (en - eb);
+    const bool in = j < ny;
+    q.exn = (xcol && in) ? load_ex(m, R, i, j + 1) : T(0);
+    q.eyc = (ycol && in) ? load_ey(m, R, i, j) : T(0);
+    q.hzo = (xcol && in) ? m.Hz[id] : T(0);
+    q.vxo = xcol ? m.vx[id] : T(0);
+    q.vyo = (ycol && in) ? m.vy[id] : T(0);
+    q.nn = (ycol && in) ? m.n[id + p] : T(0);
+    q.s2 = (c.accum && own) ? m.S2[id] : 0.0;
+    return q;
+  };
+  Row nxt = load_row(j0);
+  for (int j = j0; j < j1; ++j) {
+    const int id = j * p + i;
+    const Row cur = nxt;
+    if (j + 1 < j1) nxt = load_row(j + 1);
+    const T exn = cur.exn, eyc = cur.eyc, hzo = cur.hzo, vxo = cur.vxo, vyo = cur.vyo, nn = cur.nn;
+    const double s2 = cur.s2;
+    // ---- H (Eq. 2)
+    const T eyr = __shfl_down_sync(0xffffffffu, eyc, 1);
+    T hz = T(0);
+    if (xcol && j < ny) hz = hzo - c.ch * ((eyr - eyc) - (exn - exc));
+    const T hzl = __shfl_up_sync(0xffffffffu, hz, 1);
+    const T exl = __shfl_up_sync(0xffffffffu, exc, 1);
+    const T ncr = __shfl_down_sync(0xffffffffu, nc, 1);
+    const T eyl = __shfl_up_sync(0xffffffffu, eyc, 1);
+    const T vyl = __shfl_up_sync(0xffffffffu, vyo, 1);
+    const T vyr = __shfl_down_sync(0xffffffffu, vyo, 1);
+    if (own) {
+      if (i < nx && j < ny) dHz[id] = hz;
+      // ---- S2 += |E^n|^2 at node (i, j)
+      if (c.accum) {
+        T sx, sy;
+        if (i > 0 && i < nx) sx = T(0.5) * (exl * exl + exc * exc);
+        else if (i > 0) sx = exl * exl;
+        else sx = exc * exc;
+        const T e = eyp + inc, f = eyc + inc;
+        if (j > 0 && j < ny) sy = T(0.5) * (e * e + f * f);
+        else if (j > 0) sy = e * e;
+        else sy = f * f;
+        m.S2[id] = s2 + (double)(sx + sy);
       }
-      if (i == nx - 1 && b.mode[SIDE_RIGHT] == BC_MUR) {
-        const int ib = j * p + nx;
-        T eb = m.Ey[ib];
-        m.vy[ib] = c.va * m.vy[ib] - c.vb * (eb + incident(c, nx));
-        m.Ey[ib] = ey + c.mur * (en - eb);
+      // ---- x edge (i, j)
+      if (i < nx) {
+        if (j > 0 && j < ny) {
+          const T v = c.va * vxo - c.vb * exc;
+          m.vx[id] = v;
+          const T en = exc + c.ce * (hz - hzp) + c.cj * (nc + ncr) * v;
+          dEx[id] = en;
+          if (j == 1 && b.mode[SIDE_BOTTOM] == BC_MUR) {
+            m.vx[i] = c.va * m.vx[i] - c.vb * exp_;
+            dEx[i] = exc + c.mur * (en - exp_);
+          }
+          if (j == ny - 1 && b.mode[SIDE_TOP] == BC_MUR) {
+            const int ib = ny * p + i;
+            m.vx[ib] = c.va * m.vx[ib] - c.vb * exn;
+            dEx[ib] = exc + c.mur * (en - exn);
+          }
+        } else {
+          const int sd = (j == 0) ? SIDE_BOTTOM : SIDE_TOP;
+          if (b.mode[sd] == BC_CFB) {
+            m.vx[id] = c.va * vxo - c.vb * exc;
+            dEx[id] = cfb_value(b, sd, i);
+          }
+        }
       }
-    } else {
-      const int sd = (i == 0) ? SIDE_LEFT : SIDE_RIGHT;
-      if (b.mode[sd] == BC_CFB) {
-        m.vy[id] = c.va * m.vy[id] - c.vb * (m.Ey[id] + inc);
-        m.Ey[id] = cfb_value(b, sd, j);
+      // ---- y edge (i, j)
+      if (j < ny) {
+        if (i > 0 && i < nx) {
+          const T v = c.va * vyo - c.vb * (eyc + inc);
+          m.vy[id] = v;
+          const T en = eyc - c.ce * (hz - hzl) + c.cj * (nc + nn) * v;
+          dEy[id] = en;
+          if (i == 1 && b.mode[SIDE_LEFT] == BC_MUR) {
+            const int ib = j * p;
+            m.vy[ib] = c.va * vyl - c.vb * (eyl + inc0);
+            dEy[ib] = eyc + c.mur * (en - eyl);
+          }
+          if (i == nx - 1 && b.mode[SIDE_RIGHT] == BC_MUR) {
+            const int ib = j * p + nx;
+            m.vy[ib] = c.va * vyr - c.vb * (eyr + incn);
+            dEy[ib] = eyc + c.mur * (en - eyr);
+          }
+        } else {
+          const int sd = (i == 0) ? SIDE_LEFT : SIDE_RIGHT;
+          if (b.mode[sd] == BC_CFB) {
+            m.vy[id] = c.va * vyo - c.vb * (eyc + inc);
+            dEy[id] = cfb_value(b, sd, j);
+          }
+        }
       }
     }
+    exp_ = exc;
+    exc = exn;
+    eyp = eyc;
+    hzp = hz;
+    nc = nn;
   }
 }
 

@@ -211,10 +211,14 @@ def test_timing_counts_launches():
     run.set_timing(True)
     run.advance(32)
     kt = run.kernel_times()
-    assert kt["coarse_h"][1] == 32 and kt["fine_e"][1] == 64
+    assert kt["coarse_em"][1] == 32 and kt["fine_em"][1] == 64
     assert all(v[0] > 0 for k, v in kt.items() if v[1] > 0)
     run.set_graphs(True)
     run.set_timing(True)
     run.advance(64)
     kt = run.kernel_times()
-    assert kt["fine_e"][1] == 128 and kt["fine_e"][0] > 0
+    assert kt["fine_em"][1] == 128 and kt["fine_em"][0] > 0
+    # algorithmic bytes: 60 B per grid point per FP32 EM launch (44 B when no E^2 sample)
+    ms, n, nbytes = kt["coarse_em"]
+    pts = 41 * 33
+    assert nbytes == pytest.approx(64 * pts * 60 - 2 * pts * 16)
