@@ -180,8 +180,9 @@ int dmr_set_graphs(dmr_ctx* ctx, int enable);
 /* Per-kernel timing with CUDA events recorded on the run's stream around each
  * launch.  enable is a bit mask of the kernel classes to time (bit k for
  * class k; -1 for all; 0 switches timing off); each call resets the sums.
- * Classes: 0 coarse EM step, 1 fine EM sub-step, 2 fine->coarse E transfer
- * written to the coarse arrays, 3 period-end kernels, 4 growth.
+ * Classes: 0 EM step (the coarse step together with the first fine
+ * sub-step), 1 later fine sub-steps, 2 fine->coarse E transfer written to
+ * the coarse arrays, 3 period-end kernels, 4 growth.
  * dmr_kernel_time returns, for a class, the summed device time in ms, the
  * number of timed launches and the algorithmic bytes those launches had to
  * move (each array element read and written once; 0 for classes 3 and 4);

@@ -96,8 +96,8 @@ struct Layout {
   size_t cplane = 0;   // coarse elements per array
   size_t fplane = 0;   // fine elements per array (capacity)
   int nblk_c = 0, nblk_f = 0;
-  size_t off_c[12] = {}, off_cS2 = 0;     // Ex Ey Hz vx vy n ntmp D nu, then Ex' Ey' Hz'
-  size_t off_f[2][9] = {}, off_fS2[2] = {};  // Ex Ey Hz vx vy n, then Ex' Ey' Hz'
+  size_t off_c[14] = {}, off_cS2 = 0;     // Ex Ey Hz vx vy n ntmp D nu, then Ex' Ey' Hz' vx' vy'
+  size_t off_f[2][11] = {}, off_fS2[2] = {};  // Ex Ey Hz vx vy n, then Ex' Ey' Hz' vx' vy'
   size_t off_ftmp[3] = {};                // ntmp D nu
   size_t off_tab[4] = {};                 // ckx_c skx_c ckx_f skx_f
   size_t off_mask = 0, off_part[4] = {}, off_ctl = 0, off_view = 0;
@@ -125,11 +125,11 @@ int make_layout(const dmr_config* c, const Derived& d, Layout* L, std::string* e
   L->nblk_f = r > 1 ? (int)(((r * nx + 1 + BX - 1) / BX) * ((r * ny + 1 + BY - 1) / BY)) : 0;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t at = o; o = up(o + bytes, 256); return at; };
-  for (int q = 0; q < 12; ++q) L->off_c[q] = take(L->cplane * L->es);
+  for (int q = 0; q < 14; ++q) L->off_c[q] = take(L->cplane * L->es);
   L->off_cS2 = take(L->cplane * 8);
   if (r > 1) {
     for (int s = 0; s < 2; ++s) {
-      for (int q = 0; q < 9; ++q) L->off_f[s][q] = take(L->fplane * L->es);
+      for (int q = 0; q < 11; ++q) L->off_f[s][q] = take(L->fplane * L->es);
       L->off_fS2[s] = take(L->fplane * 8);
     }
     for (int q = 0; q < 3; ++q) L->off_ftmp[q] = take(L->fplane * L->es);
@@ -273,12 +273,12 @@ struct Engine final : Base {
   // C and F[cur] always point at the current (level n) E/H buffers; the
   // other buffer of each pair receives the next level (double buffering).
   dmr::Mesh<T> C{};
-  T* cE[2][3] = {};          // [parity][Ex, Ey, Hz]
+  T* cE[2][5] = {};          // [parity][Ex, Ey, Hz, vx, vy]
   int cpar = 0;
   T *c_ntmp = nullptr, *c_D = nullptr, *c_nu = nullptr;
   dmr::Mesh<T> F[2]{};
   T* fptr[2][6] = {};        // [set][Ex, Ey, Hz, vx, vy, n] (parity 0)
-  T* fE1[2][3] = {};         // [set][Ex', Ey', Hz'] (parity 1)
+  T* fE1[2][5] = {};         // [set][Ex', Ey', Hz', vx', vy'] (parity 1)
   double* fS2[2] = {};
   int cur = 0, fpar = 0;
   // the fine arrays hold the result of sub-steps for the current rectangle, so
@@ -296,16 +296,16 @@ struct Engine final : Base {
   P* at(size_t off) { return reinterpret_cast<P*>(ws + off); }
 
   int init() override {
-    for (int q = 0; q < 3; ++q) { cE[0][q] = at<T>(L.off_c[q]); cE[1][q] = at<T>(L.off_c[9 + q]); }
-    C.Ex = cE[0][0]; C.Ey = cE[0][1]; C.Hz = cE[0][2];
-    C.vx = at<T>(L.off_c[3]); C.vy = at<T>(L.off_c[4]); C.n = at<T>(L.off_c[5]);
+    for (int q = 0; q < 5; ++q) { cE[0][q] = at<T>(L.off_c[q]); cE[1][q] = at<T>(L.off_c[9 + q]); }
+    C.Ex = cE[0][0]; C.Ey = cE[0][1]; C.Hz = cE[0][2]; C.vx = cE[0][3]; C.vy = cE[0][4];
+    C.n = at<T>(L.off_c[5]);
     c_ntmp = at<T>(L.off_c[6]); c_D = at<T>(L.off_c[7]); c_nu = at<T>(L.off_c[8]);
     C.S2 = at<double>(L.off_cS2);
     C.nx = cfg.nx; C.ny = cfg.ny; C.p = L.pc;
     if (cfg.r > 1) {
       for (int s = 0; s < 2; ++s) {
         for (int q = 0; q < 6; ++q) fptr[s][q] = at<T>(L.off_f[s][q]);
-        for (int q = 0; q < 3; ++q) fE1[s][q] = at<T>(L.off_f[s][6 + q]);
+        for (int q = 0; q < 5; ++q) fE1[s][q] = at<T>(L.off_f[s][6 + q]);
         fS2[s] = at<double>(L.off_fS2[s]);
       }
       f_ntmp = at<T>(L.off_ftmp[0]); f_D = at<T>(L.off_ftmp[1]); f_nu = at<T>(L.off_ftmp[2]);
@@ -355,20 +355,18 @@ struct Engine final : Base {
     long long rows = (sx * (ny + 1) + target - 1) / target;
     return (int)std::min<long long>(64, std::max<long long>(1, rows));
   }
-  dim3 em_grid(int nx, int ny, int rows) const {
-    const int sy = (ny + 1 + rows - 1) / rows;
-    return dim3((nx + 1 + dmr::STRIP_W - 1) / dmr::STRIP_W, (sy + dmr::EM_WARPS - 1) / dmr::EM_WARPS);
-  }
+
 
   T* fineE(int set, int par, int q) const { return par ? fE1[set][q] : fptr[set][q]; }
 
   void flip_coarse() {
     cpar ^= 1;
-    C.Ex = cE[cpar][0]; C.Ey = cE[cpar][1]; C.Hz = cE[cpar][2];
+    C.Ex = cE[cpar][0]; C.Ey = cE[cpar][1]; C.Hz = cE[cpar][2]; C.vx = cE[cpar][3]; C.vy = cE[cpar][4];
   }
   void flip_fine() {
     fpar ^= 1;
     F[cur].Ex = fineE(cur, fpar, 0); F[cur].Ey = fineE(cur, fpar, 1); F[cur].Hz = fineE(cur, fpar, 2);
+    F[cur].vx = fineE(cur, fpar, 3); F[cur].vy = fineE(cur, fpar, 4);
   }
 
   dmr::Mesh<T> fine_view(int set, const int* rc) const {
@@ -449,8 +447,27 @@ struct Engine final : Base {
     return pts * (11.0 * (double)L.es + (accum ? 16.0 : 0.0));
   }
 
-  // one coarse step from level mlev: fused coarse EM step (reading the
-  // restricted E of the previous step on the fly), then r fused fine sub-steps
+  dmr::EmArgs<T> em_args(const dmr::Mesh<T>& src, T* const* dst, const dmr::Step<T>& c,
+                         const dmr::Bnd<T>& b, const dmr::Restr<T>& R) const {
+    dmr::EmArgs<T> A;
+    A.m = src;
+    A.dEx = dst[0]; A.dEy = dst[1]; A.dHz = dst[2]; A.dvx = dst[3]; A.dvy = dst[4];
+    A.c = c; A.b = b; A.R = R;
+    A.rows = em_rows(src.nx, src.ny);
+    A.gx = (src.nx + 1 + dmr::STRIP_W - 1) / dmr::STRIP_W;
+    const int sy = (src.ny + 1 + A.rows - 1) / A.rows;
+    A.nblk = A.gx * ((sy + dmr::EM_WARPS - 1) / dmr::EM_WARPS);
+    int ncf = 0;
+    for (int q = 0; q < 4; ++q)
+      if (b.mode[q] == dmr::BC_CFB) ncf += (q == dmr::SIDE_BOTTOM || q == dmr::SIDE_TOP) ? src.nx : src.ny;
+    A.ncfb = (ncf + 32 * dmr::EM_WARPS - 1) / (32 * dmr::EM_WARPS);
+    return A;
+  }
+
+  // one coarse step from level mlev.  The coarse step (reading the restricted
+  // E of the previous step on the fly) and the first fine sub-step (which
+  // evaluates the coarse E^{n+1} on its boundary lines itself) are
+  // independent and share one launch; fine sub-steps 2..r follow.
   int launch_coarse_step(int64_t mlev) {
     const int NT = cfg.steps_per_period, r = cfg.r;
     const bool acc_c = (mlev % NT) != 0;
@@ -465,59 +482,71 @@ struct Engine final : Base {
       restr_bounds(&R.jlo, &R.jhi, &R.ilo, &R.ihi);
       R.fEx = F[cur].Ex; R.fEy = F[cur].Ey; R.fp = F[cur].p;
     }
-    const dim3 blk(BX, BY);
     const dmr::Mesh<T> src = C;
-    T** dst = cE[cpar ^ 1];
-    const int rc = em_rows(C.nx, C.ny);
-    int h = tbeg(0, em_bytes((double)(C.nx + 1) * (C.ny + 1), acc_c));
-    dmr::k_em<T><<<em_grid(C.nx, C.ny, rc), 32 * dmr::EM_WARPS, 0, st>>>(src, dst[0], dst[1], dst[2],
-                                                                          sc, bc, R, rc);
-    tend(h);
-    counted(1);
-    flip_coarse();
-    if (int s = launched("coarse EM")) return s;
-    if (!has_fine) return DMR_OK;
-    // Eq. 5b lines: coarse tangential E before (src) and after (C) the coarse step
+    T* cdst[5] = {cE[cpar ^ 1][0], cE[cpar ^ 1][1], cE[cpar ^ 1][2], cE[cpar ^ 1][3], cE[cpar ^ 1][4]};
+    const dmr::EmArgs<T> Ac = em_args(src, cdst, sc, bc, R);
+    const double cbytes = em_bytes((double)(C.nx + 1) * (C.ny + 1), acc_c);
+    if (!has_fine) {
+      int h = tbeg(0, cbytes);
+      dmr::k_em<T><<<Ac.nblk + Ac.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Ac);
+      tend(h);
+      counted(1);
+      flip_coarse();
+      return launched("coarse EM");
+    }
+    // Eq. 5b lines: coarse tangential E before (src) and after (cdst) the coarse step
     dmr::Bnd<T> bf{};
     bf.r = r;
     for (int q = 0; q < 4; ++q) {
       if (side_on_edge(q)) { bf.mode[q] = dmr::BC_MUR; continue; }
       bf.mode[q] = dmr::BC_CFB;
       if (q == dmr::SIDE_BOTTOM || q == dmr::SIDE_TOP) {
-        const size_t off = (size_t)(q == dmr::SIDE_BOTTOM ? rect[1] : rect[3]) * C.p;
+        bf.at[q] = q == dmr::SIDE_BOTTOM ? rect[1] : rect[3];
+        const size_t off = (size_t)bf.at[q] * C.p;
         bf.old_line[q] = src.Ex + off;
-        bf.new_line[q] = C.Ex + off;
+        bf.new_line[q] = cdst[0] + off;
         bf.stride[q] = 1;
         bf.len[q] = cfg.nx;
         bf.start[q] = rect[0];
       } else {
-        const size_t off = (size_t)(q == dmr::SIDE_LEFT ? rect[0] : rect[2]);
+        bf.at[q] = q == dmr::SIDE_LEFT ? rect[0] : rect[2];
+        const size_t off = (size_t)bf.at[q];
         bf.old_line[q] = src.Ey + off;
-        bf.new_line[q] = C.Ey + off;
+        bf.new_line[q] = cdst[1] + off;
         bf.stride[q] = C.p;
         bf.len[q] = cfg.ny;
         bf.start[q] = rect[1];
       }
     }
+    bf.cm = src;
+    bf.cc = sc;
+    bf.cR = R;
     const dmr::Restr<T> none{};
-    const int rf = em_rows(F[cur].nx, F[cur].ny);
-    const dim3 gf = em_grid(F[cur].nx, F[cur].ny, rf);
     const double fn = (double)(F[cur].nx + 1) * (F[cur].ny + 1);
     for (int k = 1; k <= r; ++k) {
       const int64_t mf = (int64_t)r * mlev + (k - 1);
       const bool acc_f = (mf % ((int64_t)r * NT)) != 0;
       dmr::Step<T> sf = make_step(r, mf, acc_f);
       bf.frac = (T)((double)k / (double)r);
-      const dmr::Mesh<T> fs = F[cur];
-      h = tbeg(1, em_bytes(fn, acc_f));
-      dmr::k_em<T><<<gf, 32 * dmr::EM_WARPS, 0, st>>>(fs, fineE(cur, fpar ^ 1, 0), fineE(cur, fpar ^ 1, 1),
-                                                      fineE(cur, fpar ^ 1, 2), sf, bf, none, rf);
-      tend(h);
+      bf.recompute = k == 1 ? 1 : 0;
+      T* fdst[5] = {fineE(cur, fpar ^ 1, 0), fineE(cur, fpar ^ 1, 1), fineE(cur, fpar ^ 1, 2),
+                    fineE(cur, fpar ^ 1, 3), fineE(cur, fpar ^ 1, 4)};
+      const dmr::EmArgs<T> Af = em_args(F[cur], fdst, sf, bf, none);
+      if (k == 1) {
+        int h = tbeg(0, cbytes + em_bytes(fn, acc_f));
+        dmr::k_em2<T><<<Ac.nblk + Ac.ncfb + Af.nblk + Af.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Ac, Af);
+        tend(h);
+        flip_coarse();
+      } else {
+        int h = tbeg(1, em_bytes(fn, acc_f));
+        dmr::k_em<T><<<Af.nblk + Af.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Af);
+        tend(h);
+      }
       counted(1);
       flip_fine();
     }
     rvalid = true;
-    return launched("fine EM");
+    return launched("EM step");
   }
 
   // write the fine->coarse E transfer into the coarse arrays (the EM kernel
@@ -1011,7 +1040,7 @@ int dmr_kernel_time(const dmr_ctx* ctx, int kclass, double* ms, int64_t* n, doub
 }
 
 const char* dmr_kernel_class_name(int kclass) {
-  static const char* names[] = {"coarse_em", "fine_em", "restrict", "period_end", "expand"};
+  static const char* names[] = {"em_step", "fine_em", "restrict", "period_end", "expand"};
   if (kclass < 0 || kclass >= 5) return nullptr;
   return names[kclass];
 }

@@ -39,21 +39,7 @@ struct Step {
   int accum;             // add |E_total|^2 of this level to S2
 };
 
-// Coarse-fine boundary (Eq. 5b) for the fine mesh: per side, Mur or the
-// coarse tangential-E line before (old) and after (new) the coarse step.
-template <class T>
-struct Bnd {
-  int mode[4];              // BC_MUR or BC_CFB per side
-  const T* old_line[4];     // coarse tangential E at level n (strided)
-  const T* new_line[4];     // coarse tangential E at level n+1 (strided)
-  int stride[4];
-  int len[4];               // coarse samples along the line
-  int start[4];             // coarse index of the rectangle corner along the line
-  int r;
-  T frac;                   // k / r of the fine sub-step
-};
-
-// Fine -> coarse transfer read on the fly (a8): while a coarse tile loads its
+// Fine -> coarse transfer read on the fly (a8): while the coarse step loads
 // E^n, each coarse edge of the restriction set takes the mean of its r
 // collinear fine edges (the fine arrays hold level n after the sub-steps).
 template <class T>
@@ -63,6 +49,28 @@ struct Restr {
   int jlo, jhi, ilo, ihi;   // Ex rows [jlo, jhi], Ey columns [ilo, ihi]
   const T *fEx, *fEy;
   int fp;
+};
+
+// Coarse-fine boundary (Eq. 5b) for the fine mesh: per side, Mur or the
+// coarse tangential-E line before (old) and after (new) the coarse step.
+// With `recompute`, the new coarse values are evaluated from the coarse
+// level-n state (cm, cc, cR) with the coarse step's own arithmetic instead of
+// being read, so a fine sub-step need not wait for the coarse step.
+template <class T>
+struct Bnd {
+  int mode[4];              // BC_MUR or BC_CFB per side
+  const T* old_line[4];     // coarse tangential E at level n (strided)
+  const T* new_line[4];     // coarse tangential E at level n+1 (strided)
+  int stride[4];
+  int len[4];               // coarse samples along the line
+  int start[4];             // coarse index of the rectangle corner along the line
+  int at[4];                // coarse row (bottom/top) or column (left/right) of the line
+  int r;
+  T frac;                   // k / r of the fine sub-step
+  int recompute;
+  Mesh<T> cm;
+  Step<T> cc;
+  Restr<T> cR;
 };
 
 template <class T>
@@ -100,23 +108,6 @@ __device__ __forceinline__ T node_e2(const Mesh<T>& m, const Step<T>& c, int i, 
   return sx + sy;
 }
 
-// Eq. 5b for tangential sample q of side sd of the fine rectangle.
-template <class T>
-__device__ __forceinline__ T cfb_value(const Bnd<T>& b, int sd, int q) {
-  double pos = ((double)b.start[sd] + ((double)q + 0.5) / (double)b.r) - 0.5;
-  int i0 = (int)floor(pos);
-  double w = pos - (double)i0;
-  if (i0 < 0) { i0 = 0; w = 0.0; }
-  if (i0 > b.len[sd] - 2) { i0 = b.len[sd] - 2; w = 1.0; }
-  const T xp = (T)w, one = T(1);
-  const T* o = b.old_line[sd];
-  const T* nw = b.new_line[sd];
-  const int s = b.stride[sd];
-  T lo = o[i0 * s] * (one - xp) + o[(i0 + 1) * s] * xp;
-  T ln = nw[i0 * s] * (one - xp) + nw[(i0 + 1) * s] * xp;
-  return (one - b.frac) * lo + b.frac * ln;
-}
-
 constexpr int TX = 32, TY = 8;   // 2-D thread block of the node-wise kernels
 
 template <class T>
@@ -149,12 +140,75 @@ __device__ __forceinline__ T load_ey(const Mesh<T>& m, const Restr<T>& R, int i,
   return m.Ey[j * m.p + i];
 }
 
+// Coarse E^{n+1} of interior coarse edge Ex(i, J) / Ey(I, j) evaluated from
+// the level-n state with exactly the coarse step's operations (same values).
+template <class T>
+__device__ __forceinline__ T coarse_new_ex(const Bnd<T>& b, int i, int J) {
+  const Mesh<T>& m = b.cm;
+  const Step<T>& c = b.cc;
+  const int p = m.p;
+  const T exm = load_ex(m, b.cR, i, J - 1), exc = load_ex(m, b.cR, i, J), exn = load_ex(m, b.cR, i, J + 1);
+  const T eym = load_ey(m, b.cR, i, J - 1), eyc = load_ey(m, b.cR, i, J);
+  const T eymr = load_ey(m, b.cR, i + 1, J - 1), eyr = load_ey(m, b.cR, i + 1, J);
+  const T hzp = m.Hz[(J - 1) * p + i] - c.ch * ((eymr - eym) - (exc - exm));
+  const T hz = m.Hz[J * p + i] - c.ch * ((eyr - eyc) - (exn - exc));
+  const T v = c.va * m.vx[J * p + i] - c.vb * exc;
+  return exc + c.ce * (hz - hzp) + c.cj * (m.n[J * p + i] + m.n[J * p + i + 1]) * v;
+}
+
+template <class T>
+__device__ __forceinline__ T coarse_new_ey(const Bnd<T>& b, int I, int j) {
+  const Mesh<T>& m = b.cm;
+  const Step<T>& c = b.cc;
+  const int p = m.p;
+  const T eyl = load_ey(m, b.cR, I - 1, j), eyc = load_ey(m, b.cR, I, j), eyr = load_ey(m, b.cR, I + 1, j);
+  const T exl = load_ex(m, b.cR, I - 1, j), exln = load_ex(m, b.cR, I - 1, j + 1);
+  const T exc = load_ex(m, b.cR, I, j), exn = load_ex(m, b.cR, I, j + 1);
+  const T hzl = m.Hz[j * p + I - 1] - c.ch * ((eyc - eyl) - (exln - exl));
+  const T hz = m.Hz[j * p + I] - c.ch * ((eyr - eyc) - (exn - exc));
+  const T v = c.va * m.vy[j * p + I] - c.vb * (eyc + incident(c, I));
+  return eyc - c.ce * (hz - hzl) + c.cj * (m.n[j * p + I] + m.n[(j + 1) * p + I]) * v;
+}
+
+template <class T>
+__device__ __forceinline__ T coarse_new(const Bnd<T>& b, int sd, int k) {
+  if (sd == SIDE_BOTTOM || sd == SIDE_TOP) return coarse_new_ex(b, k, b.at[sd]);
+  return coarse_new_ey(b, b.at[sd], k);
+}
+
+// Eq. 5b for tangential sample q of side sd of the fine rectangle.  The
+// fine sample sits at coarse position start + (q + 1/2)/r - 1/2 along the
+// line = start + (2q + 1 - r)/(2r), split exactly into an index and a weight.
+template <class T>
+__device__ __forceinline__ T cfb_value(const Bnd<T>& b, int sd, int q) {
+  const int num = 2 * q + 1 - b.r, den = 2 * b.r;
+  const int fl = (num >= 0) ? num / den : -((-num + den - 1) / den);
+  int i0 = b.start[sd] + fl;
+  T xp = (T)(num - fl * den) / (T)den;
+  if (i0 < 0) { i0 = 0; xp = T(0); }
+  if (i0 > b.len[sd] - 2) { i0 = b.len[sd] - 2; xp = T(1); }
+  const T one = T(1);
+  const T* o = b.old_line[sd];
+  const int s = b.stride[sd];
+  const T lo = o[i0 * s] * (one - xp) + o[(i0 + 1) * s] * xp;
+  T n0, n1;
+  if (b.recompute) {
+    n0 = coarse_new(b, sd, i0);
+    n1 = coarse_new(b, sd, i0 + 1);
+  } else {
+    n0 = b.new_line[sd][i0 * s];
+    n1 = b.new_line[sd][(i0 + 1) * s];
+  }
+  const T ln = n0 * (one - xp) + n1 * xp;
+  return (one - b.frac) * lo + b.frac * ln;
+}
+
 // One EM step on one mesh, fused (a1-a6 + a5 of the level being left):
 //   Hz^{n+1/2} from E^n (Eq. 2); S2 += |E^n_total|^2 at the nodes when c.accum;
 //   v^{n+1/2} (Eq. 3); E^{n+1} on interior edges (Eq. 1); Mur on domain sides;
 //   Eq. 5b on coarse-fine sides.
-// E and H are double-buffered (read m.Ex/Ey/Hz, write dEx/dEy/dHz), so strips
-// may read neighbouring E^n and H^{n-1/2} while those are being advanced.
+// E, H and v are double-buffered (read m.*, write d*), so strips may read
+// neighbouring E^n, H^{n-1/2}, v^{n-1/2} while those are being advanced.
 //
 // Warp strips: lane L of a warp holds node column i = c0 - 1 + L with
 // c0 = STRIP_W * strip; lanes 1..STRIP_W own their columns, lane 0 and lane 31
@@ -167,14 +221,69 @@ __device__ __forceinline__ T load_ey(const Mesh<T>& m, const Restr<T>& R, int i,
 constexpr int STRIP_W = 30;
 constexpr int EM_WARPS = 4;   // warps per block (consecutive strips in y)
 
+// Everything one EM step of one mesh needs; `gx` strips across x, `nblk`
+// blocks (each EM_WARPS strips stacked in y).
 template <class T>
-__global__ void __launch_bounds__(32 * EM_WARPS) k_em(Mesh<T> m, T* __restrict__ dEx, T* __restrict__ dEy,
-                                                      T* __restrict__ dHz, Step<T> c, Bnd<T> b,
-                                                      Restr<T> R, int rows) {
+struct EmArgs {
+  Mesh<T> m;
+  T *dEx, *dEy, *dHz, *dvx, *dvy;
+  Step<T> c;
+  Bnd<T> b;
+  Restr<T> R;
+  int rows, gx, nblk;   // strips: rows per warp, strips across x, blocks
+  int ncfb;             // blocks that write the coarse-fine boundary E (Eq. 5b)
+};
+
+// Tangential E of the coarse-fine sides at the new level (a6, Eq. 5b), one
+// thread per boundary edge.  It depends only on the coarse lines, not on this
+// sub-step's interior update, so it runs as separate blocks of the same launch.
+template <class T>
+__device__ __forceinline__ void em_cfb(const EmArgs<T>& A, int blk) {
+  int q = blk * (32 * EM_WARPS) + (int)threadIdx.x;
+  const int nfx = A.m.nx, nfy = A.m.ny, p = A.m.p;
+  const int order[4] = {SIDE_BOTTOM, SIDE_TOP, SIDE_LEFT, SIDE_RIGHT};
+  for (int k = 0; k < 4; ++k) {
+    const int sd = order[k];
+    if (A.b.mode[sd] != BC_CFB) continue;
+    const int len = (sd == SIDE_BOTTOM || sd == SIDE_TOP) ? nfx : nfy;
+    if (q < len) {
+      const T v = cfb_value(A.b, sd, q);
+      if (sd == SIDE_BOTTOM) A.dEx[q] = v;
+      else if (sd == SIDE_TOP) A.dEx[nfy * p + q] = v;
+      else if (sd == SIDE_LEFT) A.dEy[q * p] = v;
+      else A.dEy[q * p + nfx] = v;
+      return;
+    }
+    q -= len;
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk);
+
+template <class T>
+__device__ __forceinline__ void em_segment(const EmArgs<T>& A, int blk) {
+  if (blk < A.nblk) em_strips(A, blk);
+  else em_cfb(A, blk - A.nblk);
+}
+
+template <class T>
+__device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
+  const Mesh<T>& m = A.m;
+  T* __restrict__ dEx = A.dEx;
+  T* __restrict__ dEy = A.dEy;
+  T* __restrict__ dHz = A.dHz;
+  T* __restrict__ dvx = A.dvx;
+  T* __restrict__ dvy = A.dvy;
+  const Step<T>& c = A.c;
+  const Bnd<T>& b = A.b;
+  const Restr<T>& R = A.R;
+  const int rows = A.rows;
   const int lane = threadIdx.x & 31;
-  const int sy = blockIdx.y * EM_WARPS + (threadIdx.x >> 5);
+  const int bx = blk % A.gx, byb = blk / A.gx;
+  const int sy = byb * EM_WARPS + (threadIdx.x >> 5);
   const int p = m.p, nx = m.nx, ny = m.ny;
-  const int i = blockIdx.x * STRIP_W - 1 + lane;
+  const int i = bx * STRIP_W - 1 + lane;
   const int j0 = sy * rows;
   if (j0 > ny) return;                       // whole warp leaves together
   const int j1 = min(j0 + rows, ny + 1);     // node rows [j0, j1)
@@ -248,49 +357,43 @@ __global__ void __launch_bounds__(32 * EM_WARPS) k_em(Mesh<T> m, T* __restrict__
       if (i < nx) {
         if (j > 0 && j < ny) {
           const T v = c.va * vxo - c.vb * exc;
-          m.vx[id] = v;
+          dvx[id] = v;
           const T en = exc + c.ce * (hz - hzp) + c.cj * (nc + ncr) * v;
           dEx[id] = en;
           if (j == 1 && b.mode[SIDE_BOTTOM] == BC_MUR) {
-            m.vx[i] = c.va * m.vx[i] - c.vb * exp_;
+            dvx[i] = c.va * m.vx[i] - c.vb * exp_;
             dEx[i] = exc + c.mur * (en - exp_);
           }
           if (j == ny - 1 && b.mode[SIDE_TOP] == BC_MUR) {
             const int ib = ny * p + i;
-            m.vx[ib] = c.va * m.vx[ib] - c.vb * exn;
+            dvx[ib] = c.va * m.vx[ib] - c.vb * exn;
             dEx[ib] = exc + c.mur * (en - exn);
           }
         } else {
           const int sd = (j == 0) ? SIDE_BOTTOM : SIDE_TOP;
-          if (b.mode[sd] == BC_CFB) {
-            m.vx[id] = c.va * vxo - c.vb * exc;
-            dEx[id] = cfb_value(b, sd, i);
-          }
+          if (b.mode[sd] == BC_CFB) dvx[id] = c.va * vxo - c.vb * exc;  // E: em_cfb
         }
       }
       // ---- y edge (i, j)
       if (j < ny) {
         if (i > 0 && i < nx) {
           const T v = c.va * vyo - c.vb * (eyc + inc);
-          m.vy[id] = v;
+          dvy[id] = v;
           const T en = eyc - c.ce * (hz - hzl) + c.cj * (nc + nn) * v;
           dEy[id] = en;
           if (i == 1 && b.mode[SIDE_LEFT] == BC_MUR) {
             const int ib = j * p;
-            m.vy[ib] = c.va * vyl - c.vb * (eyl + inc0);
+            dvy[ib] = c.va * vyl - c.vb * (eyl + inc0);
             dEy[ib] = eyc + c.mur * (en - eyl);
           }
           if (i == nx - 1 && b.mode[SIDE_RIGHT] == BC_MUR) {
             const int ib = j * p + nx;
-            m.vy[ib] = c.va * vyr - c.vb * (eyr + incn);
+            dvy[ib] = c.va * vyr - c.vb * (eyr + incn);
             dEy[ib] = eyc + c.mur * (en - eyr);
           }
         } else {
           const int sd = (i == 0) ? SIDE_LEFT : SIDE_RIGHT;
-          if (b.mode[sd] == BC_CFB) {
-            m.vy[id] = c.va * vyo - c.vb * (eyc + inc);
-            dEy[id] = cfb_value(b, sd, j);
-          }
+          if (b.mode[sd] == BC_CFB) dvy[id] = c.va * vyo - c.vb * (eyc + inc);  // E: em_cfb
         }
       }
     }
@@ -300,6 +403,21 @@ __global__ void __launch_bounds__(32 * EM_WARPS) k_em(Mesh<T> m, T* __restrict__
     hzp = hz;
     nc = nn;
   }
+}
+
+template <class T>
+__global__ void __launch_bounds__(32 * EM_WARPS) k_em(EmArgs<T> A) {
+  em_segment(A, blockIdx.x);
+}
+
+// Two independent EM steps in one launch (the coarse step and the first fine
+// sub-step, whose coarse boundary values are recomputed): blocks [0, A0.nblk)
+// run A0, the rest run A1.
+template <class T>
+__global__ void __launch_bounds__(32 * EM_WARPS) k_em2(EmArgs<T> A0, EmArgs<T> A1) {
+  const int n0 = A0.nblk + A0.ncfb;
+  if ((int)blockIdx.x < n0) em_segment(A0, blockIdx.x);
+  else em_segment(A1, blockIdx.x - n0);
 }
 
 // a8: coarse E edges of the closed rectangle (except tangential edges of

@@ -68,5 +68,5 @@ def test_create_rejects_bad_arguments_without_gpu(lib):
     assert b"aligned" in lib.dmr_last_error(None)
     st = lib.dmr_create(ctypes.byref(c), ctypes.c_void_p(256), 16, None, ctypes.byref(ctx))
     assert st == D.ECAPACITY
-    assert lib.dmr_kernel_class_name(0) == b"coarse_em"
+    assert lib.dmr_kernel_class_name(0) == b"em_step"
     assert lib.dmr_kernel_class_name(99) is None

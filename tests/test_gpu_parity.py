@@ -211,14 +211,15 @@ def test_timing_counts_launches():
     run.set_timing(True)
     run.advance(32)
     kt = run.kernel_times()
-    assert kt["coarse_em"][1] == 32 and kt["fine_em"][1] == 64
+    assert kt["em_step"][1] == 32 and kt["fine_em"][1] == 32
     assert all(v[0] > 0 for k, v in kt.items() if v[1] > 0)
     run.set_graphs(True)
     run.set_timing(True)
     run.advance(64)
     kt = run.kernel_times()
-    assert kt["fine_em"][1] == 128 and kt["fine_em"][0] > 0
-    # algorithmic bytes: 60 B per grid point per FP32 EM launch (44 B when no E^2 sample)
-    ms, n, nbytes = kt["coarse_em"]
-    pts = 41 * 33
-    assert nbytes == pytest.approx(64 * pts * 60 - 2 * pts * 16)
+    assert kt["fine_em"][1] == 64 and kt["fine_em"][0] > 0
+    # algorithmic bytes: 60 B per fine node per FP32 sub-step (44 B without an E^2 sample)
+    ms, n, nbytes = kt["fine_em"]
+    fr = run.get_patch()
+    pts = (2 * (fr[2] - fr[0]) + 1) * (2 * (fr[3] - fr[1]) + 1)
+    assert n == 64 and nbytes <= 64 * pts * 60
