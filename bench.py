@@ -198,6 +198,58 @@ def config_of(w, args):
             "global_batch": 1, "seq_len": None, "parallelism": "replicas" if args.gpus > 1 else "single"}
 
 
+def run_batch(args):
+    """64 independent DMR r=2 runs of uneven sizes and parameters (sizes in
+    {128..1024}^2, E0 3-8 MV/m, 100-760 Torr), one batched launch per phase,
+    one CUDA graph per period; the autotuner picks the strip height first."""
+    import torch
+    from paper_2105_13276_gb300 import build as B
+    B.build()
+    from paper_2105_13276_gb300 import dmr as D
+    from paper_2105_13276_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    ws = W.batch_runs(64)
+    for w in ws:
+        c = w["cfg"]
+        w["cfg"] = dict(c, patch_cap_cells=(c["r"] * c["nx"]) * (c["r"] * c["ny"]) // 4)
+    b = D.batch_from_workloads(ws, device=dev)
+    NT = ws[0]["cfg"]["steps_per_period"]
+    wps, trial = b.autotune()
+    b.advance(max(args.warmup, 1) * NT)
+    torch.cuda.synchronize(dev)
+    upp = sum(units_per_period(w["cfg"]) for w in ws)
+    K = args.steps
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    sampler = ClockSampler(gpu_index_for(0))
+    sampler.start()
+    l0 = b.launch_count()
+    torch.cuda.synchronize(dev)
+    for k in range(K):
+        evs[k][0].record(b.stream)
+        b.advance(NT)
+        evs[k][1].record(b.stream)
+        with torch.cuda.stream(b.stream):
+            flush.zero_()
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = sum(x.elapsed_time(y) for x, y in evs)
+    launches = b.launch_count() - l0
+    fine = [b.runs[q].stats()["fine_cells"] for q in range(len(ws))]
+    line = {"metric": METRIC, "value": K * upp / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": K, "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched: 64 DMR r=2 runs, coarse {128,256,512,1024}^2, E0 3-8 MV/m, "
+                                   "p 100-760 Torr (seed 13276)",
+                       "runs": len(ws), "coarse_cells_total": sum(w["cfg"]["nx"] * w["cfg"]["ny"] for w in ws),
+                       "autotuned_warps_per_sm": wps, "autotune_trial_ms": trial,
+                       "fine_cells_end_total": sum(fine),
+                       "l2": "flushed (256 MB write) between timed periods"},
+            "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -400,6 +452,8 @@ def main():
         raise SystemExit("--steps >= 1 and --warmup >= 0")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -200,6 +200,43 @@ int dmr_launch_count(const dmr_ctx* ctx, int64_t* launches);
 /* Wait for all work queued on the run's stream. */
 int dmr_sync(const dmr_ctx* ctx);
 
+/* ---- Batched runs (many independent breakdown runs advanced together) ----
+ * A batch holds n runs whose configurations may differ in size, E0, pressure
+ * and seeds but share precision, r (1 or even) and an even steps_per_period.
+ * Per coarse step one launch advances every run's coarse mesh and first fine
+ * sub-step, one launch each later fine sub-step; with graphs on (default)
+ * each period (EM steps of all runs, every run's continuity step, flags and
+ * totals) is one CUDA graph launch, and all control blocks come back in one
+ * read.  Set each run up through its borrowed context (dmr_batch_run:
+ * dmr_set_patch, dmr_seed_gaussian, dmr_write, dmr_read, dmr_stats) and
+ * advance only through dmr_batch_advance (DMR_ESTATE otherwise). */
+typedef struct dmr_batch dmr_batch;
+
+/* Workspace of a batch of n runs; 0 if invalid (dmr_batch_last_error(NULL)). */
+size_t dmr_batch_workspace_bytes(const dmr_config* cfgs, int32_t n);
+
+/* Create a batch in one caller-owned device buffer (256-byte aligned) on a
+ * non-default stream. */
+int dmr_batch_create(const dmr_config* cfgs, int32_t n, void* dev_workspace, size_t bytes,
+                     void* cuda_stream, dmr_batch** out);
+void dmr_batch_destroy(dmr_batch* b);
+
+/* Context of run k (owned by the batch: dmr_destroy ignores it); NULL if k is
+ * out of range. */
+dmr_ctx* dmr_batch_run(dmr_batch* b, int32_t k);
+
+/* Advance every run by n coarse steps (growth decided per run each period). */
+int dmr_batch_advance(dmr_batch* b, int64_t n_coarse_steps);
+int dmr_batch_set_graphs(dmr_batch* b, int enable);
+
+/* Autotuner (at a period boundary): times the batched EM launch for five
+ * strip heights (warps-per-SM targets 16, 32, 48, 64, 96) on the present
+ * state without changing it, keeps the fastest; returns the choice and the
+ * per-candidate launch times (ms). */
+int dmr_batch_autotune(dmr_batch* b, int32_t* warps_per_sm, double trial_ms[5]);
+int dmr_batch_launch_count(const dmr_batch* b, int64_t* launches);
+const char* dmr_batch_last_error(const dmr_batch* b);
+
 /* Electron total (per metre of depth) of one density map, without any
  * allocation.  The paper has no counterpart to this call: it exists for
  * callers that cannot allocate device memory at all -- a host application

@@ -100,6 +100,7 @@ struct Layout {
   size_t off_f[2][11] = {}, off_fS2[2] = {};  // Ex Ey Hz vx vy n, then Ex' Ey' Hz' vx' vy'
   size_t off_ftmp[3] = {};                // ntmp D nu
   size_t off_tab[4] = {};                 // ckx_c skx_c ckx_f skx_f
+  size_t off_ph[4] = {};                  // sin/cos of the phase per step: coarse, fine
   size_t off_mask = 0, off_part[4] = {}, off_ctl = 0, off_view = 0;
   size_t total = 0;
 };
@@ -138,6 +139,10 @@ int make_layout(const dmr_config* c, const Derived& d, Layout* L, std::string* e
   L->off_tab[1] = take((size_t)(nx + 1) * L->es);
   L->off_tab[2] = take((size_t)(r * nx + 1) * L->es);
   L->off_tab[3] = take((size_t)(r * nx + 1) * L->es);
+  L->off_ph[0] = take((size_t)c->steps_per_period * L->es);
+  L->off_ph[1] = take((size_t)c->steps_per_period * L->es);
+  L->off_ph[2] = take((size_t)r * c->steps_per_period * L->es);
+  L->off_ph[3] = take((size_t)r * c->steps_per_period * L->es);
   L->off_mask = take((size_t)(nx + 1) * (ny + 1));
   L->off_part[0] = take((size_t)L->nblk_c * 8);
   L->off_part[1] = take((size_t)std::max(L->nblk_f, 1) * 8);
@@ -286,6 +291,7 @@ struct Engine final : Base {
   bool rvalid = false;
   T *f_ntmp = nullptr, *f_D = nullptr, *f_nu = nullptr;
   T *ckx_c = nullptr, *skx_c = nullptr, *ckx_f = nullptr, *skx_f = nullptr;
+  T* ph[4] = {};             // sin, cos of w t per step of a period: coarse, fine
   uint8_t* mask = nullptr;
   double* part[4] = {};
   dmr::Ctl* ctl = nullptr;
@@ -312,6 +318,7 @@ struct Engine final : Base {
     }
     ckx_c = at<T>(L.off_tab[0]); skx_c = at<T>(L.off_tab[1]);
     ckx_f = at<T>(L.off_tab[2]); skx_f = at<T>(L.off_tab[3]);
+    for (int q = 0; q < 4; ++q) ph[q] = at<T>(L.off_ph[q]);
     mask = at<uint8_t>(L.off_mask);
     for (int q = 0; q < 4; ++q) part[q] = at<double>(L.off_part[q]);
     ctl = at<dmr::Ctl>(L.off_ctl);
@@ -341,6 +348,21 @@ struct Engine final : Base {
     }
     if ((s = ck(cudaMemcpyAsync(ckx_f, fc.data(), fc.size() * sizeof(T), cudaMemcpyHostToDevice, st), "upload tables"))) return s;
     if ((s = ck(cudaMemcpyAsync(skx_f, fs.data(), fs.size() * sizeof(T), cudaMemcpyHostToDevice, st), "upload tables"))) return s;
+    // phase tables: the sin / cos that make_step evaluates for each step of a period
+    for (int rr = 1; rr <= (cfg.r > 1 ? 2 : 1); ++rr) {
+      const int mr = rr == 1 ? 1 : cfg.r;
+      const int64_t N = (int64_t)mr * cfg.steps_per_period;
+      std::vector<T> ps(N), pcv(N);
+      for (int64_t q = 0; q < N; ++q) {
+        const double phase = 2.0 * PI * (double)q / (double)N;
+        ps[q] = (T)std::sin(phase);
+        pcv[q] = (T)std::cos(phase);
+      }
+      T* dsn = ph[rr == 1 ? 0 : 2];
+      T* dcs = ph[rr == 1 ? 1 : 3];
+      if ((s = ck(cudaMemcpyAsync(dsn, ps.data(), N * sizeof(T), cudaMemcpyHostToDevice, st), "upload phases"))) return s;
+      if ((s = ck(cudaMemcpyAsync(dcs, pcv.data(), N * sizeof(T), cudaMemcpyHostToDevice, st), "upload phases"))) return s;
+    }
     return ck(cudaStreamSynchronize(st), "init sync");
   }
 
@@ -349,9 +371,10 @@ struct Engine final : Base {
   // node rows per warp of the strip EM kernel: enough warps to fill the GPU
   // (about 48 per SM); small meshes get 1-2 rows per warp so a launch costs
   // about one memory latency, large ones up to 64 (the warm-up row is 1/rows)
+  int warps_per_sm = 48;     // strip-height policy (the batch autotuner may change it)
   int em_rows(int nx, int ny) const {
     const long long sx = (nx + 1 + dmr::STRIP_W - 1) / dmr::STRIP_W;
-    const long long target = (long long)num_sms * 48;
+    const long long target = (long long)num_sms * warps_per_sm;
     long long rows = (sx * (ny + 1) + target - 1) / target;
     return (int)std::min<long long>(64, std::max<long long>(1, rows));
   }
@@ -464,37 +487,32 @@ struct Engine final : Base {
     return A;
   }
 
-  // one coarse step from level mlev.  The coarse step (reading the restricted
-  // E of the previous step on the fly) and the first fine sub-step (which
-  // evaluates the coarse E^{n+1} on its boundary lines itself) are
-  // independent and share one launch; fine sub-steps 2..r follow.
-  int launch_coarse_step(int64_t mlev) {
+  // Arguments of the EM launches of coarse step mlev: the coarse step (Ac,
+  // phase k = 1 only) and fine sub-step k (Af), for coarse buffer parity cp,
+  // fine parity fp at the start of sub-step k, restriction state rv.
+  void em_args_for(int k, int64_t mlev, int cp, int fp, bool rv, dmr::EmArgs<T>* Ac,
+                   dmr::EmArgs<T>* Af) const {
     const int NT = cfg.steps_per_period, r = cfg.r;
-    const bool acc_c = (mlev % NT) != 0;
-    dmr::Step<T> sc = make_step(1, mlev, acc_c);
-    dmr::Bnd<T> bc{};
-    for (int q = 0; q < 4; ++q) bc.mode[q] = dmr::BC_MUR;
-    bc.r = 1;
+    dmr::Step<T> sc = make_step(1, mlev, (mlev % NT) != 0);
+    dmr::Mesh<T> src = C;
+    src.Ex = cE[cp][0]; src.Ey = cE[cp][1]; src.Hz = cE[cp][2]; src.vx = cE[cp][3]; src.vy = cE[cp][4];
+    T* const* cdst = cE[cp ^ 1];
     dmr::Restr<T> R{};
-    if (has_fine && rvalid) {
+    const dmr::Mesh<T> fsrc = fine_at(fp);
+    if (has_fine && rv) {
       R.on = 1;
       R.I0 = rect[0]; R.J0 = rect[1]; R.I1 = rect[2]; R.J1 = rect[3]; R.r = r;
       restr_bounds(&R.jlo, &R.jhi, &R.ilo, &R.ihi);
-      R.fEx = F[cur].Ex; R.fEy = F[cur].Ey; R.fp = F[cur].p;
+      R.fEx = fsrc.Ex; R.fEy = fsrc.Ey; R.fp = fsrc.p;   // fine level n (k = 1: the step's start)
     }
-    const dmr::Mesh<T> src = C;
-    T* cdst[5] = {cE[cpar ^ 1][0], cE[cpar ^ 1][1], cE[cpar ^ 1][2], cE[cpar ^ 1][3], cE[cpar ^ 1][4]};
-    const dmr::EmArgs<T> Ac = em_args(src, cdst, sc, bc, R);
-    const double cbytes = em_bytes((double)(C.nx + 1) * (C.ny + 1), acc_c);
-    if (!has_fine) {
-      int h = tbeg(0, cbytes);
-      dmr::k_em<T><<<Ac.nblk + Ac.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Ac);
-      tend(h);
-      counted(1);
-      flip_coarse();
-      return launched("coarse EM");
+    if (Ac) {
+      dmr::Bnd<T> bc{};
+      for (int q = 0; q < 4; ++q) bc.mode[q] = dmr::BC_MUR;
+      bc.r = 1;
+      *Ac = em_args(src, cdst, sc, bc, R);
+      Ac->kind = 0; Ac->N = NT; Ac->r = 1; Ac->ps = ph[0]; Ac->pc = ph[1];
     }
-    // Eq. 5b lines: coarse tangential E before (src) and after (cdst) the coarse step
+    if (!Af || !has_fine) return;
     dmr::Bnd<T> bf{};
     bf.r = r;
     for (int q = 0; q < 4; ++q) {
@@ -521,17 +539,50 @@ struct Engine final : Base {
     bf.cm = src;
     bf.cc = sc;
     bf.cR = R;
+    bf.cps = ph[0]; bf.cpc = ph[1]; bf.cN = NT;
+    const int64_t mf = (int64_t)r * mlev + (k - 1);
+    dmr::Step<T> sf = make_step(r, mf, (mf % ((int64_t)r * NT)) != 0);
+    bf.frac = (T)((double)k / (double)r);
+    bf.recompute = k == 1 ? 1 : 0;
+    T* fdst[5] = {fineE(cur, fp ^ 1, 0), fineE(cur, fp ^ 1, 1), fineE(cur, fp ^ 1, 2),
+                  fineE(cur, fp ^ 1, 3), fineE(cur, fp ^ 1, 4)};
     const dmr::Restr<T> none{};
+    *Af = em_args(fsrc, fdst, sf, bf, none);
+    Af->kind = 1; Af->N = r * NT; Af->r = r; Af->ps = ph[2]; Af->pc = ph[3];
+  }
+
+  // fine mesh view with E/H/v of parity fp
+  dmr::Mesh<T> fine_at(int fp) const {
+    dmr::Mesh<T> f = F[cur];
+    f.Ex = fineE(cur, fp, 0); f.Ey = fineE(cur, fp, 1); f.Hz = fineE(cur, fp, 2);
+    f.vx = fineE(cur, fp, 3); f.vy = fineE(cur, fp, 4);
+    return f;
+  }
+
+  // one coarse step from level mlev.  The coarse step (reading the restricted
+  // E of the previous step on the fly) and the first fine sub-step (which
+  // evaluates the coarse E^{n+1} on its boundary lines itself) are
+  // independent and share one launch; fine sub-steps 2..r follow.
+  int launch_coarse_step(int64_t mlev) {
+    const int NT = cfg.steps_per_period, r = cfg.r;
+    const bool acc_c = (mlev % NT) != 0;
+    dmr::EmArgs<T> Ac, Af;
+    em_args_for(1, mlev, cpar, fpar, rvalid, &Ac, has_fine ? &Af : nullptr);
+    const double cbytes = em_bytes((double)(C.nx + 1) * (C.ny + 1), acc_c);
+    if (!has_fine) {
+      int h = tbeg(0, cbytes);
+      dmr::k_em<T><<<Ac.nblk + Ac.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Ac);
+      tend(h);
+      counted(1);
+      flip_coarse();
+      return launched("coarse EM");
+    }
+    const int cp0 = cpar;
     const double fn = (double)(F[cur].nx + 1) * (F[cur].ny + 1);
     for (int k = 1; k <= r; ++k) {
       const int64_t mf = (int64_t)r * mlev + (k - 1);
       const bool acc_f = (mf % ((int64_t)r * NT)) != 0;
-      dmr::Step<T> sf = make_step(r, mf, acc_f);
-      bf.frac = (T)((double)k / (double)r);
-      bf.recompute = k == 1 ? 1 : 0;
-      T* fdst[5] = {fineE(cur, fpar ^ 1, 0), fineE(cur, fpar ^ 1, 1), fineE(cur, fpar ^ 1, 2),
-                    fineE(cur, fpar ^ 1, 3), fineE(cur, fpar ^ 1, 4)};
-      const dmr::EmArgs<T> Af = em_args(F[cur], fdst, sf, bf, none);
+      if (k > 1) em_args_for(k, mlev, cp0, fpar, rvalid, nullptr, &Af);
       if (k == 1) {
         int h = tbeg(0, cbytes + em_bytes(fn, acc_f));
         dmr::k_em2<T><<<Ac.nblk + Ac.ncfb + Af.nblk + Af.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Ac, Af);
@@ -642,6 +693,11 @@ struct Engine final : Base {
     if (int s = ck(cudaMemcpyAsync(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, st), "read control block")) return s;
     if (int s = ck(cudaStreamSynchronize(st), "period sync")) return s;
     harvest_period(graph_ran);
+    return period_decide(hc);
+  }
+
+  // stability guard and growth decision from a period's control block
+  int period_decide(const dmr::Ctl& hc) {
     if (hc.err) return fail(DMR_EUNSTABLE, "NaN in the density or totals at a period end");
     const double wp_lim = (2.0 / (has_fine ? d.dtf : d.dtc));
     const double n_lim = wp_lim * wp_lim * ME * EPS0 / (QE * QE);
@@ -899,11 +955,416 @@ struct Engine final : Base {
   }
 };
 
+// --------------------------------------------------------------------------
+// Batched runs: independent DMR runs (sizes, E0, pressure, seeds may differ;
+// precision, r and N_T shared) advanced together.  Per coarse step one launch
+// covers every run's coarse step and first fine sub-step (segment tables in
+// device memory; the level-dependent values are looked up in the kernel), one
+// launch per later fine sub-step; each run's period-end kernels are parallel
+// branches of the same per-period CUDA graph; one gather kernel collects the
+// runs' control blocks for a single read-back.
+__global__ void k_gather_ctl(const dmr::Ctl* const* src, dmr::Ctl* dst, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = *src[i];
+}
+
+struct BatchBase {
+  std::string err;
+  int64_t launches = 0;
+  int tuned_wps = 0;
+  double tune_ms[8] = {};
+  virtual ~BatchBase() {}
+  virtual int advance(int64_t n) = 0;
+  virtual int set_graphs(bool on) = 0;
+  virtual int autotune() = 0;
+  virtual int nruns() const = 0;
+  virtual Base* run(int k) = 0;
+  int fail(int code, const std::string& msg) { err = msg; return code; }
+};
+
+// bytes of the batch's own tables (segment arguments, offsets, control blocks)
+size_t batch_table_bytes(int n, int r, int es) {
+  const size_t args = es == 4 ? sizeof(dmr::EmArgs<float>) : sizeof(dmr::EmArgs<double>);
+  const size_t nseg = (size_t)4 * 2 * n + (size_t)2 * (r > 1 ? r - 1 : 0) * n;
+  const size_t ntab = 4 + 2 * (size_t)(r > 1 ? r - 1 : 0);
+  return up(nseg * args, 256) + up((nseg + ntab) * sizeof(int), 256) +
+         up((size_t)n * sizeof(void*), 256) + up((size_t)n * sizeof(dmr::Ctl), 256);
+}
+
+template <class T>
+struct Batch final : BatchBase {
+  std::vector<Engine<T>*> runs;
+  cudaStream_t st = nullptr;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  char* tdev = nullptr;       // table area (device)
+  size_t tbytes = 0;
+  dmr::Ctl** ctl_ptrs = nullptr;
+  dmr::Ctl* ctl_all = nullptr;
+  int NT = 0, r = 1;
+  int64_t m = 0;
+  bool graphs = true;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t graph_nodes = 0;
+  struct Tab { const dmr::EmArgs<T>* args; const int* off; int nseg; int nblk; };
+  Tab t1[2][2] = {};          // phase 1: [first step after a table build][coarse parity]
+  std::vector<Tab> tk[2];     // phase k = 2..r: [coarse parity][k - 2]
+  std::vector<int> shape;     // segment block counts the graph was captured with
+  bool first_pending = true;
+
+  ~Batch() override {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    for (auto s_ : side) cudaStreamDestroy(s_);
+    for (auto e : join) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    for (auto e : runs) delete e;
+  }
+  int nruns() const override { return (int)runs.size(); }
+  Base* run(int k) override { return runs[k]; }
+  int ck(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return DMR_OK;
+    return fail(DMR_ECUDA, fmt("%s: %s", what, cudaGetErrorString(e)));
+  }
+  int run_fail(int k, int code) { return fail(code, fmt("run %d: %s", k, runs[k]->err.c_str())); }
+
+  int init() {
+    side.resize(runs.size());
+    join.resize(runs.size());
+    for (size_t q = 0; q < runs.size(); ++q) {
+      if (int s = ck(cudaStreamCreateWithFlags(&side[q], cudaStreamNonBlocking), "stream")) return s;
+      if (int s = ck(cudaEventCreateWithFlags(&join[q], cudaEventDisableTiming), "event")) return s;
+    }
+    if (int s = ck(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming), "event")) return s;
+    std::vector<dmr::Ctl*> ptrs(runs.size());
+    for (size_t q = 0; q < runs.size(); ++q) ptrs[q] = runs[q]->ctl;
+    if (int s = ck(cudaMemcpyAsync(ctl_ptrs, ptrs.data(), ptrs.size() * sizeof(void*),
+                                   cudaMemcpyHostToDevice, st), "upload control pointers")) return s;
+    return ck(cudaStreamSynchronize(st), "batch init sync");
+  }
+
+  // (re)build and upload the segment tables from the runs' present state
+  int build_tables() {
+    std::vector<dmr::EmArgs<T>> segs;
+    std::vector<int> offs;
+    std::vector<std::pair<size_t, size_t>> marks;   // (first segment, first offset) per table
+    auto add_table = [&](std::vector<dmr::EmArgs<T>>& v) {
+      marks.push_back({segs.size(), offs.size()});
+      int acc = 0;
+      for (auto& a : v) { offs.push_back(acc); acc += a.nblk + a.ncfb; segs.push_back(a); }
+      offs.push_back(acc);
+    };
+    for (int first = 0; first < 2; ++first)
+      for (int cp = 0; cp < 2; ++cp) {
+        std::vector<dmr::EmArgs<T>> v;
+        for (auto* e : runs) {
+          dmr::EmArgs<T> Ac, Af;
+          const bool rv = first ? e->rvalid : e->has_fine;
+          e->em_args_for(1, m, cp, 0, rv, &Ac, e->has_fine ? &Af : nullptr);
+          v.push_back(Ac);
+          if (e->has_fine) v.push_back(Af);
+        }
+        add_table(v);
+      }
+    for (int cp = 0; cp < 2; ++cp)
+      for (int k = 2; k <= r; ++k) {
+        std::vector<dmr::EmArgs<T>> v;
+        for (auto* e : runs) {
+          if (!e->has_fine) continue;
+          dmr::EmArgs<T> Af;
+          e->em_args_for(k, m, cp, (k - 1) & 1, true, nullptr, &Af);
+          v.push_back(Af);
+        }
+        add_table(v);
+      }
+    const size_t abytes = up(segs.size() * sizeof(dmr::EmArgs<T>), 256);
+    const size_t obytes = offs.size() * sizeof(int);
+    if (abytes + obytes > tbytes) return fail(DMR_ECAPACITY, "batch tables exceed their area");
+    std::vector<char> stage(abytes + obytes, 0);
+    memcpy(stage.data(), segs.data(), segs.size() * sizeof(dmr::EmArgs<T>));
+    memcpy(stage.data() + abytes, offs.data(), obytes);
+    if (int s = ck(cudaMemcpyAsync(tdev, stage.data(), stage.size(), cudaMemcpyHostToDevice, st),
+                   "upload batch tables")) return s;
+    if (int s = ck(cudaStreamSynchronize(st), "table sync")) return s;
+    const auto* A = reinterpret_cast<const dmr::EmArgs<T>*>(tdev);
+    const int* O = reinterpret_cast<const int*>(tdev + abytes);
+    std::vector<int> new_shape;
+    auto tab = [&](size_t t) {
+      Tab x;
+      const size_t s0 = marks[t].first, o0 = marks[t].second;
+      const size_t s1 = t + 1 < marks.size() ? marks[t + 1].first : segs.size();
+      x.args = A + s0;
+      x.off = O + o0;
+      x.nseg = (int)(s1 - s0);
+      x.nblk = offs[o0 + x.nseg];
+      new_shape.push_back(x.nblk);
+      return x;
+    };
+    size_t t = 0;
+    for (int first = 0; first < 2; ++first)
+      for (int cp = 0; cp < 2; ++cp) t1[first][cp] = tab(t++);
+    for (int cp = 0; cp < 2; ++cp) {
+      tk[cp].clear();
+      for (int k = 2; k <= r; ++k) tk[cp].push_back(tab(t++));
+    }
+    if (new_shape != shape) {
+      shape = new_shape;
+      if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+    }
+    // the first-step tables differ from the steady ones while a run's fine
+    // mesh has not stepped since it was (re)built
+    first_pending = false;
+    for (auto* e : runs) first_pending |= e->has_fine && !e->rvalid;
+    return DMR_OK;
+  }
+
+  int launch_em(const Tab& t, int64_t level, int k) {
+    if (t.nseg == 0 || t.nblk == 0) return 0;
+    dmr::k_em_batch<T><<<t.nblk, 32 * dmr::EM_WARPS, 0, st>>>(t.args, t.off, t.nseg, (long long)level, k);
+    return 1;
+  }
+
+  // EM launches of coarse step q of the period starting at level m0
+  int launch_step(int64_t m0, int q, bool first) {
+    const int cp = (int)((m0 + q) & 1);
+    int n = launch_em(t1[first ? 1 : 0][cp], m0 + q, 1);
+    for (int k = 2; k <= r; ++k) n += launch_em(tk[cp][k - 2], m0 + q, k);
+    return n;
+  }
+
+  int check_state() {
+    for (size_t q = 0; q < runs.size(); ++q) {
+      auto* e = runs[q];
+      if (e->m != m || e->cpar != (int)(m & 1) || (e->has_fine && e->fpar != 0))
+        return fail(DMR_ESTATE, fmt("run %d was advanced outside the batch", (int)q));
+    }
+    return DMR_OK;
+  }
+
+  // host state of every run after one coarse step done by the batch
+  void after_step() {
+    for (auto* e : runs) {
+      e->flip_coarse();
+      if (e->has_fine) {
+        for (int k = 0; k < r; ++k) e->flip_fine();
+        e->rvalid = true;
+      }
+      ++e->m;
+    }
+    ++m;
+  }
+
+  int period_end_direct() {
+    for (auto* e : runs)
+      if (int s = e->launch_period_end(m)) return fail(s, e->err);
+    k_gather_ctl<<<(int)((runs.size() + 127) / 128), 128, 0, st>>>(ctl_ptrs, ctl_all, (int)runs.size());
+    launches += 1;
+    return decide();
+  }
+
+  // read all control blocks once, then each run's stability guard and growth
+  int decide() {
+    std::vector<dmr::Ctl> hc(runs.size());
+    if (int s = ck(cudaMemcpyAsync(hc.data(), ctl_all, hc.size() * sizeof(dmr::Ctl),
+                                   cudaMemcpyDeviceToHost, st), "read control blocks")) return s;
+    if (int s = ck(cudaStreamSynchronize(st), "period sync")) return s;
+    bool changed = false;
+    for (size_t q = 0; q < runs.size(); ++q) {
+      auto* e = runs[q];
+      int old[4] = {e->rect[0], e->rect[1], e->rect[2], e->rect[3]};
+      if (int s = e->period_decide(hc[q])) return run_fail((int)q, s);
+      for (int k = 0; k < 4; ++k) changed |= old[k] != e->rect[k];
+    }
+    // a grown rectangle changes the period-end launches captured in the graph
+    if (changed && gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+    if (changed || first_pending) return build_tables();
+    return DMR_OK;
+  }
+
+  int capture() {
+    if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+    cudaGraph_t g = nullptr;
+    if (int s = ck(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture")) return s;
+    int s = DMR_OK;
+    graph_nodes = 0;
+    for (int q = 0; q < NT; ++q) graph_nodes += launch_step(m, q, q == 0 && first_pending);
+    // period ends: one parallel branch per run
+    cudaEventRecord(fork, st);
+    std::vector<bool> rv(runs.size());
+    for (size_t q = 0; q < runs.size() && !s; ++q) {
+      auto* e = runs[q];
+      cudaStreamWaitEvent(side[q], fork, 0);
+      e->st = side[q];
+      e->capturing = true;
+      e->graph_nodes = 0;
+      rv[q] = e->rvalid;
+      if (e->has_fine) e->rvalid = true;     // the fine mesh will have stepped by then
+      s = e->launch_period_end(m + NT);
+      graph_nodes += e->graph_nodes;
+      e->capturing = false;
+      e->rvalid = rv[q];
+      e->st = st;
+      cudaEventRecord(join[q], side[q]);
+      cudaStreamWaitEvent(st, join[q], 0);
+    }
+    k_gather_ctl<<<(int)((runs.size() + 127) / 128), 128, 0, st>>>(ctl_ptrs, ctl_all, (int)runs.size());
+    graph_nodes += 1;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (s) { if (g) cudaGraphDestroy(g); return fail(s, "period-end capture failed"); }
+    if (e != cudaSuccess) return ck(e, "end capture");
+    e = cudaGraphInstantiate(&gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { gexec = nullptr; return ck(e, "graph instantiate"); }
+    gexec_first = first_pending;
+    return DMR_OK;
+  }
+  bool gexec_first = false;
+
+  int advance(int64_t n) override {
+    if (n < 0) return fail(DMR_EINVAL, "negative step count");
+    if (int s = check_state()) return s;
+    if (shape.empty())
+      if (int s = build_tables()) return s;
+    while (n > 0) {
+      const int q0 = (int)(m % NT);
+      if (graphs && q0 == 0 && n >= NT) {
+        if (gexec && first_pending && !gexec_first) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+        if (!gexec)
+          if (int s = capture()) return s;
+        if (int s = ck(cudaGraphLaunch(gexec, st), "cudaGraphLaunch")) return s;
+        launches += graph_nodes;
+        for (int q = 0; q < NT; ++q) after_step();
+        n -= NT;
+        if (int s = decide()) return s;
+        continue;
+      }
+      launches += launch_step(m - q0, q0, q0 == 0 && first_pending);
+      if (int s = ck(cudaGetLastError(), "batched EM launch")) return s;
+      after_step();
+      --n;
+      if (m % NT == 0) {
+        if (int s = period_end_direct()) return s;
+      }
+    }
+    return DMR_OK;
+  }
+
+  int set_graphs(bool on) override {
+    graphs = on;
+    if (!on && gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+    return DMR_OK;
+  }
+
+  // Autotuner: the strip height (rows per warp) follows a warps-per-SM target;
+  // each candidate is timed on the phase-1 launch of the current step.  At a
+  // period boundary that launch adds no E^2 sample and writes only the
+  // next-level buffers, so repeating it leaves the run unchanged.
+  int autotune() override {
+    if (int s = check_state()) return s;
+    if (m % NT != 0) return fail(DMR_ESTATE, "autotune at a period boundary");
+    const int cand[5] = {16, 32, 48, 64, 96};
+    cudaEvent_t a, b;
+    if (int s = ck(cudaEventCreate(&a), "event")) return s;
+    if (int s = ck(cudaEventCreate(&b), "event")) { cudaEventDestroy(a); return s; }
+    double best = 1e30;
+    int best_w = 48;
+    for (int c = 0; c < 5; ++c) {
+      for (auto* e : runs) e->warps_per_sm = cand[c];
+      if (int s = build_tables()) { cudaEventDestroy(a); cudaEventDestroy(b); return s; }
+      const Tab& t = t1[first_pending ? 1 : 0][m & 1];
+      for (int w = 0; w < 3; ++w) launch_em(t, m, 1);
+      cudaEventRecord(a, st);
+      for (int w = 0; w < 10; ++w) launch_em(t, m, 1);
+      cudaEventRecord(b, st);
+      if (int s = ck(cudaEventSynchronize(b), "autotune sync")) { cudaEventDestroy(a); cudaEventDestroy(b); return s; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      tune_ms[c] = ms / 10.0;
+      launches += 13;
+      if (tune_ms[c] < best) { best = tune_ms[c]; best_w = cand[c]; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    for (auto* e : runs) e->warps_per_sm = best_w;
+    tuned_wps = best_w;
+    return build_tables();
+  }
+};
+
 }  // namespace
 
 struct dmr_ctx {
   Base* e;
+  bool borrowed = false;   // a run of a batch: owned by the batch
 };
+
+struct dmr_batch {
+  BatchBase* b;
+  std::vector<dmr_ctx> ctxs;
+};
+
+namespace {
+int batch_check(const dmr_config* cfgs, int n, std::vector<Derived>* ds, std::vector<Layout>* ls,
+                size_t* total, std::string* err) {
+  if (!cfgs || n < 1) { *err = "need at least one configuration"; return DMR_EINVAL; }
+  ds->resize(n);
+  ls->resize(n);
+  size_t tot = 0;
+  for (int q = 0; q < n; ++q) {
+    std::string e;
+    if (int s = derive(&cfgs[q], &(*ds)[q], &e)) { *err = fmt("run %d: %s", q, e.c_str()); return s; }
+    if (int s = make_layout(&cfgs[q], (*ds)[q], &(*ls)[q], &e)) { *err = fmt("run %d: %s", q, e.c_str()); return s; }
+    if (cfgs[q].precision != cfgs[0].precision || cfgs[q].r != cfgs[0].r ||
+        cfgs[q].steps_per_period != cfgs[0].steps_per_period) {
+      *err = "runs of a batch share precision, r and steps_per_period";
+      return DMR_EINVAL;
+    }
+    tot += up((*ls)[q].total, 256);
+  }
+  if (cfgs[0].steps_per_period % 2 != 0 || (cfgs[0].r > 1 && cfgs[0].r % 2 != 0)) {
+    *err = "a batch needs an even steps_per_period and r = 1 or even";
+    return DMR_EINVAL;
+  }
+  *total = batch_table_bytes(n, cfgs[0].r, cfgs[0].precision == 1 ? 4 : 8) + tot;
+  return DMR_OK;
+}
+
+template <class T>
+int batch_make(const dmr_config* cfgs, int n, const std::vector<Derived>& ds,
+               const std::vector<Layout>& ls, char* ws, cudaStream_t st, BatchBase** out,
+               std::string* err) {
+  auto* b = new (std::nothrow) Batch<T>();
+  if (!b) { *err = "out of host memory"; return DMR_EINVAL; }
+  b->st = st;
+  b->NT = cfgs[0].steps_per_period;
+  b->r = cfgs[0].r;
+  const size_t es = cfgs[0].precision == 1 ? 4 : 8;
+  const size_t tb = batch_table_bytes(n, b->r, (int)es);
+  // table area: segment arguments and offsets, then control pointers and blocks
+  const size_t ctl_bytes = up((size_t)n * sizeof(dmr::Ctl), 256);
+  const size_t ptr_bytes = up((size_t)n * sizeof(void*), 256);
+  b->tdev = ws;
+  b->tbytes = tb - ctl_bytes - ptr_bytes;
+  b->ctl_ptrs = reinterpret_cast<dmr::Ctl**>(ws + b->tbytes);
+  b->ctl_all = reinterpret_cast<dmr::Ctl*>(ws + b->tbytes + ptr_bytes);
+  size_t o = tb;
+  for (int q = 0; q < n; ++q) {
+    auto* e = new (std::nothrow) Engine<T>();
+    if (!e) { delete b; *err = "out of host memory"; return DMR_EINVAL; }
+    e->cfg = cfgs[q];
+    e->d = ds[q];
+    e->L = ls[q];
+    e->ws = ws + o;
+    e->st = st;
+    o += up(ls[q].total, 256);
+    b->runs.push_back(e);
+    if (int s = e->init()) { *err = fmt("run %d: %s", q, e->err.c_str()); delete b; return s; }
+  }
+  if (int s = b->init()) { *err = b->err; delete b; return s; }
+  *out = b;
+  return DMR_OK;
+}
+}  // namespace
 
 extern "C" {
 
@@ -944,7 +1405,7 @@ int dmr_create(const dmr_config* cfg, void* ws, size_t bytes, void* stream, dmr_
 }
 
 void dmr_destroy(dmr_ctx* ctx) {
-  if (!ctx) return;
+  if (!ctx || ctx->borrowed) return;
   delete ctx->e;
   delete ctx;
 }
@@ -1054,6 +1515,82 @@ int dmr_launch_count(const dmr_ctx* ctx, int64_t* n) {
 int dmr_sync(const dmr_ctx* ctx) {
   CTX_OR_FAIL(ctx);
   return ctx->e->ck(cudaStreamSynchronize(ctx->e->st), "sync");
+}
+
+size_t dmr_batch_workspace_bytes(const dmr_config* cfgs, int32_t n) {
+  std::vector<Derived> ds;
+  std::vector<Layout> ls;
+  size_t total = 0;
+  std::string err;
+  if (batch_check(cfgs, n, &ds, &ls, &total, &err)) { g_err = err; return 0; }
+  return total;
+}
+
+int dmr_batch_create(const dmr_config* cfgs, int32_t n, void* ws, size_t bytes, void* stream,
+                     dmr_batch** out) {
+  if (!out) { g_err = "null output pointer"; return DMR_EINVAL; }
+  *out = nullptr;
+  std::vector<Derived> ds;
+  std::vector<Layout> ls;
+  size_t total = 0;
+  std::string err;
+  if (int s = batch_check(cfgs, n, &ds, &ls, &total, &err)) { g_err = err; return s; }
+  if (!ws || ((uintptr_t)ws & 255u)) { g_err = "workspace must be a 256-byte aligned device pointer"; return DMR_EINVAL; }
+  if (bytes < total) { g_err = fmt("workspace too small: %zu < %zu bytes", bytes, total); return DMR_ECAPACITY; }
+  if (!stream) { g_err = "a batch needs a non-default stream (it is captured in CUDA graphs)"; return DMR_EINVAL; }
+  BatchBase* b = nullptr;
+  const int s = cfgs[0].precision == 1
+                    ? batch_make<float>(cfgs, n, ds, ls, (char*)ws, (cudaStream_t)stream, &b, &err)
+                    : batch_make<double>(cfgs, n, ds, ls, (char*)ws, (cudaStream_t)stream, &b, &err);
+  if (s) { g_err = err; return s; }
+  dmr_batch* h = new (std::nothrow) dmr_batch{b, {}};
+  if (!h) { delete b; g_err = "out of host memory"; return DMR_EINVAL; }
+  h->ctxs.resize(n);
+  for (int q = 0; q < n; ++q) { h->ctxs[q].e = b->run(q); h->ctxs[q].borrowed = true; }
+  *out = h;
+  return DMR_OK;
+}
+
+void dmr_batch_destroy(dmr_batch* b) {
+  if (!b) return;
+  delete b->b;
+  delete b;
+}
+
+dmr_ctx* dmr_batch_run(dmr_batch* b, int32_t k) {
+  if (!b || k < 0 || k >= b->b->nruns()) return nullptr;
+  return &b->ctxs[k];
+}
+
+int dmr_batch_advance(dmr_batch* b, int64_t n) {
+  if (!b) { g_err = "null batch"; return DMR_EINVAL; }
+  return b->b->advance(n);
+}
+
+int dmr_batch_set_graphs(dmr_batch* b, int enable) {
+  if (!b) { g_err = "null batch"; return DMR_EINVAL; }
+  return b->b->set_graphs(enable != 0);
+}
+
+int dmr_batch_autotune(dmr_batch* b, int32_t* warps_per_sm, double trial_ms[5]) {
+  if (!b) { g_err = "null batch"; return DMR_EINVAL; }
+  const int s = b->b->autotune();
+  if (warps_per_sm) *warps_per_sm = b->b->tuned_wps;
+  if (trial_ms)
+    for (int q = 0; q < 5; ++q) trial_ms[q] = b->b->tune_ms[q];
+  return s;
+}
+
+int dmr_batch_launch_count(const dmr_batch* b, int64_t* n) {
+  if (!b || !n) { g_err = "null argument"; return DMR_EINVAL; }
+  *n = b->b->launches;
+  for (int q = 0; q < b->b->nruns(); ++q) *n += b->b->run(q)->launches;
+  return DMR_OK;
+}
+
+const char* dmr_batch_last_error(const dmr_batch* b) {
+  if (!b) return g_err.c_str();
+  return b->b->err.c_str();
 }
 
 }  // extern "C"

@@ -71,6 +71,9 @@ struct Bnd {
   Mesh<T> cm;
   Step<T> cc;
   Restr<T> cR;
+  // batched launches: sin/cos of the coarse phase per step of a period
+  const T *cps, *cpc;
+  int cN;
 };
 
 template <class T>
@@ -232,7 +235,31 @@ struct EmArgs {
   Restr<T> R;
   int rows, gx, nblk;   // strips: rows per warp, strips across x, blocks
   int ncfb;             // blocks that write the coarse-fine boundary E (Eq. 5b)
+  // batched launches: the level-dependent fields (phase, E^2 sample, Eq. 5b
+  // time weight) are filled in the kernel from the step index
+  int kind;             // 0 coarse step, 1 fine sub-step
+  int N, r;             // steps per period of this mesh, refinement factor
+  const T *ps, *pc;     // sin / cos of w t for each step of a period
 };
+
+// Fill the level-dependent fields of a batched segment for coarse step m,
+// sub-step k (1..r): the same values a single-run launch computes on the host.
+template <class T>
+__device__ __forceinline__ void em_set_level(EmArgs<T>& A, long long m, int k) {
+  const long long level = A.kind == 0 ? m : (long long)A.r * m + (k - 1);
+  const int q = (int)(level % A.N);
+  A.c.sphi = A.ps[q];
+  A.c.cphi = A.pc[q];
+  A.c.accum = q != 0;
+  if (A.kind == 1) {
+    A.b.frac = (T)((double)k / (double)A.r);
+    A.b.recompute = k == 1;
+    const int qc = (int)(m % A.b.cN);
+    A.b.cc.sphi = A.b.cps[qc];
+    A.b.cc.cphi = A.b.cpc[qc];
+    A.b.cc.accum = qc != 0;
+  }
+}
 
 // Tangential E of the coarse-fine sides at the new level (a6, Eq. 5b), one
 // thread per boundary edge.  It depends only on the coarse lines, not on this
@@ -413,6 +440,34 @@ __global__ void __launch_bounds__(32 * EM_WARPS) k_em(EmArgs<T> A) {
 // Two independent EM steps in one launch (the coarse step and the first fine
 // sub-step, whose coarse boundary values are recomputed): blocks [0, A0.nblk)
 // run A0, the rest run A1.
+// Batched EM launch: segment s (one mesh of one run) owns blocks
+// [off[s], off[s+1]); its arguments come from a table in device memory.
+template <class T>
+__global__ void __launch_bounds__(32 * EM_WARPS) k_em_batch(const EmArgs<T>* __restrict__ tab,
+                                                            const int* __restrict__ off, int nseg,
+                                                            long long m, int k) {
+  __shared__ EmArgs<T> A;
+  __shared__ int seg;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    seg = lo;
+  }
+  __syncthreads();
+  {
+    const int* src = reinterpret_cast<const int*>(tab + seg);
+    int* dst = reinterpret_cast<int*>(&A);
+    for (int q = threadIdx.x; q < (int)(sizeof(EmArgs<T>) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) em_set_level(A, m, k);
+  __syncthreads();
+  em_segment(A, (int)blockIdx.x - off[seg]);
+}
+
 template <class T>
 __global__ void __launch_bounds__(32 * EM_WARPS) k_em2(EmArgs<T> A0, EmArgs<T> A1) {
   const int n0 = A0.nblk + A0.ncfb;

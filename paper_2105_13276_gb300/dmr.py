@@ -78,6 +78,15 @@ def load():
         "dmr_launch_count": (c_int, [P, POINTER(c_int64)]),
         "dmr_sync": (c_int, [P]),
         "dmr_electron_total_noalloc": (c_int, [P, c_int32, c_int32, c_int32, c_double, P, P]),
+        "dmr_batch_workspace_bytes": (c_size_t, [POINTER(DmrConfig), c_int32]),
+        "dmr_batch_create": (c_int, [POINTER(DmrConfig), c_int32, P, c_size_t, P, POINTER(P)]),
+        "dmr_batch_destroy": (None, [P]),
+        "dmr_batch_run": (P, [P, c_int32]),
+        "dmr_batch_advance": (c_int, [P, c_int64]),
+        "dmr_batch_set_graphs": (c_int, [P, c_int]),
+        "dmr_batch_autotune": (c_int, [P, POINTER(c_int32), POINTER(c_double)]),
+        "dmr_batch_launch_count": (c_int, [P, POINTER(c_int64)]),
+        "dmr_batch_last_error": (c_char_p, [P]),
         "dmr_noalloc_last_error": (c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -283,6 +292,94 @@ class Run:
         out = (c_double * len(STATS))()
         self._check(self.lib.dmr_stats(self.ctx, out))
         return dict(zip(STATS, list(out)))
+
+
+class BatchRun(Run):
+    """A run owned by a Batch (set-up, reads and stats; advanced by the batch)."""
+
+    def __init__(self, batch, k):
+        self.lib = batch.lib
+        self.cfg = dict(batch.cfgs[k])
+        self._c = make_config(self.cfg)
+        self.ctx = c_void_p(self.lib.dmr_batch_run(batch.handle, k))
+        self.device = batch.device
+        self.stream = batch.stream
+        self.fdtype = np.float32 if self._c.precision == 1 else np.float64
+        self.lam = C0 / self._c.freq
+        self.dxc = self.lam / self._c.n_lambda
+        self._batch = batch
+
+    def close(self):
+        self.ctx = None
+
+
+class Batch:
+    """Independent runs advanced together (one launch per phase for all runs,
+    one CUDA graph per period)."""
+
+    def __init__(self, cfgs, device=None, stream=None):
+        import torch
+        self.lib = lib = load()
+        self.cfgs = [dict(c) for c in cfgs]
+        arr = (DmrConfig * len(cfgs))(*[make_config(c) for c in cfgs])
+        self._arr = arr
+        nbytes = lib.dmr_batch_workspace_bytes(arr, len(cfgs))
+        if nbytes == 0:
+            raise DMRError(EINVAL, lib.dmr_batch_last_error(None).decode())
+        self.device = torch.device(device if device is not None else "cuda")
+        self.ws = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        h = c_void_p()
+        st = lib.dmr_batch_create(arr, len(cfgs), c_void_p(self.ws.data_ptr()), c_size_t(nbytes),
+                                  c_void_p(self.stream.cuda_stream), byref(h))
+        if st != OK:
+            raise DMRError(st, lib.dmr_batch_last_error(None).decode())
+        self.handle = h
+        self.runs = [BatchRun(self, k) for k in range(len(cfgs))]
+
+    def _check(self, st):
+        if st != OK:
+            raise DMRError(st, self.lib.dmr_batch_last_error(self.handle).decode())
+
+    def advance(self, n_coarse_steps):
+        self._check(self.lib.dmr_batch_advance(self.handle, int(n_coarse_steps)))
+
+    def set_graphs(self, on=True):
+        self._check(self.lib.dmr_batch_set_graphs(self.handle, int(bool(on))))
+
+    def autotune(self):
+        w = c_int32()
+        ms = (c_double * 5)()
+        self._check(self.lib.dmr_batch_autotune(self.handle, byref(w), ms))
+        return w.value, list(ms)
+
+    def launch_count(self):
+        n = c_int64()
+        self._check(self.lib.dmr_batch_launch_count(self.handle, byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            for r in self.runs:
+                r.close()
+            self.lib.dmr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_from_workloads(ws, device=None):
+    """Batch of runs, each patched and seeded from its workload dict."""
+    b = Batch([w["cfg"] for w in ws], device=device)
+    for run, w in zip(b.runs, ws):
+        if w["cfg"].get("r", 1) > 1 and w.get("rect") is not None:
+            run.set_patch(w["rect"])
+        run.seed_workload(w["seeds"])
+    return b
 
 
 def run_from_workload(w, device=None, precision=None, cfg_overrides=None, rect=None):
