@@ -200,6 +200,32 @@ int dmr_launch_count(const dmr_ctx* ctx, int64_t* launches);
 /* Wait for all work queued on the run's stream. */
 int dmr_sync(const dmr_ctx* ctx);
 
+/* ---- Adjoint (reverse mode) with the refinement schedule held fixed ----
+ * Gradients of a loss L(n_coarse(t_end)) with respect to the incident
+ * amplitude E0, the ionization scale s_nu and the initial density map of the
+ * fine rectangle (the seed map; of the coarse mesh when r = 1).
+ *  1. dmr_adjoint_record advances n_steps (a multiple of steps_per_period,
+ *     from a period boundary) and keeps a copy of the whole workspace every K
+ *     steps (K a multiple of steps_per_period) in ckpt
+ *     (dmr_adjoint_checkpoint_bytes), and the rectangle after every period.
+ *  2. dmr_adjoint_backward takes dL/dn at t_end (device, dense (ny+1) x
+ *     (nx+1) coarse node map in the run's precision) and a device workspace
+ *     of dmr_adjoint_workspace_bytes (valid after step 1).  For each segment,
+ *     last first, it restores the checkpoint, recomputes the segment with the
+ *     recorded rectangles while writing every step's E and v to a tape, and
+ *     sweeps the tape backwards with the adjoint kernels.  It writes dL/dE0,
+ *     dL/ds_nu (host doubles) and dL/d(seed map) (device, dense rows x cols of
+ *     the initial fine rectangle's nodes, the run's precision).  Afterwards
+ *     the run holds the state at the end of its first recorded segment.
+ * The forward loss, the refinement schedule and the gradients are those of
+ * the discrete scheme: flags and growth are not differentiated. */
+size_t dmr_adjoint_checkpoint_bytes(const dmr_ctx* ctx, int64_t n_steps, int64_t K);
+int dmr_adjoint_record(dmr_ctx* ctx, int64_t n_steps, int64_t K, void* ckpt, size_t bytes);
+size_t dmr_adjoint_workspace_bytes(const dmr_ctx* ctx);
+int dmr_adjoint_backward(dmr_ctx* ctx, const void* dL_dn, void* dev_workspace, size_t bytes,
+                         void* ckpt, size_t ckpt_bytes, double* dL_dE0, double* dL_dnu_scale,
+                         void* dL_dseed);
+
 /* ---- Batched runs (many independent breakdown runs advanced together) ----
  * A batch holds n runs whose configurations may differ in size, E0, pressure
  * and seeds but share precision, r (1 or even) and an even steps_per_period.
@@ -230,7 +256,7 @@ int dmr_batch_advance(dmr_batch* b, int64_t n_coarse_steps);
 int dmr_batch_set_graphs(dmr_batch* b, int enable);
 
 /* Autotuner (at a period boundary): times the batched EM launch for five
- * strip heights (warps-per-SM targets 16, 32, 48, 64, 96) on the present
+ * strip heights (warps-per-SM targets 8, 16, 32, 48, 96) on the present
  * state without changing it, keeps the fastest; returns the choice and the
  * per-candidate launch times (ms). */
 int dmr_batch_autotune(dmr_batch* b, int32_t* warps_per_sm, double trial_ms[5]);

@@ -14,6 +14,7 @@
 
 #include "dmr.h"
 #include "dmr_kernels.cuh"
+#include "dmr_adjoint.cuh"
 
 namespace {
 
@@ -271,6 +272,11 @@ struct Base {
   virtual int read(int field, int level, void* dst, size_t bytes, int dev) = 0;
   virtual int write(int field, int level, const void* src, size_t bytes, int dev) = 0;
   virtual int stats(double* out) = 0;
+  virtual int adj_record(int64_t n, int64_t K, void* ckpt, size_t bytes) = 0;
+  virtual size_t adj_ckpt_bytes(int64_t n, int64_t K) const = 0;
+  virtual size_t adj_bytes() const = 0;
+  virtual int adj_backward(const void* dLdn, void* ws, size_t bytes, void* ckpt, size_t cbytes,
+                           double* dE0, double* dnu, void* dseed) = 0;
 };
 
 template <class T>
@@ -936,6 +942,540 @@ struct Engine final : Base {
     return launched("write");
   }
 
+  // ======================================================================
+  // Adjoint (reverse mode) with the refinement schedule held fixed.
+  // adj_record: advance n steps from a period boundary, keeping a full copy of
+  // the workspace every K steps and the rectangle after every period.
+  // adj_backward: for each segment in reverse order, restore its checkpoint,
+  // recompute the segment with every step's E^l and v^{l+1/2} (and each
+  // period's density, S2 and last-level E) written to a tape, then sweep the
+  // tape backwards with the adjoint kernels of dmr_adjoint.cuh.
+  // ======================================================================
+  struct HostState {
+    int64_t m;
+    int cpar, fpar, cur;
+    int rect[4];
+    bool has_fine, rvalid;
+    dmr::Mesh<T> C, F0, F1;
+  };
+  struct Rec {
+    bool valid = false;
+    int64_t m0 = 0, n = 0, K = 0;
+    char* ckpt = nullptr;
+    std::vector<HostState> ck;
+    std::vector<int32_t> log;      // rectangle after each recorded period
+  } rec;
+
+  HostState save_host() const {
+    HostState h;
+    h.m = m; h.cpar = cpar; h.fpar = fpar; h.cur = cur;
+    for (int q = 0; q < 4; ++q) h.rect[q] = rect[q];
+    h.has_fine = has_fine; h.rvalid = rvalid;
+    h.C = C; h.F0 = F[0]; h.F1 = F[1];
+    return h;
+  }
+  void load_host(const HostState& h) {
+    m = h.m; cpar = h.cpar; fpar = h.fpar; cur = h.cur;
+    for (int q = 0; q < 4; ++q) rect[q] = h.rect[q];
+    has_fine = h.has_fine; rvalid = h.rvalid;
+    C = h.C; F[0] = h.F0; F[1] = h.F1;
+  }
+  size_t wbytes() const { return up(L.total, 256); }
+
+  size_t adj_ckpt_bytes(int64_t n, int64_t K) const override {
+    if (K <= 0 || n <= 0) return 0;
+    return (size_t)((n + K - 1) / K) * wbytes();
+  }
+
+  int adj_record(int64_t n, int64_t K, void* ckpt, size_t bytes) override {
+    const int NT = cfg.steps_per_period;
+    if (n <= 0 || K <= 0 || n % NT || K % NT)
+      return fail(DMR_EINVAL, "steps and checkpoint interval must be positive multiples of steps_per_period");
+    if (m % NT) return fail(DMR_ESTATE, "recording starts at a period boundary");
+    if (!ckpt || bytes < adj_ckpt_bytes(n, K)) return fail(DMR_ECAPACITY, "checkpoint buffer too small");
+    rec = Rec();
+    rec.m0 = m; rec.n = n; rec.K = K; rec.ckpt = (char*)ckpt;
+    const std::vector<int32_t> user_replay = replay;
+    const size_t user_pos = replay_pos;
+    for (int64_t done = 0; done < n;) {
+      rec.ck.push_back(save_host());
+      if (int s = ck(cudaMemcpyAsync(rec.ckpt + (rec.ck.size() - 1) * wbytes(), ws, L.total,
+                                     cudaMemcpyDeviceToDevice, st), "checkpoint")) return s;
+      const int64_t seg = std::min<int64_t>(K, n - done);
+      for (int64_t q = 0; q < seg; q += NT) {
+        if (int s = advance(NT)) return s;
+        for (int k = 0; k < 4; ++k) rec.log.push_back(has_fine ? rect[k] : -1);
+      }
+      done += seg;
+    }
+    replay = user_replay;
+    replay_pos = user_pos;
+    rec.valid = true;
+    return ck(cudaStreamSynchronize(st), "record sync");
+  }
+
+  // fine dims (cells, pitch) of a rectangle
+  void fdims(const int* rc, int* nx, int* ny, int* p) const {
+    *nx = cfg.r * (rc[2] - rc[0]);
+    *ny = cfg.r * (rc[3] - rc[1]);
+    *p = (int)fine_pitch(*nx);
+  }
+  size_t fplane_b(const int* rc) const {
+    int nx, ny, p;
+    fdims(rc, &nx, &ny, &p);
+    return (size_t)(ny + 1) * p * L.es;
+  }
+  size_t cplane_b() const { return L.cplane * L.es; }
+
+  // tape bytes of one recorded segment starting at period index p0
+  size_t seg_tape_bytes(int64_t p0, int64_t periods) const {
+    const int NT = cfg.steps_per_period, r = cfg.r;
+    size_t b = 0;
+    for (int64_t p = p0; p < p0 + periods; ++p) {
+      int rc[4];
+      const HostState& h0 = rec.ck[0];
+      for (int k = 0; k < 4; ++k) rc[k] = p == 0 ? h0.rect[k] : rec.log[(size_t)(p - 1) * 4 + k];
+      const bool fine = cfg.r > 1 && rc[0] >= 0;
+      const size_t fb = fine ? fplane_b(rc) : 0;
+      b += (size_t)NT * (4 * up(cplane_b(), 256) + (fine ? (size_t)4 * r * up(fb, 256) : 0));
+      b += 3 * up(cplane_b(), 256) + up(L.cplane * 8, 256);
+      if (fine) b += 3 * up(fb, 256) + up(fb / L.es * 8, 256);
+    }
+    return b;
+  }
+
+  size_t adj_fixed_bytes() const {
+    const size_t mx = std::max(L.cplane, L.fplane);
+    size_t b = 10 * up(cplane_b(), 256);                          // coarse adjoints
+    if (cfg.r > 1) b += 2 * 10 * up(L.fplane * L.es, 256);        // fine adjoints, two layouts
+    b += 6 * up(mx * L.es, 256);                                  // continuity-step scratch
+    b += 256;                                                     // FP64 sums
+    return b;
+  }
+
+  size_t adj_bytes() const override {
+    if (!rec.valid) return 0;
+    const int64_t ppseg = rec.K / cfg.steps_per_period;
+    const int64_t periods = rec.n / cfg.steps_per_period;
+    size_t mx = 0;
+    for (int64_t p0 = 0; p0 < periods; p0 += ppseg)
+      mx = std::max(mx, seg_tape_bytes(p0, std::min(ppseg, periods - p0)));
+    return adj_fixed_bytes() + mx;
+  }
+
+  struct StepRec {
+    int64_t m;
+    int rect[4];
+    bool fine, rvalid;
+    const T *cEx, *cEy, *cvx, *cvy;
+    std::vector<const T*> fEx, fEy, fvx, fvy;   // per sub-step k (index k - 1)
+  };
+  struct PerRec {
+    int64_t L;
+    int rect_b[4], rect_a[4], cur_b, cur_a;
+    bool fine, expanded, rvalid;
+    const T *cEx, *cEy, *nc, *fEx, *fEy, *nf;
+    const double *S2c, *S2f;
+  };
+
+  // tape allocator
+  char* tape = nullptr;
+  size_t tape_used = 0, tape_cap = 0;
+  // tape slots never go past the caller's buffer: an overflowing request is
+  // counted (and reported after the segment) but gets no slot
+  bool tape_over = false;
+  char* tape_slot(size_t bytes) {
+    if (tape_used + up(bytes, 256) > tape_cap) { tape_over = true; return nullptr; }
+    char* d = tape + tape_used;
+    tape_used += up(bytes, 256);
+    return d;
+  }
+  const T* tape_copy(const void* src, size_t bytes) {
+    T* d = reinterpret_cast<T*>(tape_slot(bytes));
+    if (d) cudaMemcpyAsync(d, src, bytes, cudaMemcpyDeviceToDevice, st);
+    return d;
+  }
+  double* tape_alloc_d(size_t bytes) { return reinterpret_cast<double*>(tape_slot(bytes)); }
+
+  dmr::Step<T> make_step_at(int rr, int64_t level, bool accum, int i0) const {
+    const int save = rect[0];
+    Engine<T>* self = const_cast<Engine<T>*>(this);
+    self->rect[0] = i0;
+    dmr::Step<T> s_ = make_step(rr, level, accum);
+    self->rect[0] = save;
+    return s_;
+  }
+
+  // one coarse step with its tape records (same kernels as launch_coarse_step,
+  // the first fine sub-step launched on its own)
+  int record_step(StepRec* R) {
+    const int NT = cfg.steps_per_period, r = cfg.r;
+    R->m = m;
+    for (int k = 0; k < 4; ++k) R->rect[k] = rect[k];
+    R->fine = has_fine;
+    R->rvalid = rvalid;
+    materialize_restriction();
+    R->cEx = tape_copy(C.Ex, cplane_b());
+    R->cEy = tape_copy(C.Ey, cplane_b());
+    const int cp0 = cpar;
+    dmr::EmArgs<T> Ac, Af;
+    em_args_for(1, m, cpar, fpar, rvalid, &Ac, nullptr);
+    dmr::k_em<T><<<Ac.nblk + Ac.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Ac);
+    counted(1);
+    flip_coarse();
+    R->cvx = tape_copy(C.vx, cplane_b());
+    R->cvy = tape_copy(C.vy, cplane_b());
+    if (has_fine) {
+      const size_t fb = fplane_b(rect);
+      for (int k = 1; k <= r; ++k) {
+        R->fEx.push_back(tape_copy(F[cur].Ex, fb));
+        R->fEy.push_back(tape_copy(F[cur].Ey, fb));
+        em_args_for(k, m, cp0, fpar, rvalid, nullptr, &Af);
+        dmr::k_em<T><<<Af.nblk + Af.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Af);
+        counted(1);
+        flip_fine();
+        R->fvx.push_back(tape_copy(F[cur].vx, fb));
+        R->fvy.push_back(tape_copy(F[cur].vy, fb));
+      }
+      rvalid = true;
+    }
+    ++m;
+    (void)NT;
+    return launched("recorded EM step");
+  }
+
+  int record_period(PerRec* P) {
+    P->L = m;
+    for (int k = 0; k < 4; ++k) P->rect_b[k] = rect[k];
+    P->cur_b = cur;
+    P->fine = has_fine;
+    P->rvalid = rvalid;
+    materialize_restriction();
+    P->cEx = tape_copy(C.Ex, cplane_b());
+    P->cEy = tape_copy(C.Ey, cplane_b());
+    P->nc = tape_copy(C.n, cplane_b());
+    double* s2c = tape_alloc_d(L.cplane * 8);
+    if (s2c)
+      dmr::k_s2_view<T><<<nodes_grid(C.nx, C.ny), dim3(BX, BY), 0, st>>>(C, make_step(1, m, true), s2c);
+    P->S2c = s2c;
+    if (has_fine) {
+      const size_t fb = fplane_b(rect);
+      P->fEx = tape_copy(F[cur].Ex, fb);
+      P->fEy = tape_copy(F[cur].Ey, fb);
+      P->nf = tape_copy(F[cur].n, fb);
+      double* s2f = tape_alloc_d(fb / L.es * 8);
+      if (s2f)
+        dmr::k_s2_view<T><<<nodes_grid(F[cur].nx, F[cur].ny), dim3(BX, BY), 0, st>>>(
+            F[cur], make_step(cfg.r, (int64_t)cfg.r * m, true), s2f);
+      P->S2f = s2f;
+    }
+    if (int s = launch_period_end(m)) return s;
+    if (int s = period_end_host()) return s;
+    P->expanded = has_fine && (rect[0] != P->rect_b[0] || rect[1] != P->rect_b[1] ||
+                               rect[2] != P->rect_b[2] || rect[3] != P->rect_b[3]);
+    for (int k = 0; k < 4; ++k) P->rect_a[k] = rect[k];
+    P->cur_a = cur;
+    return DMR_OK;
+  }
+
+  // adjoint arrays of one mesh
+  struct AdjArr {
+    T* E[2][2];      // [buffer][x, y]
+    T *H, *vx, *vy, *n, *ntmp, *S2;
+  };
+
+  dmr::Modes modes_of(const int* rc) const {
+    dmr::Modes md;
+    md.m[dmr::SIDE_LEFT] = rc[0] == 0 ? dmr::BC_MUR : dmr::BC_CFB;
+    md.m[dmr::SIDE_RIGHT] = rc[2] == cfg.nx ? dmr::BC_MUR : dmr::BC_CFB;
+    md.m[dmr::SIDE_BOTTOM] = rc[1] == 0 ? dmr::BC_MUR : dmr::BC_CFB;
+    md.m[dmr::SIDE_TOP] = rc[3] == cfg.ny ? dmr::BC_MUR : dmr::BC_CFB;
+    return md;
+  }
+
+  dmr::AdjM<T> adjm(const AdjArr& a, int in, int nx, int ny, int p) const {
+    dmr::AdjM<T> A;
+    A.aEx_in = a.E[in][0]; A.aEy_in = a.E[in][1];
+    A.aEx_out = a.E[in ^ 1][0]; A.aEy_out = a.E[in ^ 1][1];
+    A.aHz = a.H; A.avx = a.vx; A.avy = a.vy; A.an = a.n; A.aS2 = a.S2;
+    A.nx = nx; A.ny = ny; A.p = p;
+    return A;
+  }
+
+  void restrict_t(const AdjArr& ca, int cin, const AdjArr& fa, int fin, const int* rc) {
+    const int r = cfg.r;
+    int jlo = side_at(rc, dmr::SIDE_BOTTOM) ? rc[1] : rc[1] + 1;
+    int jhi = side_at(rc, dmr::SIDE_TOP) ? rc[3] : rc[3] - 1;
+    int ilo = side_at(rc, dmr::SIDE_LEFT) ? rc[0] : rc[0] + 1;
+    int ihi = side_at(rc, dmr::SIDE_RIGHT) ? rc[2] : rc[2] - 1;
+    int fnx, fny, fp;
+    fdims(rc, &fnx, &fny, &fp);
+    const dim3 g((rc[2] - rc[0] + 1 + BX - 1) / BX, (rc[3] - rc[1] + 1 + BY - 1) / BY);
+    dmr::ka_restrict<T><<<g, dim3(BX, BY), 0, st>>>(ca.E[cin][0], ca.E[cin][1], C.p, fa.E[fin][0],
+                                                    fa.E[fin][1], fp, rc[0], rc[1], rc[2], rc[3], r,
+                                                    jlo, jhi, ilo, ihi);
+  }
+  bool side_at(const int* rc, int sd) const {
+    switch (sd) {
+      case dmr::SIDE_LEFT: return rc[0] == 0;
+      case dmr::SIDE_RIGHT: return rc[2] == cfg.nx;
+      case dmr::SIDE_BOTTOM: return rc[1] == 0;
+      default: return rc[3] == cfg.ny;
+    }
+  }
+
+  int adj_backward(const void* dLdn, void* wsa, size_t bytes, void* ckpt, size_t cbytes,
+                   double* dE0, double* dnu, void* dseed) override {
+    if (!rec.valid) return fail(DMR_ESTATE, "dmr_adjoint_record has not run");
+    if ((char*)ckpt != rec.ckpt || cbytes < adj_ckpt_bytes(rec.n, rec.K))
+      return fail(DMR_EINVAL, "pass the checkpoint buffer given to dmr_adjoint_record");
+    if (!wsa || bytes < adj_bytes()) return fail(DMR_ECAPACITY, "adjoint workspace too small");
+    const int NT = cfg.steps_per_period, r = cfg.r;
+    const bool dmr_ = cfg.r > 1;
+    char* w = (char*)wsa;
+    size_t o = 0;
+    auto take = [&](size_t b) { char* q = w + o; o += up(b, 256); return q; };
+    AdjArr ca, fa[2];
+    {
+      T* pl[10];
+      for (int k = 0; k < 10; ++k) pl[k] = (T*)take(cplane_b());
+      ca.E[0][0] = pl[0]; ca.E[0][1] = pl[1]; ca.E[1][0] = pl[2]; ca.E[1][1] = pl[3];
+      ca.H = pl[4]; ca.vx = pl[5]; ca.vy = pl[6]; ca.n = pl[7]; ca.ntmp = pl[8]; ca.S2 = pl[9];
+    }
+    for (int sset = 0; sset < 2 && dmr_; ++sset) {
+      T* pl[10];
+      for (int k = 0; k < 10; ++k) pl[k] = (T*)take(L.fplane * L.es);
+      fa[sset].E[0][0] = pl[0]; fa[sset].E[0][1] = pl[1]; fa[sset].E[1][0] = pl[2]; fa[sset].E[1][1] = pl[3];
+      fa[sset].H = pl[4]; fa[sset].vx = pl[5]; fa[sset].vy = pl[6]; fa[sset].n = pl[7];
+      fa[sset].ntmp = pl[8]; fa[sset].S2 = pl[9];
+    }
+    const size_t mx = std::max(L.cplane, L.fplane);
+    T* sc[6];
+    for (int k = 0; k < 6; ++k) sc[k] = (T*)take(mx * L.es);
+    double* sums = (double*)take(256);
+    tape = w + o;
+    tape_cap = bytes - o;
+    if (int s_ = ck(cudaMemsetAsync(w, 0, o, st), "zero adjoints")) return s_;
+    // dL/dn at the end (dense coarse map) -> pitched adjoint of the coarse density
+    if (int s_ = ck(cudaMemcpy2DAsync(ca.n, (size_t)C.p * L.es, dLdn, (size_t)(C.nx + 1) * L.es,
+                                      (size_t)(C.nx + 1) * L.es, C.ny + 1, cudaMemcpyDeviceToDevice, st),
+                    "load dL/dn")) return s_;
+    const bool graphs0 = graphs;
+    graphs = false;
+    drop_graph();
+    const std::vector<int32_t> user_replay = replay;
+    const size_t user_pos = replay_pos;
+    int cin = 0, fin = 0;       // which adjoint E buffer holds the "in" level
+    int fset = -1;              // fine adjoint layout in use (= forward set index)
+    const int64_t ppseg = rec.K / NT;
+    const int nseg = (int)rec.ck.size();
+    const dmr::Dens dc = make_dens(1), df = make_dens(r);
+    const double A1 = 5.14e11 * cfg.p_torr;
+    int st_ = DMR_OK;
+    for (int sg = nseg - 1; sg >= 0 && !st_; --sg) {
+      // ---- restore the segment's start and recompute it onto the tape
+      if ((st_ = ck(cudaMemcpyAsync(ws, rec.ckpt + (size_t)sg * wbytes(), L.total,
+                                    cudaMemcpyDeviceToDevice, st), "restore checkpoint"))) break;
+      load_host(rec.ck[sg]);
+      const int64_t p0 = (int64_t)sg * ppseg;
+      const int64_t periods = std::min<int64_t>(ppseg, rec.n / NT - p0);
+      replay.assign(rec.log.begin() + p0 * 4, rec.log.begin() + (p0 + periods) * 4);
+      replay_pos = 0;
+      tape_used = 0;
+      tape_over = false;
+      std::vector<StepRec> steps;
+      std::vector<PerRec> pers;
+      for (int64_t pp = 0; pp < periods && !st_; ++pp) {
+        for (int q = 0; q < NT && !st_; ++q) {
+          steps.emplace_back();
+          st_ = record_step(&steps.back());
+        }
+        if (st_) break;
+        pers.emplace_back();
+        st_ = record_period(&pers.back());
+      }
+      if (st_) break;
+      if (tape_over) { st_ = fail(DMR_ECAPACITY, "adjoint tape overflow"); break; }
+      if (fset < 0) fset = cur;
+      // ---- reverse sweep over the segment
+      for (int64_t idx = (int64_t)steps.size() - 1; idx >= 0 && !st_; --idx) {
+        const StepRec& R = steps[idx];
+        const PerRec& P = pers[idx / NT];
+        if ((idx + 1) % NT == 0) {
+          // period end at level P.L (forward order: restriction, S2 sample,
+          // continuity steps, commit, growth)
+          if (P.expanded) {
+            dmr::ExpT<T> e;
+            int nnx, nny, np_, onx, ony, op;
+            fdims(P.rect_a, &nnx, &nny, &np_);
+            fdims(P.rect_b, &onx, &ony, &op);
+            const AdjArr& nA = fa[P.cur_a];
+            const AdjArr& oA = fa[P.cur_b];
+            e.nEx = nA.E[fin][0]; e.nEy = nA.E[fin][1]; e.nHz = nA.H; e.nvx = nA.vx; e.nvy = nA.vy; e.nn = nA.n;
+            e.oEx = oA.E[fin][0]; e.oEy = oA.E[fin][1]; e.oHz = oA.H; e.ovx = oA.vx; e.ovy = oA.vy; e.on = oA.n;
+            e.cEx = ca.E[cin][0]; e.cEy = ca.E[cin][1]; e.cHz = ca.H; e.cvx = ca.vx; e.cvy = ca.vy; e.cn = ca.n;
+            e.nnx = nnx; e.nny = nny; e.np = np_; e.onx = onx; e.ony = ony; e.op = op;
+            e.cnx = C.nx; e.cny = C.ny; e.cp = C.p;
+            e.I0 = P.rect_a[0]; e.J0 = P.rect_a[1]; e.oI0 = P.rect_b[0]; e.oJ0 = P.rect_b[1]; e.r = r;
+            dmr::ka_expand<T><<<nodes_grid(nnx, nny), dim3(BX, BY), 0, st>>>(e);
+            fset = P.cur_b;
+          }
+          st_ = adj_period(P, ca, fa, cin, fin, fset, sc, sums, dc, df, A1);
+          if (st_) break;
+        }
+        // ---- coarse step R.m: fine sub-steps r..1, then the coarse step
+        st_ = adj_step(R, P, ca, fa, cin, fin, fset, sums);
+      }
+    }
+    // seed map gradient: initial fine density (+ the coarse nodes it was copied to)
+    if (!st_) {
+      const HostState& h0 = rec.ck[0];
+      if (dmr_ && h0.has_fine) {
+        int fnx, fny, fp;
+        fdims(h0.rect, &fnx, &fny, &fp);
+        const int* rc = h0.rect;
+        const dim3 gi((rc[2] - rc[0] + 1 + BX - 1) / BX, (rc[3] - rc[1] + 1 + BY - 1) / BY);
+        dmr::ka_inject<T><<<gi, dim3(BX, BY), 0, st>>>(ca.n, C.p, fa[fset < 0 ? h0.cur : fset].n, fp,
+                                                       rc[0], rc[1], rc[2], rc[3], r);
+        if (dseed)
+          st_ = ck(cudaMemcpy2DAsync(dseed, (size_t)(fnx + 1) * L.es, fa[fset < 0 ? h0.cur : fset].n,
+                                     (size_t)fp * L.es, (size_t)(fnx + 1) * L.es, fny + 1,
+                                     cudaMemcpyDeviceToDevice, st), "write seed gradient");
+      } else if (dseed) {
+        st_ = ck(cudaMemcpy2DAsync(dseed, (size_t)(C.nx + 1) * L.es, ca.n, (size_t)C.p * L.es,
+                                   (size_t)(C.nx + 1) * L.es, C.ny + 1, cudaMemcpyDeviceToDevice, st),
+                 "write seed gradient");
+      }
+    }
+    double hs[2] = {0.0, 0.0};
+    if (!st_) st_ = ck(cudaMemcpyAsync(hs, sums, sizeof hs, cudaMemcpyDeviceToHost, st), "read sums");
+    if (!st_) st_ = ck(cudaStreamSynchronize(st), "backward sync");
+    if (dE0) *dE0 = hs[0];
+    if (dnu) *dnu = hs[1];
+    replay = user_replay;
+    replay_pos = user_pos;
+    graphs = graphs0;
+    tape = nullptr;
+    return st_ ? st_ : launched("adjoint");
+  }
+
+  // reverse of the period end at level P.L (after any growth^T): commit^T,
+  // Dirichlet^T, fine and coarse continuity^T, S2 sample^T, restriction^T
+  int adj_period(const PerRec& P, AdjArr& ca, AdjArr* fa, int cin, int fin, int fset, T** sc,
+                 double* sums, const dmr::Dens& dc, const dmr::Dens& df, double A1) {
+    const int r = cfg.r;
+    const dim3 blk(BX, BY);
+    if (P.fine) {
+      int fnx, fny, fp;
+      fdims(P.rect_b, &fnx, &fny, &fp);
+      AdjArr& A = fa[fset];
+      const int* rc = P.rect_b;
+      const dim3 gi((rc[2] - rc[0] + 1 + BX - 1) / BX, (rc[3] - rc[1] + 1 + BY - 1) / BY);
+      dmr::ka_inject<T><<<gi, blk, 0, st>>>(ca.n, C.p, A.n, fp, rc[0], rc[1], rc[2], rc[3], r);
+      dmr::Dir<T> dir{};
+      dir.r = r;
+      for (int q = 0; q < 4; ++q) {
+        if (side_at(rc, q)) continue;
+        dir.on[q] = 1;
+        if (q == dmr::SIDE_BOTTOM || q == dmr::SIDE_TOP) {
+          dir.line[q] = ca.n + (size_t)(q == dmr::SIDE_BOTTOM ? rc[1] : rc[3]) * C.p;
+          dir.stride[q] = 1; dir.len[q] = cfg.nx + 1; dir.start[q] = rc[0];
+        } else {
+          dir.line[q] = ca.n + (q == dmr::SIDE_LEFT ? rc[0] : rc[2]);
+          dir.stride[q] = C.p; dir.len[q] = cfg.ny + 1; dir.start[q] = rc[1];
+        }
+      }
+      const dim3 gf = nodes_grid(fnx, fny);
+      dmr::ka_dir<T><<<gf, blk, 0, st>>>(A.n, fnx, fny, fp, dir);
+      // the fine density adjoint kernels read the S2 sum as T: convert in place
+      dmr::ka_rates_d<T><<<gf, blk, 0, st>>>(P.nf, P.S2f, df, A1, fnx, fny, fp, sc[0], sc[1], sc[2],
+                                             sc[3], sc[4], sc[5]);
+      dmr::ka_density<T><<<gf, blk, 0, st>>>(P.nf, sc[0], sc[1], sc[2], sc[3], sc[4], sc[5], A.n,
+                                             A.ntmp, A.S2, df, dir, fnx, fny, fp, sums + 1);
+      std::swap(A.n, A.ntmp);
+    }
+    {
+      const dim3 gc = nodes_grid(C.nx, C.ny);
+      dmr::Dir<T> none{};
+      dmr::ka_rates_d<T><<<gc, blk, 0, st>>>(P.nc, P.S2c, dc, A1, C.nx, C.ny, C.p, sc[0], sc[1],
+                                             sc[2], sc[3], sc[4], sc[5]);
+      dmr::ka_density<T><<<gc, blk, 0, st>>>(P.nc, sc[0], sc[1], sc[2], sc[3], sc[4], sc[5], ca.n,
+                                             ca.ntmp, ca.S2, dc, none, C.nx, C.ny, C.p, sums + 1);
+      std::swap(ca.n, ca.ntmp);
+      dmr::Step<T> s_ = make_step(1, P.L, true);
+      dmr::ka_s2<T><<<gc, blk, 0, st>>>(ca.E[cin][0], ca.E[cin][1], P.cEx, P.cEy, ca.S2, s_, C.nx,
+                                        C.ny, C.p, sums);
+    }
+    if (P.fine) {
+      int fnx, fny, fp;
+      fdims(P.rect_b, &fnx, &fny, &fp);
+      AdjArr& A = fa[fset];
+      dmr::Step<T> s_ = make_step_at(r, (int64_t)r * P.L, true, P.rect_b[0]);
+      dmr::ka_s2<T><<<nodes_grid(fnx, fny), blk, 0, st>>>(A.E[fin][0], A.E[fin][1], P.fEx, P.fEy, A.S2,
+                                                          s_, fnx, fny, fp, sums);
+      if (P.rvalid) restrict_t(ca, cin, A, fin, P.rect_b);
+    }
+    return launched("adjoint period end");
+  }
+
+  // reverse of coarse step R.m: fine sub-steps r..1, then the coarse step,
+  // then the transfer^T of the restricted coarse edges to the fine mesh
+  int adj_step(const StepRec& R, const PerRec& P, AdjArr& ca, AdjArr* fa, int& cin, int& fin,
+               int fset, double* sums) {
+    const int NT = cfg.steps_per_period, r = cfg.r;
+    const dim3 blk(BX, BY);
+    cudaMemsetAsync(ca.E[cin ^ 1][0], 0, cplane_b(), st);
+    cudaMemsetAsync(ca.E[cin ^ 1][1], 0, cplane_b(), st);
+    if (R.fine) {
+      int fnx, fny, fp;
+      fdims(R.rect, &fnx, &fny, &fp);
+      AdjArr& A = fa[fset];
+      const dmr::Modes md = modes_of(R.rect);
+      dmr::CfbT<T> cb{};
+      for (int q = 0; q < 4; ++q) {
+        cb.mode[q] = md.m[q];
+        if (q == dmr::SIDE_BOTTOM || q == dmr::SIDE_TOP) {
+          cb.start[q] = R.rect[0]; cb.len[q] = cfg.nx; cb.at[q] = q == dmr::SIDE_BOTTOM ? R.rect[1] : R.rect[3];
+        } else {
+          cb.start[q] = R.rect[1]; cb.len[q] = cfg.ny; cb.at[q] = q == dmr::SIDE_LEFT ? R.rect[0] : R.rect[2];
+        }
+      }
+      cb.r = r;
+      cb.cp = C.p;
+      cb.old_x = ca.E[cin ^ 1][0]; cb.old_y = ca.E[cin ^ 1][1];
+      cb.new_x = ca.E[cin][0]; cb.new_y = ca.E[cin][1];
+      const int ncfb = 2 * fnx + 2 * fny;
+      const dim3 gf = nodes_grid(fnx, fny);
+      const size_t fb = fplane_b(R.rect);
+      for (int k = r; k >= 1; --k) {
+        cudaMemsetAsync(A.E[fin ^ 1][0], 0, fb, st);
+        cudaMemsetAsync(A.E[fin ^ 1][1], 0, fb, st);
+        const int64_t mf = (int64_t)r * R.m + (k - 1);
+        const dmr::Step<T> sf = make_step_at(r, mf, (mf % ((int64_t)r * NT)) != 0, R.rect[0]);
+        const dmr::AdjM<T> am = adjm(A, fin, fnx, fny, fp);
+        dmr::ka_h<T><<<gf, blk, 0, st>>>(am, sf, md);
+        cb.frac = (T)((double)k / (double)r);
+        dmr::ka_cfb<T><<<(ncfb + 127) / 128, 128, 0, st>>>(am, cb);
+        dmr::FwdM<T> fw;
+        fw.Ex = R.fEx[k - 1]; fw.Ey = R.fEy[k - 1]; fw.vx = R.fvx[k - 1]; fw.vy = R.fvy[k - 1]; fw.n = P.nf;
+        dmr::ka_e<T><<<gf, blk, 0, st>>>(am, fw, sf, md, sums);
+        fin ^= 1;
+      }
+    }
+    const dmr::Step<T> sc = make_step(1, R.m, (R.m % NT) != 0);
+    dmr::Modes mc;
+    for (int q = 0; q < 4; ++q) mc.m[q] = dmr::BC_MUR;
+    const dmr::AdjM<T> am = adjm(ca, cin, C.nx, C.ny, C.p);
+    const dim3 gc = nodes_grid(C.nx, C.ny);
+    dmr::ka_h<T><<<gc, blk, 0, st>>>(am, sc, mc);
+    dmr::FwdM<T> fw;
+    fw.Ex = R.cEx; fw.Ey = R.cEy; fw.vx = R.cvx; fw.vy = R.cvy; fw.n = P.nc;
+    dmr::ka_e<T><<<gc, blk, 0, st>>>(am, fw, sc, mc, sums);
+    cin ^= 1;
+    if (R.fine && R.rvalid) restrict_t(ca, cin, fa[fset], fin, R.rect);
+    return launched("adjoint step");
+  }
+
   int stats(double* out) override {
     dmr::Ctl hc;
     if (int s = ck(cudaMemcpyAsync(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, st), "stats")) return s;
@@ -1262,7 +1802,7 @@ struct Batch final : BatchBase {
   int autotune() override {
     if (int s = check_state()) return s;
     if (m % NT != 0) return fail(DMR_ESTATE, "autotune at a period boundary");
-    const int cand[5] = {16, 32, 48, 64, 96};
+    const int cand[5] = {8, 16, 32, 48, 96};
     cudaEvent_t a, b;
     if (int s = ck(cudaEventCreate(&a), "event")) return s;
     if (int s = ck(cudaEventCreate(&b), "event")) { cudaEventDestroy(a); return s; }
@@ -1591,6 +2131,28 @@ int dmr_batch_launch_count(const dmr_batch* b, int64_t* n) {
 const char* dmr_batch_last_error(const dmr_batch* b) {
   if (!b) return g_err.c_str();
   return b->b->err.c_str();
+}
+
+size_t dmr_adjoint_checkpoint_bytes(const dmr_ctx* ctx, int64_t n_steps, int64_t K) {
+  if (!ctx) return 0;
+  return ctx->e->adj_ckpt_bytes(n_steps, K);
+}
+
+int dmr_adjoint_record(dmr_ctx* ctx, int64_t n_steps, int64_t K, void* ckpt, size_t bytes) {
+  CTX_OR_FAIL(ctx);
+  return ctx->e->adj_record(n_steps, K, ckpt, bytes);
+}
+
+size_t dmr_adjoint_workspace_bytes(const dmr_ctx* ctx) {
+  if (!ctx) return 0;
+  return ctx->e->adj_bytes();
+}
+
+int dmr_adjoint_backward(dmr_ctx* ctx, const void* dL_dn, void* ws, size_t bytes, void* ckpt,
+                         size_t ckpt_bytes, double* dL_dE0, double* dL_dnu_scale, void* dL_dseed) {
+  CTX_OR_FAIL(ctx);
+  if (!dL_dn) return ctx->e->fail(DMR_EINVAL, "null dL/dn");
+  return ctx->e->adj_backward(dL_dn, ws, bytes, ckpt, ckpt_bytes, dL_dE0, dL_dnu_scale, dL_dseed);
 }
 
 }  // extern "C"

@@ -78,6 +78,11 @@ def load():
         "dmr_launch_count": (c_int, [P, POINTER(c_int64)]),
         "dmr_sync": (c_int, [P]),
         "dmr_electron_total_noalloc": (c_int, [P, c_int32, c_int32, c_int32, c_double, P, P]),
+        "dmr_adjoint_checkpoint_bytes": (c_size_t, [P, c_int64, c_int64]),
+        "dmr_adjoint_record": (c_int, [P, c_int64, c_int64, P, c_size_t]),
+        "dmr_adjoint_workspace_bytes": (c_size_t, [P]),
+        "dmr_adjoint_backward": (c_int, [P, P, P, c_size_t, P, c_size_t, POINTER(c_double),
+                                         POINTER(c_double), P]),
         "dmr_batch_workspace_bytes": (c_size_t, [POINTER(DmrConfig), c_int32]),
         "dmr_batch_create": (c_int, [POINTER(DmrConfig), c_int32, P, c_size_t, P, POINTER(P)]),
         "dmr_batch_destroy": (None, [P]),
@@ -287,6 +292,30 @@ class Run:
         self._check(self.lib.dmr_write(self.ctx, FIELDS[field], level,
                                        c_void_p(src_tensor.data_ptr()),
                                        src_tensor.numel() * src_tensor.element_size(), 1))
+
+    # -- adjoint ------------------------------------------------------------------
+    def adjoint_record(self, n_steps, K):
+        """Advance n_steps keeping checkpoints every K steps; returns the
+        checkpoint buffer (a device tensor owned by the caller)."""
+        import torch
+        nb = self.lib.dmr_adjoint_checkpoint_bytes(self.ctx, int(n_steps), int(K))
+        ckpt = torch.empty(max(int(nb), 1), dtype=torch.uint8, device=self.device)
+        self._check(self.lib.dmr_adjoint_record(self.ctx, int(n_steps), int(K),
+                                                c_void_p(ckpt.data_ptr()), c_size_t(nb)))
+        return ckpt
+
+    def adjoint_backward(self, dL_dn, ckpt, dseed):
+        """dL/dn (device, dense coarse node map) -> (dL/dE0, dL/ds_nu); the
+        seed-map gradient is written into the device tensor dseed."""
+        import torch
+        nb = self.lib.dmr_adjoint_workspace_bytes(self.ctx)
+        ws = torch.empty(max(int(nb), 1), dtype=torch.uint8, device=self.device)
+        dE0, dnu = c_double(), c_double()
+        self._check(self.lib.dmr_adjoint_backward(
+            self.ctx, c_void_p(dL_dn.data_ptr()), c_void_p(ws.data_ptr()), c_size_t(nb),
+            c_void_p(ckpt.data_ptr()), c_size_t(ckpt.numel()), byref(dE0), byref(dnu),
+            c_void_p(dseed.data_ptr()) if dseed is not None else None))
+        return dE0.value, dnu.value
 
     def stats(self):
         out = (c_double * len(STATS))()

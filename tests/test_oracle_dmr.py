@@ -185,3 +185,31 @@ def test_capacity_error():
     sim = O.Sim(cfg, rect=w["rect"])
     with pytest.raises(O.CapacityError):
         sim._expand((0, 0, 40, 32))
+
+
+def test_p12_oracle_complex_step_matches_central_differences():
+    """P12 reference: the oracle runs on complex128, so a complex step gives
+    dL/dE0 exact to rounding; it must agree with central differences (h = 1e-6
+    relative) to the FD truncation error, with the schedule replayed."""
+    w = W.small_dmr()
+    base = O.sim_from_workload(w)
+    seed = base.fine.n.copy()
+    steps = 2 * w["cfg"]["steps_per_period"]
+
+    def run(E0, log=None, dtype=np.float64):
+        sim = O.Sim(dict(w["cfg"], E0=E0), rect=w["rect"], dtype=dtype)
+        sim.seed_map(seed.astype(dtype), 0, 0)
+        if log is not None:
+            sim.replay = list(log)
+        sim.advance(steps)
+        return sim
+
+    ref = run(5e6)
+    target = 0.9 * ref.coarse.n
+    L = lambda s: np.sum((s.coarse.n - target) ** 2)
+    h = 5e6 * 1e-20
+    cs = L(run(complex(5e6, h), ref.log, np.complex128)).imag / h
+    hf = 5e6 * 1e-6
+    fd = (L(run(5e6 + hf, ref.log)) - L(run(5e6 - hf, ref.log))) / (2 * hf)
+    assert abs(cs / fd - 1) < 1e-8
+    assert abs(L(run(complex(5e6, h), ref.log, np.complex128)).real / L(ref) - 1) < 1e-14
