@@ -250,6 +250,60 @@ def run_batch(args):
     return 0
 
 
+def run_adjoint(args):
+    """Adjoint workload: DMR r=2 on coarse 512^2 (FP32), 4096 coarse steps with
+    the refinement schedule recorded, loss = L2 mismatch of n at t_end to a
+    target from a perturbed seed map, gradients w.r.t. E0, the 65x65-node seed
+    map and s_nu, checkpoints every 256 steps.  Timed: forward with recording
+    plus the backward sweep."""
+    import torch
+    from paper_2105_13276_gb300 import build as B
+    B.build()
+    from paper_2105_13276_gb300 import adjoint as AD
+    from paper_2105_13276_gb300 import dmr as D
+    from paper_2105_13276_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    w = W.dmr_512_r2(precision=1)
+    cfg = w["cfg"]
+    steps = args.steps if args.steps != 2200 else 4096
+    K = 256
+    base = D.run_from_workload(w, device=dev)
+    seed = torch.tensor(base.read("n", 1), device=dev)
+    del base
+    pert = torch.tensor(W.adjoint_target_map(tuple(seed.shape)), dtype=seed.dtype, device=dev)
+    with torch.no_grad():
+        tgt = AD.dmr_density(torch.tensor(cfg["E0"], dtype=torch.float64),
+                             torch.tensor(1.0, dtype=torch.float64), seed * pert, cfg, w["rect"],
+                             steps, K)
+    E0 = torch.tensor(cfg["E0"], dtype=torch.float64, requires_grad=True)
+    nu = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    sm = seed.clone().requires_grad_(True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    n_end = AD.dmr_density(E0, nu, sm, cfg, w["rect"], steps, K)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    L = ((n_end.double() - tgt.double()) ** 2).sum()
+    L.backward()
+    torch.cuda.synchronize(dev)
+    t2 = time.perf_counter()
+    upp = (cfg["r"] * cfg["nx"]) * (cfg["r"] * cfg["ny"]) * cfg["r"]
+    line = {"metric": METRIC, "value": steps * upp / (t2 - t0), "unit": UNIT, "n_gpus": 1,
+            "steps": steps, "warmup": 0, "ms_per_step": 1e3 * (t2 - t0) / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "adjoint: DMR r=2 coarse 512x512, %d coarse steps, checkpoints every %d"
+                                   % (steps, K),
+                       "forward_record_s": t1 - t0, "backward_s": t2 - t1,
+                       "forward_only_fine_equiv_per_s": steps * upp / (t1 - t0),
+                       "loss": L.item(), "dL_dE0": E0.grad.item(), "dL_dnu_scale": nu.grad.item(),
+                       "dL_dseed_norm": float(sm.grad.norm().item()),
+                       "note": "value = fine-equivalent cell-updates of the forward steps / "
+                               "(forward with recording + backward) wall time"}}
+    print(json.dumps(line))
+    return 0
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -281,6 +335,7 @@ def run_ours(args):
     # warm-up run: graphs captured, every kernel class timed to find the dominant
     # bandwidth kernel (largest total time among classes with algorithmic bytes)
     warm = D.run_from_workload(w, device=dev)
+    wps, trial = warm.autotune()
     warm.set_graphs(True)
     warm.set_timing(True)
     warm.advance(max(Wm, 1) * NT)
@@ -317,6 +372,7 @@ def run_ours(args):
 
     # timed run: no per-kernel instrumentation
     run = D.run_from_workload(w, device=dev)
+    run.autotune()
     run.set_graphs(True)
     l0 = run.launch_count()
     ms, t_wall, clocks = timed_periods(run, True)
@@ -335,6 +391,7 @@ def run_ours(args):
     roof = None
     if dominant:
         rr = D.run_from_workload(w, device=dev)
+        rr.autotune()
         rr.set_graphs(True)
         rr.set_timing(True, classes=[dominant])
         ms_r, _, _ = timed_periods(rr, False)
@@ -357,6 +414,7 @@ def run_ours(args):
         u = W.uniform_fine_equivalent(w)
         Ku = max(1, min(args.uniform_periods, K))
         ur = D.run_from_workload(u, device=dev)
+        ur.autotune()
         ur.set_graphs(True)
         ur.advance(u["cfg"]["steps_per_period"])          # capture + warm
         ur.sync()
@@ -387,6 +445,7 @@ def run_ours(args):
         er.read_to_host("n", 1, h_nf)
         h_out = torch.empty((rc, cc), dtype=dt_, pin_memory=True)
         er2 = D.run_from_workload(dict(w, seeds=[(0.0, 0.5, 0.5, 0.1, 0.1)]), device=dev)
+        er2.autotune()
         er2.set_graphs(True)
         del er
         torch.cuda.synchronize(dev)
@@ -416,7 +475,8 @@ def run_ours(args):
 
     if rank == 0:
         c = config_of(w, args)
-        c.update({"periods_timed": K, "simulated_ns": K / cfg["freq"] * 1e9,
+        c.update({"autotuned_warps_per_sm": wps, "autotune_trial_ms": trial,
+                  "periods_timed": K, "simulated_ns": K / cfg["freq"] * 1e9,
                   "l2": "flushed (256 MB write) between timed periods",
                   "final_rect": final_rect,
                   "R_end": st["R"], "fine_cells_end": st["fine_cells"], "N_e_end": st["N_e"],
@@ -454,6 +514,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "adjoint512":
+        return run_adjoint(args)
     return run_ours(args)
 
 

@@ -200,6 +200,12 @@ int dmr_launch_count(const dmr_ctx* ctx, int64_t* launches);
 /* Wait for all work queued on the run's stream. */
 int dmr_sync(const dmr_ctx* ctx);
 
+/* Autotuner (at a period boundary): times the run's first EM launch of the
+ * present step for five strip heights (warps-per-SM targets 8, 16, 32, 48,
+ * 96) without changing the run, keeps the fastest; returns the choice and
+ * the per-candidate launch times (ms). */
+int dmr_autotune(dmr_ctx* ctx, int32_t* warps_per_sm, double trial_ms[5]);
+
 /* ---- Adjoint (reverse mode) with the refinement schedule held fixed ----
  * Gradients of a loss L(n_coarse(t_end)) with respect to the incident
  * amplitude E0, the ionization scale s_nu and the initial density map of the

@@ -272,6 +272,7 @@ struct Base {
   virtual int read(int field, int level, void* dst, size_t bytes, int dev) = 0;
   virtual int write(int field, int level, const void* src, size_t bytes, int dev) = 0;
   virtual int stats(double* out) = 0;
+  virtual int autotune(int32_t* wps, double* trial_ms) = 0;
   virtual int adj_record(int64_t n, int64_t K, void* ckpt, size_t bytes) = 0;
   virtual size_t adj_ckpt_bytes(int64_t n, int64_t K) const = 0;
   virtual size_t adj_bytes() const = 0;
@@ -1476,6 +1477,47 @@ struct Engine final : Base {
     return launched("adjoint step");
   }
 
+  // Autotuner of the strip height for this run: times the first EM launch of
+  // the present step for five warps-per-SM targets.  At a period boundary
+  // that launch adds no E^2 sample and only writes the next-level buffers, so
+  // repeating it leaves the run unchanged.
+  int autotune(int32_t* wps_out, double* trial_ms) override {
+    if (m % cfg.steps_per_period != 0) return fail(DMR_ESTATE, "autotune at a period boundary");
+    const int cand[5] = {8, 16, 32, 48, 96};
+    cudaEvent_t a, b;
+    if (int s_ = ck(cudaEventCreate(&a), "event")) return s_;
+    if (int s_ = ck(cudaEventCreate(&b), "event")) { cudaEventDestroy(a); return s_; }
+    double best = 1e30;
+    int best_w = warps_per_sm;
+    for (int c = 0; c < 5; ++c) {
+      warps_per_sm = cand[c];
+      dmr::EmArgs<T> Ac, Af;
+      em_args_for(1, m, cpar, fpar, rvalid, &Ac, has_fine ? &Af : nullptr);
+      auto launch = [&]() {
+        if (has_fine)
+          dmr::k_em2<T><<<Ac.nblk + Ac.ncfb + Af.nblk + Af.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Ac, Af);
+        else
+          dmr::k_em<T><<<Ac.nblk + Ac.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Ac);
+      };
+      for (int w = 0; w < 3; ++w) launch();
+      cudaEventRecord(a, st);
+      for (int w = 0; w < 20; ++w) launch();
+      cudaEventRecord(b, st);
+      counted(23);
+      if (int s_ = ck(cudaEventSynchronize(b), "autotune sync")) { cudaEventDestroy(a); cudaEventDestroy(b); return s_; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (trial_ms) trial_ms[c] = ms / 20.0;
+      if (ms < best) { best = ms; best_w = cand[c]; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    warps_per_sm = best_w;
+    drop_graph();
+    if (wps_out) *wps_out = best_w;
+    return launched("autotune");
+  }
+
   int stats(double* out) override {
     dmr::Ctl hc;
     if (int s = ck(cudaMemcpyAsync(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, st), "stats")) return s;
@@ -2153,6 +2195,11 @@ int dmr_adjoint_backward(dmr_ctx* ctx, const void* dL_dn, void* ws, size_t bytes
   CTX_OR_FAIL(ctx);
   if (!dL_dn) return ctx->e->fail(DMR_EINVAL, "null dL/dn");
   return ctx->e->adj_backward(dL_dn, ws, bytes, ckpt, ckpt_bytes, dL_dE0, dL_dnu_scale, dL_dseed);
+}
+
+int dmr_autotune(dmr_ctx* ctx, int32_t* warps_per_sm, double trial_ms[5]) {
+  CTX_OR_FAIL(ctx);
+  return ctx->e->autotune(warps_per_sm, trial_ms);
 }
 
 }  // extern "C"

@@ -77,6 +77,7 @@ def load():
         "dmr_kernel_class_name": (c_char_p, [c_int]),
         "dmr_launch_count": (c_int, [P, POINTER(c_int64)]),
         "dmr_sync": (c_int, [P]),
+        "dmr_autotune": (c_int, [P, POINTER(c_int32), POINTER(c_double)]),
         "dmr_electron_total_noalloc": (c_int, [P, c_int32, c_int32, c_int32, c_double, P, P]),
         "dmr_adjoint_checkpoint_bytes": (c_size_t, [P, c_int64, c_int64]),
         "dmr_adjoint_record": (c_int, [P, c_int64, c_int64, P, c_size_t]),
@@ -236,6 +237,13 @@ class Run:
         n = c_int64()
         self._check(self.lib.dmr_launch_count(self.ctx, byref(n)))
         return n.value
+
+    def autotune(self):
+        """Pick the strip height by timed trial launches (at a period boundary)."""
+        w = c_int32()
+        ms = (c_double * 5)()
+        self._check(self.lib.dmr_autotune(self.ctx, byref(w), ms))
+        return w.value, list(ms)
 
     def sync(self):
         self._check(self.lib.dmr_sync(self.ctx))

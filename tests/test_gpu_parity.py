@@ -223,3 +223,19 @@ def test_timing_counts_launches():
     fr = run.get_patch()
     pts = (2 * (fr[2] - fr[0]) + 1) * (2 * (fr[3] - fr[1]) + 1)
     assert n == 64 and nbytes <= 64 * pts * 60
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotune_leaves_run_unchanged(precision):
+    w = W.small_dmr(precision=precision)
+    a = D.run_from_workload(w)
+    b = D.run_from_workload(w)
+    a.advance(32)
+    b.advance(32)
+    wps, ms = b.autotune()
+    assert wps in (8, 16, 32, 48, 96) and all(t > 0 for t in ms)
+    a.advance(2 * 32 + 7)
+    b.advance(2 * 32 + 7)
+    for level in (0, 1):
+        for name in FIELDS + ("S2",):
+            assert np.array_equal(a.read(name, level), b.read(name, level)), (level, name)
