@@ -206,6 +206,11 @@ int dmr_sync(const dmr_ctx* ctx);
  * the per-candidate launch times (ms). */
 int dmr_autotune(dmr_ctx* ctx, int32_t* warps_per_sm, double trial_ms[5]);
 
+/* Set the strip height of the EM launches directly, as a warps-per-SM target
+ * in [1, 1024] (e.g. the choice dmr_autotune made on an earlier run of the
+ * same size).  Results do not depend on it.  DMR_EINVAL otherwise. */
+int dmr_set_launch_shape(dmr_ctx* ctx, int32_t warps_per_sm);
+
 /* ---- Adjoint (reverse mode) with the refinement schedule held fixed ----
  * Gradients of a loss L(n_coarse(t_end)) with respect to the incident
  * amplitude E0, the ionization scale s_nu and the initial density map of the

@@ -273,6 +273,7 @@ struct Base {
   virtual int write(int field, int level, const void* src, size_t bytes, int dev) = 0;
   virtual int stats(double* out) = 0;
   virtual int autotune(int32_t* wps, double* trial_ms) = 0;
+  virtual void set_shape(int wps) = 0;
   virtual int adj_record(int64_t n, int64_t K, void* ckpt, size_t bytes) = 0;
   virtual size_t adj_ckpt_bytes(int64_t n, int64_t K) const = 0;
   virtual size_t adj_bytes() const = 0;
@@ -454,6 +455,9 @@ struct Engine final : Base {
     const double dx = rr == 1 ? d.dxc : d.dxf;
     q.dx2 = dx * dx;
     q.r_ei = d.r_ei;
+    q.invN = 1.0 / q.N;
+    q.invg = 1.0 / q.g;
+    q.inv_hp = 1.0 / q.hp;
     return q;
   }
 
@@ -1481,6 +1485,11 @@ struct Engine final : Base {
   // the present step for five warps-per-SM targets.  At a period boundary
   // that launch adds no E^2 sample and only writes the next-level buffers, so
   // repeating it leaves the run unchanged.
+  void set_shape(int wps) override {
+    warps_per_sm = wps;
+    drop_graph();
+  }
+
   int autotune(int32_t* wps_out, double* trial_ms) override {
     if (m % cfg.steps_per_period != 0) return fail(DMR_ESTATE, "autotune at a period boundary");
     const int cand[5] = {8, 16, 32, 48, 96};
@@ -2059,6 +2068,13 @@ int dmr_set_graphs(dmr_ctx* ctx, int enable) {
   CTX_OR_FAIL(ctx);
   ctx->e->graphs = enable != 0;
   if (!enable) ctx->e->drop_graph();
+  return DMR_OK;
+}
+
+int dmr_set_launch_shape(dmr_ctx* ctx, int32_t warps_per_sm) {
+  CTX_OR_FAIL(ctx);
+  if (warps_per_sm < 1 || warps_per_sm > 1024) return ctx->e->fail(DMR_EINVAL, "warps_per_sm outside [1, 1024]");
+  ctx->e->set_shape(warps_per_sm);
   return DMR_OK;
 }
 

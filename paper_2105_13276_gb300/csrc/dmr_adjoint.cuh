@@ -270,9 +270,9 @@ __global__ void ka_rates_d(const T* n, const double* S2f, Dens d, double A1, int
   if (i > nx || j > ny) return;
   const int id = j * p + i;
   const double s2 = S2f[id];
-  const double erms2 = s2 / d.N;
-  const double eeff = sqrt(erms2 / d.g);
-  const T x = (T)(eeff / d.hp);
+  const double e2 = eeff2_of(s2, d);
+  const double eeff = sqrt(e2);
+  const T x = ehp_of<T>(e2, d);
   T nui = T(0), dn = T(0), per_s = T(0);
   if (x > T(0)) {
     const T ex = exp(T(-73.0) * pow(x, T(-0.44)));

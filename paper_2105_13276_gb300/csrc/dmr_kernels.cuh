@@ -513,7 +513,19 @@ struct Dens {
   double T;          // period
   double dx2;        // dx^2
   double r_ei;
+  double invN, invg, inv_hp;   // 1/N, 1/g, 1/hp
 };
+
+// E_eff^2 of a node from its FP64 running E^2 sum of the period:
+// E_rms^2 = S2 / N, E_eff^2 = E_rms^2 / (1 + (w/nu_m)^2) (Sec. II.B).  FP64
+// multiplies by host reciprocals: divides and square roots in FP64 are slow
+// software sequences on this GPU.
+__device__ __forceinline__ double eeff2_of(double s2, const Dens& d) { return s2 * d.invN * d.invg; }
+
+// E_eff / p in V/(cm Torr), the argument of the ionization fit, in the run's
+// precision
+template <class T>
+__device__ __forceinline__ T ehp_of(double e2, const Dens& d) { return sqrt((T)e2) * (T)d.inv_hp; }
 
 // composite trapezoid weight of node (i, j): coarse mesh outside the
 // rectangle, fine mesh inside it
@@ -574,10 +586,9 @@ __global__ void k_rates(Mesh<T> m, Step<T> c, Dens d, Wts w, T* D, T* nu, double
   double contrib = 0.0;
   if (i <= m.nx && j <= m.ny) {
     const int id = j * m.p + i;
-    double s2 = m.S2[id] + (double)node_e2(m, c, i, j);
-    double erms2 = s2 / d.N;
-    double eeff = sqrt(erms2 / d.g);
-    T x = (T)(eeff / d.hp);
+    const double s2 = m.S2[id] + (double)node_e2(m, c, i, j);
+    const double e2 = eeff2_of(s2, d);
+    const T x = ehp_of<T>(e2, d);
     T nui = (x > T(0)) ? (T)d.A * exp(T(-73.0) * pow(x, T(-0.44))) : T(0);
     T n = m.n[id];
     T wp2 = n * (T)d.wp2c;
@@ -585,7 +596,7 @@ __global__ void k_rates(Mesh<T> m, Step<T> c, Dens d, Wts w, T* D, T* nu, double
     T den = nui * (T)d.nu_m + wp2;
     D[id] = (den == T(0)) ? (T)d.De : num / den;
     nu[id] = nui - (T)d.nu_a;
-    contrib = trap_w(w, i, j) * (double)n * d.heat * eeff * eeff;
+    contrib = trap_w(w, i, j) * (double)n * d.heat * e2;
     m.S2[id] = 0.0;
   }
   double s = block_sum(contrib);

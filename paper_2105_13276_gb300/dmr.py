@@ -71,6 +71,7 @@ def load():
         "dmr_write": (c_int, [P, c_int, c_int, P, c_size_t, c_int]),
         "dmr_stats": (c_int, [P, POINTER(c_double)]),
         "dmr_set_graphs": (c_int, [P, c_int]),
+        "dmr_set_launch_shape": (c_int, [P, c_int32]),
         "dmr_set_timing": (c_int, [P, c_int]),
         "dmr_kernel_time": (c_int, [P, c_int, POINTER(c_double), POINTER(c_int64),
                                     POINTER(c_double)]),
@@ -207,6 +208,10 @@ class Run:
 
     def set_graphs(self, on=True):
         self._check(self.lib.dmr_set_graphs(self.ctx, int(bool(on))))
+
+    def set_launch_shape(self, warps_per_sm):
+        """Strip height of the EM launches as a warps-per-SM target."""
+        self._check(self.lib.dmr_set_launch_shape(self.ctx, int(warps_per_sm)))
 
     def set_timing(self, on=True, classes=None):
         """Time every kernel class (on=True), none (on=False) or the named

@@ -105,6 +105,28 @@ def test_dmr_fp64_growth_matches_oracle(rect):
     assert sim.log[-1] != tuple(rect) or rect == (0, 0, 10, 9)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_dmr_many_strips_match_oracle(precision):
+    """Meshes several warp strips wide on both levels, with strips inside
+    the mesh, at its edges and over the restricted region; growth
+    free-running in FP64, the oracle's log replayed in FP32."""
+    w = W.small_dmr(nx=128, ny=96, rect=(40, 30, 80, 62), precision=precision)
+    sim = O.sim_from_workload(w)
+    NT = w["cfg"]["steps_per_period"]
+    run = D.run_from_workload(w)
+    if precision:
+        ref = O.sim_from_workload(w)
+        ref.advance(2 * NT + 7)
+        run.replay_log(ref.log)
+    for _ in range(2):
+        sim.advance(NT)
+        run.advance(NT)
+        assert run.get_patch() == tuple(sim.rect)
+    sim.advance(7)
+    run.advance(7)
+    compare(run, sim, TOL64 if precision == 0 else TOL32)
+
+
 def test_fp32_against_fp64_oracle_with_replay():
     w = W.small_dmr(precision=1)
     sim = O.sim_from_workload(w)
@@ -153,6 +175,28 @@ def test_graphs_equal_direct_launches(precision):
         for name in FIELDS:
             assert np.array_equal(a.read(name, level), b.read(name, level)), (level, name)
     assert b.launch_count() > 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_launch_shapes_give_identical_results(precision):
+    """Every strip height the autotuner may pick (and one row per warp) gives
+    the same bits, graphs on, through growth."""
+    w = W.small_dmr(precision=precision)
+    ref = D.run_from_workload(w)
+    ref.set_graphs(True)
+    ref.advance(3 * 32 + 5)
+    for wps in (1, 8, 16, 96, 1024):
+        run = D.run_from_workload(w)
+        run.set_graphs(True)
+        run.set_launch_shape(wps)
+        run.advance(3 * 32 + 5)
+        assert run.get_patch() == ref.get_patch()
+        for level in (0, 1):
+            for name in FIELDS + ("S2",):
+                assert np.array_equal(run.read(name, level), ref.read(name, level)), (wps, level, name)
+    with pytest.raises(D.DMRError) as e:
+        ref.set_launch_shape(0)
+    assert e.value.code == D.EINVAL
 
 
 def test_vacuum_stays_exactly_zero():
