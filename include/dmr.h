@@ -202,8 +202,9 @@ int dmr_sync(const dmr_ctx* ctx);
 
 /* Autotuner (at a period boundary): times the run's first EM launch of the
  * present step for five strip heights (warps-per-SM targets 8, 16, 32, 48,
- * 96) without changing the run, keeps the fastest; returns the choice and
- * the per-candidate launch times (ms). */
+ * 96) without changing the run -- 20 back-to-back copies of the launch are
+ * captured in a CUDA graph and replayed, as the periods are -- keeps the
+ * fastest; returns the choice and the per-candidate mean launch times (ms). */
 int dmr_autotune(dmr_ctx* ctx, int32_t* warps_per_sm, double trial_ms[5]);
 
 /* Set the strip height of the EM launches directly, as a warps-per-SM target
@@ -268,8 +269,8 @@ int dmr_batch_set_graphs(dmr_batch* b, int enable);
 
 /* Autotuner (at a period boundary): times the batched EM launch for five
  * strip heights (warps-per-SM targets 8, 16, 32, 48, 96) on the present
- * state without changing it, keeps the fastest; returns the choice and the
- * per-candidate launch times (ms). */
+ * state without changing it (5 copies per CUDA graph replay), keeps the
+ * fastest; returns the choice and the per-candidate mean launch times (ms). */
 int dmr_batch_autotune(dmr_batch* b, int32_t* warps_per_sm, double trial_ms[5]);
 int dmr_batch_launch_count(const dmr_batch* b, int64_t* launches);
 const char* dmr_batch_last_error(const dmr_batch* b);

@@ -28,6 +28,42 @@ constexpr double PI = 3.14159265358979323846;
 
 thread_local std::string g_err;
 
+constexpr int kTrialLaunches = 20;   // launches per autotuner trial graph
+
+// Mean duration (ms) of one of n back-to-back launches made by `launch`,
+// captured in a CUDA graph on st and replayed (best of three timed replays
+// after one untimed): the periods run as graphs too, and direct launches of
+// small kernels would measure the host's launch rate instead.
+template <class F>
+cudaError_t graph_time(cudaStream_t st, F&& launch, int n, float* ms_out) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  for (int w = 0; w < n; ++w) launch();
+  e = cudaStreamEndCapture(st, &g);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t a = nullptr, b = nullptr;
+  e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+    e = cudaEventRecord(a, st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess && rep > 0 && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best) best = ms;
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaGraphExecDestroy(ge);
+  *ms_out = best / (float)n;
+  return e;
+}
+
 std::string fmt(const char* f, ...) {
   char buf[512];
   va_list ap;
@@ -491,10 +527,12 @@ struct Engine final : Base {
     A.gx = (src.nx + 1 + dmr::STRIP_W - 1) / dmr::STRIP_W;
     const int sy = (src.ny + 1 + A.rows - 1) / A.rows;
     A.nblk = A.gx * ((sy + dmr::EM_WARPS - 1) / dmr::EM_WARPS);
-    int ncf = 0;
+    A.ncfb = 0;   // blocks per coarse-fine side (em_cfb)
     for (int q = 0; q < 4; ++q)
-      if (b.mode[q] == dmr::BC_CFB) ncf += (q == dmr::SIDE_BOTTOM || q == dmr::SIDE_TOP) ? src.nx : src.ny;
-    A.ncfb = (ncf + 32 * dmr::EM_WARPS - 1) / (32 * dmr::EM_WARPS);
+      if (b.mode[q] == dmr::BC_CFB) {
+        const int len = (q == dmr::SIDE_BOTTOM || q == dmr::SIDE_TOP) ? src.nx : src.ny;
+        A.ncfb += (len + 32 * dmr::EM_WARPS - 1) / (32 * dmr::EM_WARPS);
+      }
     return A;
   }
 
@@ -1493,9 +1531,6 @@ struct Engine final : Base {
   int autotune(int32_t* wps_out, double* trial_ms) override {
     if (m % cfg.steps_per_period != 0) return fail(DMR_ESTATE, "autotune at a period boundary");
     const int cand[5] = {8, 16, 32, 48, 96};
-    cudaEvent_t a, b;
-    if (int s_ = ck(cudaEventCreate(&a), "event")) return s_;
-    if (int s_ = ck(cudaEventCreate(&b), "event")) { cudaEventDestroy(a); return s_; }
     double best = 1e30;
     int best_w = warps_per_sm;
     for (int c = 0; c < 5; ++c) {
@@ -1508,19 +1543,12 @@ struct Engine final : Base {
         else
           dmr::k_em<T><<<Ac.nblk + Ac.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Ac);
       };
-      for (int w = 0; w < 3; ++w) launch();
-      cudaEventRecord(a, st);
-      for (int w = 0; w < 20; ++w) launch();
-      cudaEventRecord(b, st);
-      counted(23);
-      if (int s_ = ck(cudaEventSynchronize(b), "autotune sync")) { cudaEventDestroy(a); cudaEventDestroy(b); return s_; }
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, a, b);
-      if (trial_ms) trial_ms[c] = ms / 20.0;
+      if (int s_ = ck(graph_time(st, launch, kTrialLaunches, &ms), "autotune trial")) return s_;
+      launches += 4 * kTrialLaunches;
+      if (trial_ms) trial_ms[c] = ms;
       if (ms < best) { best = ms; best_w = cand[c]; }
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     warps_per_sm = best_w;
     drop_graph();
     if (wps_out) *wps_out = best_w;
@@ -1854,28 +1882,18 @@ struct Batch final : BatchBase {
     if (int s = check_state()) return s;
     if (m % NT != 0) return fail(DMR_ESTATE, "autotune at a period boundary");
     const int cand[5] = {8, 16, 32, 48, 96};
-    cudaEvent_t a, b;
-    if (int s = ck(cudaEventCreate(&a), "event")) return s;
-    if (int s = ck(cudaEventCreate(&b), "event")) { cudaEventDestroy(a); return s; }
     double best = 1e30;
     int best_w = 48;
     for (int c = 0; c < 5; ++c) {
       for (auto* e : runs) e->warps_per_sm = cand[c];
-      if (int s = build_tables()) { cudaEventDestroy(a); cudaEventDestroy(b); return s; }
+      if (int s = build_tables()) return s;
       const Tab& t = t1[first_pending ? 1 : 0][m & 1];
-      for (int w = 0; w < 3; ++w) launch_em(t, m, 1);
-      cudaEventRecord(a, st);
-      for (int w = 0; w < 10; ++w) launch_em(t, m, 1);
-      cudaEventRecord(b, st);
-      if (int s = ck(cudaEventSynchronize(b), "autotune sync")) { cudaEventDestroy(a); cudaEventDestroy(b); return s; }
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, a, b);
-      tune_ms[c] = ms / 10.0;
-      launches += 13;
+      if (int s = ck(graph_time(st, [&]() { launch_em(t, m, 1); }, 5, &ms), "autotune trial")) return s;
+      tune_ms[c] = ms;
+      launches += 4 * 5;
       if (tune_ms[c] < best) { best = tune_ms[c]; best_w = cand[c]; }
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     for (auto* e : runs) e->warps_per_sm = best_w;
     tuned_wps = best_w;
     return build_tables();

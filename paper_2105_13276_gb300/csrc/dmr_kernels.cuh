@@ -181,27 +181,34 @@ __device__ __forceinline__ T coarse_new(const Bnd<T>& b, int sd, int k) {
 
 // Eq. 5b for tangential sample q of side sd of the fine rectangle.  The
 // fine sample sits at coarse position start + (q + 1/2)/r - 1/2 along the
-// line = start + (2q + 1 - r)/(2r), split exactly into an index and a weight.
+// line = start + (2q + 1 - r)/(2r), split exactly into an index i0 and a
+// weight xp (clamped to the line).
 template <class T>
-__device__ __forceinline__ T cfb_value(const Bnd<T>& b, int sd, int q) {
+__device__ __forceinline__ int cfb_pos(const Bnd<T>& b, int sd, int q, T* xp_out) {
   const int num = 2 * q + 1 - b.r, den = 2 * b.r;
   const int fl = (num >= 0) ? num / den : -((-num + den - 1) / den);
   int i0 = b.start[sd] + fl;
   T xp = (T)(num - fl * den) / (T)den;
   if (i0 < 0) { i0 = 0; xp = T(0); }
   if (i0 > b.len[sd] - 2) { i0 = b.len[sd] - 2; xp = T(1); }
+  *xp_out = xp;
+  return i0;
+}
+
+// Eq. 5b: the coarse tangential E at level n (old line) interpolated in
+// space at the sample, lo, blended in time with the level-n+1 one from n0, n1
+// at coarse positions i0, i0 + 1.
+template <class T>
+__device__ __forceinline__ T cfb_old(const Bnd<T>& b, int sd, int i0, T xp) {
   const T one = T(1);
   const T* o = b.old_line[sd];
   const int s = b.stride[sd];
-  const T lo = o[i0 * s] * (one - xp) + o[(i0 + 1) * s] * xp;
-  T n0, n1;
-  if (b.recompute) {
-    n0 = coarse_new(b, sd, i0);
-    n1 = coarse_new(b, sd, i0 + 1);
-  } else {
-    n0 = b.new_line[sd][i0 * s];
-    n1 = b.new_line[sd][(i0 + 1) * s];
-  }
+  return o[i0 * s] * (one - xp) + o[(i0 + 1) * s] * xp;
+}
+
+template <class T>
+__device__ __forceinline__ T cfb_blend(const Bnd<T>& b, T lo, T xp, T n0, T n1) {
+  const T one = T(1);
   const T ln = n0 * (one - xp) + n1 * xp;
   return (one - b.frac) * lo + b.frac * ln;
 }
@@ -261,28 +268,50 @@ __device__ __forceinline__ void em_set_level(EmArgs<T>& A, long long m, int k) {
   }
 }
 
-// Tangential E of the coarse-fine sides at the new level (a6, Eq. 5b), one
-// thread per boundary edge.  It depends only on the coarse lines, not on this
-// sub-step's interior update, so it runs as separate blocks of the same launch.
+// Tangential E of the coarse-fine sides at the new level (a6, Eq. 5b).  It
+// depends only on the coarse lines, not on this sub-step's interior update,
+// so it runs as separate blocks of the same launch: one block per 32 *
+// EM_WARPS consecutive samples of one side.  For the first sub-step of a
+// coarse step (recompute) the coarse E^{n+1} at the positions the block's
+// samples use is evaluated once per position into shared memory, then
+// blended; later sub-steps read the stored level-n+1 line.
 template <class T>
 __device__ __forceinline__ void em_cfb(const EmArgs<T>& A, int blk) {
-  int q = blk * (32 * EM_WARPS) + (int)threadIdx.x;
+  constexpr int NTH = 32 * EM_WARPS;
+  __shared__ T cn[NTH + 2];
   const int nfx = A.m.nx, nfy = A.m.ny, p = A.m.p;
   const int order[4] = {SIDE_BOTTOM, SIDE_TOP, SIDE_LEFT, SIDE_RIGHT};
+  int sd = -1, len = 0;
   for (int k = 0; k < 4; ++k) {
-    const int sd = order[k];
-    if (A.b.mode[sd] != BC_CFB) continue;
-    const int len = (sd == SIDE_BOTTOM || sd == SIDE_TOP) ? nfx : nfy;
-    if (q < len) {
-      const T v = cfb_value(A.b, sd, q);
-      if (sd == SIDE_BOTTOM) A.dEx[q] = v;
-      else if (sd == SIDE_TOP) A.dEx[nfy * p + q] = v;
-      else if (sd == SIDE_LEFT) A.dEy[q * p] = v;
-      else A.dEy[q * p + nfx] = v;
-      return;
-    }
-    q -= len;
+    if (A.b.mode[order[k]] != BC_CFB) continue;
+    len = (order[k] == SIDE_BOTTOM || order[k] == SIDE_TOP) ? nfx : nfy;
+    const int nb = (len + NTH - 1) / NTH;
+    if (blk < nb) { sd = order[k]; break; }
+    blk -= nb;
   }
+  if (sd < 0) return;                          // whole block
+  const int qa = blk * NTH, qb = min(qa + NTH, len) - 1;
+  const int q = qa + (int)threadIdx.x;
+  T xp = T(0);
+  const int i0 = cfb_pos(A.b, sd, min(q, qb), &xp);
+  const T lo = cfb_old(A.b, sd, i0, xp);        // in flight during the recompute
+  T v;
+  if (A.b.recompute) {
+    T xa;
+    const int c0 = cfb_pos(A.b, sd, qa, &xa), c1 = cfb_pos(A.b, sd, qb, &xa) + 1;
+    for (int t = threadIdx.x; t <= c1 - c0; t += NTH) cn[t] = coarse_new(A.b, sd, c0 + t);
+    __syncthreads();
+    v = cfb_blend(A.b, lo, xp, cn[i0 - c0], cn[i0 + 1 - c0]);
+  } else {
+    const T* nl = A.b.new_line[sd];
+    const int s = A.b.stride[sd];
+    v = cfb_blend(A.b, lo, xp, nl[i0 * s], nl[(i0 + 1) * s]);
+  }
+  if (q > qb) return;
+  if (sd == SIDE_BOTTOM) A.dEx[q] = v;
+  else if (sd == SIDE_TOP) A.dEx[nfy * p + q] = v;
+  else if (sd == SIDE_LEFT) A.dEy[q * p] = v;
+  else A.dEy[q * p + nfx] = v;
 }
 
 template <class T>
