@@ -201,10 +201,13 @@ int dmr_launch_count(const dmr_ctx* ctx, int64_t* launches);
 int dmr_sync(const dmr_ctx* ctx);
 
 /* Autotuner (at a period boundary): times the run's first EM launch of the
- * present step for five strip heights (warps-per-SM targets 8, 16, 32, 48,
- * 96) without changing the run -- 20 back-to-back copies of the launch are
- * captured in a CUDA graph and replayed, as the periods are -- keeps the
- * fastest; returns the choice and the per-candidate mean launch times (ms). */
+ * present step in its steady form (the coarse step reading the fine E under
+ * the rectangle, as every step but the first after a start or growth does)
+ * for five strip heights (warps-per-SM targets 8, 16, 32, 48, 96) without
+ * changing the run -- 20 back-to-back copies of the launch are captured in a
+ * CUDA graph and replayed, as the periods are; they write only next-level
+ * buffers that the next step rewrites in full -- keeps the fastest; returns
+ * the choice and the per-candidate mean launch times (ms). */
 int dmr_autotune(dmr_ctx* ctx, int32_t* warps_per_sm, double trial_ms[5]);
 
 /* Set the strip height of the EM launches directly, as a warps-per-SM target

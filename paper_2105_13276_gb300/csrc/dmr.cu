@@ -553,6 +553,7 @@ struct Engine final : Base {
       R.I0 = rect[0]; R.J0 = rect[1]; R.I1 = rect[2]; R.J1 = rect[3]; R.r = r;
       restr_bounds(&R.jlo, &R.jhi, &R.ilo, &R.ihi);
       R.fEx = fsrc.Ex; R.fEy = fsrc.Ey; R.fp = fsrc.p;   // fine level n (k = 1: the step's start)
+      R.rinv = (T)(1.0 / (double)r);
     }
     if (Ac) {
       dmr::Bnd<T> bc{};
@@ -659,7 +660,7 @@ struct Engine final : Base {
     const int h = tbeg(2, (double)(rect[2] - rect[0] + 1) * (rect[3] - rect[1] + 1) *
                               (double)(2 * cfg.r + 2) * (double)L.es);
     dmr::k_restrict<T><<<gr, dim3(BX, BY), 0, st>>>(C, F[cur], rect[0], rect[1], rect[2], rect[3],
-                                                    cfg.r, jlo, jhi, ilo, ihi);
+                                                    cfg.r, (T)(1.0 / (double)cfg.r), jlo, jhi, ilo, ihi);
     tend(h);
     counted(1);
   }
@@ -1535,8 +1536,11 @@ struct Engine final : Base {
     int best_w = warps_per_sm;
     for (int c = 0; c < 5; ++c) {
       warps_per_sm = cand[c];
+      // the steady form of the launch (coarse step reading the fine E under
+      // the rectangle), also right after the start or a growth; its output
+      // buffers are rewritten in full by the next real step
       dmr::EmArgs<T> Ac, Af;
-      em_args_for(1, m, cpar, fpar, rvalid, &Ac, has_fine ? &Af : nullptr);
+      em_args_for(1, m, cpar, fpar, has_fine, &Ac, has_fine ? &Af : nullptr);
       auto launch = [&]() {
         if (has_fine)
           dmr::k_em2<T><<<Ac.nblk + Ac.ncfb + Af.nblk + Af.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Ac, Af);
@@ -1675,14 +1679,17 @@ struct Batch final : BatchBase {
     };
     for (int first = 0; first < 2; ++first)
       for (int cp = 0; cp < 2; ++cp) {
-        std::vector<dmr::EmArgs<T>> v;
+        // all first fine sub-steps, then all coarse steps: the fine side
+        // blocks carry the longest dependent chain and are dispatched first
+        std::vector<dmr::EmArgs<T>> v, vc;
         for (auto* e : runs) {
           dmr::EmArgs<T> Ac, Af;
           const bool rv = first ? e->rvalid : e->has_fine;
           e->em_args_for(1, m, cp, 0, rv, &Ac, e->has_fine ? &Af : nullptr);
-          v.push_back(Ac);
+          vc.push_back(Ac);
           if (e->has_fine) v.push_back(Af);
         }
+        v.insert(v.end(), vc.begin(), vc.end());
         add_table(v);
       }
     for (int cp = 0; cp < 2; ++cp)
@@ -1887,7 +1894,7 @@ struct Batch final : BatchBase {
     for (int c = 0; c < 5; ++c) {
       for (auto* e : runs) e->warps_per_sm = cand[c];
       if (int s = build_tables()) return s;
-      const Tab& t = t1[first_pending ? 1 : 0][m & 1];
+      const Tab& t = t1[0][m & 1];   // steady tables (see Engine::autotune)
       float ms = 0.f;
       if (int s = ck(graph_time(st, [&]() { launch_em(t, m, 1); }, 5, &ms), "autotune trial")) return s;
       tune_ms[c] = ms;

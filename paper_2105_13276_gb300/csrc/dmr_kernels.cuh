@@ -49,6 +49,7 @@ struct Restr {
   int jlo, jhi, ilo, ihi;   // Ex rows [jlo, jhi], Ey columns [ilo, ihi]
   const T *fEx, *fEy;
   int fp;
+  T rinv;                   // 1/r (exact for r a power of two)
 };
 
 // Coarse-fine boundary (Eq. 5b) for the fine mesh: per side, Mur or the
@@ -118,7 +119,7 @@ __device__ __forceinline__ T restricted_ex(const Restr<T>& R, int i, int j) {
   const T* f = R.fEx + (size_t)(R.r * (j - R.J0)) * R.fp + R.r * (i - R.I0);
   T acc = f[0];
   for (int q = 1; q < R.r; ++q) acc = acc + f[q];
-  return acc / (T)R.r;
+  return acc * R.rinv;
 }
 
 template <class T>
@@ -126,7 +127,7 @@ __device__ __forceinline__ T restricted_ey(const Restr<T>& R, int i, int j) {
   const T* f = R.fEy + (size_t)(R.r * (j - R.J0)) * R.fp + R.r * (i - R.I0);
   T acc = f[0];
   for (int q = 1; q < R.r; ++q) acc = acc + f[(size_t)q * R.fp];
-  return acc / (T)R.r;
+  return acc * R.rinv;
 }
 
 template <class T>
@@ -317,10 +318,13 @@ __device__ __forceinline__ void em_cfb(const EmArgs<T>& A, int blk) {
 template <class T>
 __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk);
 
+// Blocks of one mesh's EM step: the coarse-fine side blocks first (the
+// longest dependent chain of the launch, so they are dispatched first), then
+// the strips.
 template <class T>
 __device__ __forceinline__ void em_segment(const EmArgs<T>& A, int blk) {
-  if (blk < A.nblk) em_strips(A, blk);
-  else em_cfb(A, blk - A.nblk);
+  if (blk < A.ncfb) em_cfb(A, blk);
+  else em_strips(A, blk - A.ncfb);
 }
 
 template <class T>
@@ -466,9 +470,6 @@ __global__ void __launch_bounds__(32 * EM_WARPS) k_em(EmArgs<T> A) {
   em_segment(A, blockIdx.x);
 }
 
-// Two independent EM steps in one launch (the coarse step and the first fine
-// sub-step, whose coarse boundary values are recomputed): blocks [0, A0.nblk)
-// run A0, the rest run A1.
 // Batched EM launch: segment s (one mesh of one run) owns blocks
 // [off[s], off[s+1]); its arguments come from a table in device memory.
 template <class T>
@@ -497,18 +498,22 @@ __global__ void __launch_bounds__(32 * EM_WARPS) k_em_batch(const EmArgs<T>* __r
   em_segment(A, (int)blockIdx.x - off[seg]);
 }
 
+// Two independent EM steps in one launch: the coarse step A0 and the first
+// fine sub-step A1, whose coarse boundary values are recomputed.  The fine
+// blocks come first in the grid (their side blocks carry the launch's
+// longest dependent chain).
 template <class T>
 __global__ void __launch_bounds__(32 * EM_WARPS) k_em2(EmArgs<T> A0, EmArgs<T> A1) {
-  const int n0 = A0.nblk + A0.ncfb;
-  if ((int)blockIdx.x < n0) em_segment(A0, blockIdx.x);
-  else em_segment(A1, blockIdx.x - n0);
+  const int n1 = A1.nblk + A1.ncfb;   // the fine sub-step's blocks first
+  if ((int)blockIdx.x < n1) em_segment(A1, blockIdx.x);
+  else em_segment(A0, blockIdx.x - n1);
 }
 
 // a8: coarse E edges of the closed rectangle (except tangential edges of
 // interior sides) = mean of the r collinear fine edges.  Grid over the
 // rectangle's coarse nodes.
 template <class T>
-__global__ void k_restrict(Mesh<T> c, Mesh<T> f, int I0, int J0, int I1, int J1, int r,
+__global__ void k_restrict(Mesh<T> c, Mesh<T> f, int I0, int J0, int I1, int J1, int r, T rinv,
                            int jlo, int jhi, int ilo, int ihi) {
   const int i = I0 + blockIdx.x * blockDim.x + threadIdx.x;
   const int j = J0 + blockIdx.y * blockDim.y + threadIdx.y;
@@ -518,13 +523,13 @@ __global__ void k_restrict(Mesh<T> c, Mesh<T> f, int I0, int J0, int I1, int J1,
     const T* s = f.Ex + (size_t)fb * f.p + fa;
     T acc = s[0];
     for (int q = 1; q < r; ++q) acc = acc + s[q];
-    c.Ex[j * c.p + i] = acc / (T)r;
+    c.Ex[j * c.p + i] = acc * rinv;
   }
   if (j < J1 && i >= ilo && i <= ihi) {
     const T* s = f.Ey + (size_t)fb * f.p + fa;
     T acc = s[0];
     for (int q = 1; q < r; ++q) acc = acc + s[(size_t)q * f.p];
-    c.Ey[j * c.p + i] = acc / (T)r;
+    c.Ey[j * c.p + i] = acc * rinv;
   }
 }
 

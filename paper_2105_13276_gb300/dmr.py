@@ -24,6 +24,8 @@ STATUS_NAMES = {0: "DMR_OK", -1: "DMR_EINVAL", -2: "DMR_ECAPACITY", -3: "DMR_ECU
 FIELDS = {"Ex": 0, "Ey": 1, "Hz": 2, "vx": 3, "vy": 4, "n": 5, "S2": 6, "mask": 7}
 STATS = ["t", "R", "fine_cells", "N_e", "P_abs", "W_abs", "periods", "coarse_steps", "n_max",
          "flags"]
+# strip heights the autotuners try, as warps-per-SM targets (trial_ms order)
+TUNE_WPS = (8, 16, 32, 48, 96)
 
 C0 = 299792458.0
 
