@@ -301,9 +301,19 @@ def run_adjoint(args):
         tgt = AD.dmr_density(torch.tensor(cfg["E0"], dtype=torch.float64),
                              torch.tensor(1.0, dtype=torch.float64), seed * pert, cfg, w["rect"],
                              steps, K)
-    E0 = torch.tensor(cfg["E0"], dtype=torch.float64, requires_grad=True)
-    nu = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
-    sm = seed.clone().requires_grad_(True)
+    def grads():
+        E0 = torch.tensor(cfg["E0"], dtype=torch.float64, requires_grad=True)
+        nu = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+        sm = seed.clone().requires_grad_(True)
+        return E0, nu, sm
+
+    # warm-up: one full untimed forward + backward of the same configuration
+    # (first use of the checkpoint and adjoint buffers, graph captures)
+    E0, nu, sm = grads()
+    n_w = AD.dmr_density(E0, nu, sm, cfg, w["rect"], steps, K)
+    ((n_w.double() - tgt.double()) ** 2).sum().backward()
+    del n_w
+    E0, nu, sm = grads()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     n_end = AD.dmr_density(E0, nu, sm, cfg, w["rect"], steps, K)
@@ -315,7 +325,7 @@ def run_adjoint(args):
     t2 = time.perf_counter()
     upp = (cfg["r"] * cfg["nx"]) * (cfg["r"] * cfg["ny"]) * cfg["r"]
     line = {"metric": METRIC, "value": steps * upp / (t2 - t0), "unit": UNIT, "n_gpus": 1,
-            "steps": steps, "warmup": 0, "ms_per_step": 1e3 * (t2 - t0) / steps,
+            "steps": steps, "warmup": steps, "ms_per_step": 1e3 * (t2 - t0) / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "adjoint: DMR r=2 coarse 512x512, %d coarse steps, checkpoints every %d"
@@ -325,7 +335,9 @@ def run_adjoint(args):
                        "loss": L.item(), "dL_dE0": E0.grad.item(), "dL_dnu_scale": nu.grad.item(),
                        "dL_dseed_norm": float(sm.grad.norm().item()),
                        "note": "value = fine-equivalent cell-updates of the forward steps / "
-                               "(forward with recording + backward) wall time"}}
+                               "(forward with recording + backward) wall time, device "
+                               "synchronised on both sides, after one untimed forward + "
+                               "backward of the same configuration"}}
     print(json.dumps(line))
     return 0
 
