@@ -88,7 +88,11 @@ typedef struct dmr_config {
                                 Courant c dt/dx = n_lambda/N_T must be <= 1/sqrt(2) */
   int32_t precision;         /* 0: FP64 everywhere; 1: FP32 fields, FP64 E^2 sums and totals */
   int32_t buffer_cells;      /* growth buffer in coarse cells [4] */
-  int32_t growth;            /* 1: flags grow the rectangle; 0: it stays fixed */
+  int32_t growth;            /* 0: the rectangle stays fixed; 1: it grows to the flags'
+                                bounding box widened by buffer_cells; 2: threshold
+                                lines (Sec. III.D): a side on which n > n_th at some
+                                coarse node moves out by m_ex (left/right) or m_ey
+                                (bottom/top) coarse cells */
   int64_t patch_cap_cells;   /* fine-cell capacity [(r nx)(r ny)] */
   double freq;               /* EM frequency f (Hz) */
   double E0;                 /* incident amplitude (V/m), E along y, incident from the left */
@@ -99,6 +103,9 @@ typedef struct dmr_config {
   double nu_a;               /* attachment frequency (1/s) [0] */
   double n_th;               /* threshold density (m^-3) [1e-3 n_crit] (Sec. III.A) */
   double g_th;               /* gradient threshold (m^-4) [n_th/(4 dx_c)] (Sec. III.B) */
+  int32_t m_ex, m_ey;        /* growth = 2: jumps along x and y in coarse cells
+                                [2 buffer_cells, buffer_cells]; the paper takes
+                                m_ex > m_ey (Sec. III.B) */
 } dmr_config;
 
 /* Bytes of device workspace a run of this configuration needs; 0 if the

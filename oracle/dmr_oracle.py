@@ -60,7 +60,7 @@ class Params:
 
     ``cfg`` is a plain dict with keys nx, ny, r, n_lambda, steps_per_period,
     freq, E0, p_torr and optional De, Da, beta_rec, Te, nu_scale, nu_a, n_th,
-    g_th, buffer_cells, growth, patch_cap_cells.  A value of None (or a
+    g_th, buffer_cells, growth, m_ex, m_ey, patch_cap_cells.  A value of None (or a
     missing key) selects the default reading.
     """
 
@@ -94,7 +94,12 @@ class Params:
         self.n_th = float(g("n_th") if g("n_th") is not None else 1e-3 * self.n_crit)
         self.g_th = float(g("g_th") if g("g_th") is not None else self.n_th / (4.0 * self.dxc))
         self.buffer = int(g("buffer_cells") if g("buffer_cells") is not None else 4)
-        self.growth = bool(g("growth") if g("growth") is not None else True)
+        # growth: 0 fixed rectangle, 1 flag bounding box + buffer, 2 threshold
+        # lines with jumps m_ex, m_ey (Sec. III.D; reading: 2 and 1 buffers)
+        gr = g("growth")
+        self.growth = 1 if gr is None else int(gr)
+        self.m_ex = int(g("m_ex") if g("m_ex") is not None else 2 * self.buffer)
+        self.m_ey = int(g("m_ey") if g("m_ey") is not None else self.buffer)
         self.cap = int(g("patch_cap_cells") if g("patch_cap_cells") is not None
                        else (self.r * self.nx) * (self.r * self.ny))
         # Sec. II.A: r_ei = beta 1e-13 (300/T_e)^(1/2), read in m^3/s.
@@ -393,6 +398,33 @@ def grow_rect(rect, bbox, buffer, nx, ny):
     return (min(rect[0], c[0]), min(rect[1], c[1]), max(rect[2], c[2]), max(rect[3], c[3]))
 
 
+def line_hits(n, rect, n_th):
+    """Threshold-line test of Sec. III.D: the threshold lines are the sides
+    of the fine rectangle (the coarse-fine boundary); a side is hit when the
+    density exceeds the threshold density at a coarse node on it (corners
+    included).  The fine boundary values are linear interpolations of these
+    nodes, so the coarse nodes hold the line's maximum.  Returns
+    (left, bottom, right, top) booleans, with the strict comparison n > n_th.
+    ``n`` is indexed [i, j]."""
+    i0, j0, i1, j1 = rect
+    a = np.real(n)
+    return (bool(np.any(a[i0, j0:j1 + 1] > n_th)), bool(np.any(a[i0:i1 + 1, j0] > n_th)),
+            bool(np.any(a[i1, j0:j1 + 1] > n_th)), bool(np.any(a[i0:i1 + 1, j1] > n_th)))
+
+
+def grow_lines(rect, hits, m_ex, m_ey, nx, ny):
+    """Expansion of Sec. III.D by threshold lines: a hit on the backward or
+    forward line (left, right side) moves that side outwards by m_ex coarse
+    cells along x, a hit on the lower or upper line (bottom, top) by m_ey
+    along y (the paper takes m_ex > m_ey); clipped to the domain, so the
+    rectangle only grows."""
+    left, bottom, right, top = hits
+    return (max(rect[0] - m_ex, 0) if left else rect[0],
+            max(rect[1] - m_ey, 0) if bottom else rect[1],
+            min(rect[2] + m_ex, nx) if right else rect[2],
+            min(rect[3] + m_ey, ny) if top else rect[3])
+
+
 # ----------------------------------------------------------------------------
 # Simulation driver: coarse mesh + one growing fine rectangle
 # ----------------------------------------------------------------------------
@@ -619,6 +651,9 @@ class Sim:
             self.masks.append(mask)
             if self.replay is not None:
                 new_rect = tuple(self.replay[self.period - 1])
+            elif P.growth == 2:
+                new_rect = grow_lines(self.rect, line_hits(c.n, self.rect, P.n_th),
+                                      P.m_ex, P.m_ey, P.nx, P.ny)
             elif P.growth:
                 new_rect = grow_rect(self.rect, mask_bbox(mask), P.buffer, P.nx, P.ny)
             else:

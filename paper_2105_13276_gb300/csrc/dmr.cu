@@ -80,6 +80,7 @@ struct Derived {
   double omega, lam, k, nu_m, dxc, dxf, dtc, dtf, De, Da, r_ei, nu_scale, nu_a, n_crit, n_th,
       g_th, T;
   int64_t cap;
+  int m_ex, m_ey;   // threshold-line jumps (growth = 2)
 };
 
 int derive(const dmr_config* c, Derived* d, std::string* err) {
@@ -90,6 +91,9 @@ int derive(const dmr_config* c, Derived* d, std::string* err) {
   if (c->precision != 0 && c->precision != 1) { *err = "precision must be 0 (fp64) or 1 (fp32)"; return DMR_EINVAL; }
   if (!(c->freq > 0) || !(c->p_torr > 0) || !std::isfinite(c->E0)) { *err = "freq and p_torr must be > 0, E0 finite"; return DMR_EINVAL; }
   if (c->buffer_cells < 0) { *err = "buffer_cells must be >= 0"; return DMR_EINVAL; }
+  if (c->growth < 0 || c->growth > 2) { *err = "growth must be 0, 1 or 2"; return DMR_EINVAL; }
+  d->m_ex = c->m_ex >= 0 ? c->m_ex : 2 * c->buffer_cells;
+  d->m_ey = c->m_ey >= 0 ? c->m_ey : c->buffer_cells;
   d->omega = 2.0 * PI * c->freq;
   d->lam = C0 / c->freq;
   d->k = d->omega / C0;
@@ -724,7 +728,8 @@ struct Engine final : Base {
     if (has_fine) {
       dmr::k_commit<T><<<gf, blk, 0, st>>>(f, f_ntmp, wf, nullptr, 0, r, part[3]);
       const double gs = 1.0 / (2.0 * d.dxc * d.g_th);
-      dmr::k_flags<T><<<gc, blk, 0, st>>>(C, (T)d.n_th, (T)gs, mask, ctl);
+      dmr::k_flags<T><<<gc, blk, 0, st>>>(C, (T)d.n_th, (T)gs, mask, ctl,
+                                          make_int4(rect[0], rect[1], rect[2], rect[3]));
       n_launch += 2;
     }
     dmr::k_finalize<<<1, 1024, 0, st>>>(part[0], (int)(gc.x * gc.y), part[1], nbf, part[2],
@@ -760,7 +765,13 @@ struct Engine final : Base {
         for (int q = 0; q < 4; ++q) nr[q] = replay[replay_pos * 4 + q];
         ++replay_pos;
       }
-    } else if (cfg.growth && hc.nflag > 0) {
+    } else if (cfg.growth == 2) {
+      // threshold lines (Sec. III.D): a hit side jumps out by m_ex / m_ey
+      if (hc.side & 1) nr[0] = std::max(rect[0] - d.m_ex, 0);
+      if (hc.side & 2) nr[1] = std::max(rect[1] - d.m_ey, 0);
+      if (hc.side & 4) nr[2] = std::min(rect[2] + d.m_ex, cfg.nx);
+      if (hc.side & 8) nr[3] = std::min(rect[3] + d.m_ey, cfg.ny);
+    } else if (cfg.growth == 1 && hc.nflag > 0) {
       const int b = cfg.buffer_cells;
       const int c4[4] = {std::max(hc.bbox[0] - b, 0), std::max(hc.bbox[1] - b, 0),
                          std::min(hc.bbox[2] + b, cfg.nx), std::min(hc.bbox[3] + b, cfg.ny)};

@@ -603,6 +603,7 @@ struct Ctl {           // device control block
   int bbox[4];         // imin, jmin, imax, jmax of the flags
   int nflag;
   int err;
+  int side;            // threshold-line hits: bit 0 left, 1 bottom, 2 right, 3 top
 };
 
 // a9 first pass: finish the period's S2 with the last level, E_eff, nu_net,
@@ -615,7 +616,7 @@ __global__ void k_rates(Mesh<T> m, Step<T> c, Dens d, Wts w, T* D, T* nu, double
   if (ctl && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
     ctl->bbox[0] = 0x7fffffff; ctl->bbox[1] = 0x7fffffff;
     ctl->bbox[2] = -1; ctl->bbox[3] = -1;
-    ctl->nflag = 0; ctl->st[4] = 0.0;
+    ctl->nflag = 0; ctl->st[4] = 0.0; ctl->side = 0;
   }
   double contrib = 0.0;
   if (i <= m.nx && j <= m.ny) {
@@ -710,7 +711,9 @@ __global__ void k_commit(Mesh<T> m, const T* nnew, Wts w, const T* fine_n, int f
 // as (dn_x s)^2 + (dn_y s)^2 > 1 with s = 1/(2 dx g_th)); uint8 mask, flag
 // bounding box and count, largest density.
 template <class T>
-__global__ void k_flags(Mesh<T> m, T n_th, T gs, uint8_t* mask, Ctl* ctl) {
+// rect: the fine rectangle's corner nodes (I0, J0, I1, J1): nodes on its
+// sides with n > n_th set the threshold-line bits (Sec. III.D)
+__global__ void k_flags(Mesh<T> m, T n_th, T gs, uint8_t* mask, Ctl* ctl, int4 rect) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i > m.nx || j > m.ny) return;
@@ -729,6 +732,12 @@ __global__ void k_flags(Mesh<T> m, T n_th, T gs, uint8_t* mask, Ctl* ctl) {
     atomicOr(&ctl->err, 1);
   } else if (dn > 0.0) {
     atomicMax((unsigned long long*)&ctl->st[4], (unsigned long long)__double_as_longlong(dn));
+  }
+  if (n > n_th) {
+    const bool in_y = j >= rect.y && j <= rect.w, in_x = i >= rect.x && i <= rect.z;
+    const int bits = (i == rect.x && in_y ? 1 : 0) | (j == rect.y && in_x ? 2 : 0) |
+                     (i == rect.z && in_y ? 4 : 0) | (j == rect.w && in_x ? 8 : 0);
+    if (bits) atomicOr(&ctl->side, bits);
   }
   if (f) {
     atomicMin(&ctl->bbox[0], i);

@@ -58,6 +58,9 @@ class Naive:
         self.nth = 1e-3 * ncrit if cfg.get("n_th") is None else cfg["n_th"]
         self.gth = self.nth / (4 * dxc) if cfg.get("g_th") is None else cfg["g_th"]
         self.buf = cfg.get("buffer_cells", 4)
+        self.mode = 1 if cfg.get("growth") is None else int(cfg["growth"])
+        self.mex = 2 * self.buf if cfg.get("m_ex") is None else cfg["m_ex"]
+        self.mey = self.buf if cfg.get("m_ey") is None else cfg["m_ey"]
         self.nl = nl
         self.c = NMesh(self.nx, self.ny, lam / nl, 1.0 / (self.f * self.NT), self.NT, 0, 0)
         self.rect = tuple(rect)
@@ -270,7 +273,28 @@ class Naive:
         self.inject()
         hits = self.flags()
         self.last_hits = hits
-        if hits:
+        if self.mode == 2:
+            # threshold lines = the rectangle's sides, node by node
+            th = self.nth
+            left = right = bottom = top = False
+            for j in range(j0, j1 + 1):
+                left = left or c.n[i0][j] > th
+                right = right or c.n[i1][j] > th
+            for i in range(i0, i1 + 1):
+                bottom = bottom or c.n[i][j0] > th
+                top = top or c.n[i][j1] > th
+            new = (i0, j0, i1, j1)
+            if left:
+                new = (max(i0 - self.mex, 0), new[1], new[2], new[3])
+            if right:
+                new = (new[0], new[1], min(i1 + self.mex, self.nx), new[3])
+            if bottom:
+                new = (new[0], max(j0 - self.mey, 0), new[2], new[3])
+            if top:
+                new = (new[0], new[1], new[2], min(j1 + self.mey, self.ny))
+            if new != self.rect:
+                self.expand(new)
+        elif hits and self.mode == 1:
             bi0 = max(min(h[0] for h in hits) - self.buf, 0)
             bj0 = max(min(h[1] for h in hits) - self.buf, 0)
             bi1 = min(max(h[0] for h in hits) + self.buf, self.nx)

@@ -46,6 +46,9 @@ def test_config_validation_host_only(lib):
         D.workspace_bytes(W.base_cfg(precision=3))
     with pytest.raises(D.DMRError, match="diffusion number"):
         D.workspace_bytes(W.base_cfg(De=1e4))
+    with pytest.raises(D.DMRError, match="growth"):
+        D.workspace_bytes(W.base_cfg(growth=3))
+    assert D.workspace_bytes(W.base_cfg(growth=2, m_ex=6, m_ey=2)) > 0
 
 
 def test_workspace_grows_with_capacity_and_precision(lib):

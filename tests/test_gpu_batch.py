@@ -85,6 +85,28 @@ def test_batched_run_matches_oracle():
                 assert rel < 1e-12, (q, level, name, rel)
 
 
+@pytest.mark.parametrize("graphs", [False, True])
+def test_batch_with_threshold_line_growth(graphs):
+    """Runs with both growth policies in one batch (Sec. III.D threshold lines
+    for two of them): each batched run equals the same run alone, and the
+    threshold-line run's rectangle log equals the FP64 oracle's."""
+    ws = mixed(0)
+    ws[1] = W.small_dmr(rect=(16, 14, 21, 18), growth=2, n_th=3e16)
+    ws[2] = W.small_dmr(nx=44, ny=36, rect=(17, 15, 20, 17), growth=2, n_th=5e16, m_ex=30, m_ey=3)
+    b = D.batch_from_workloads(ws)
+    b.set_graphs(graphs)
+    singles = [D.run_from_workload(w) for w in ws]
+    steps = 3 * 32 + 4
+    b.advance(steps)
+    for s in singles:
+        s.advance(steps)
+    for q in range(len(ws)):
+        same(b.runs[q], singles[q])
+    sim = O.sim_from_workload(ws[1])
+    sim.advance(steps)
+    assert b.runs[1].get_patch() == tuple(sim.rect) != tuple(ws[1]["rect"])
+
+
 def test_autotune_keeps_state_and_results():
     ws = mixed(1)
     a = D.batch_from_workloads(ws)

@@ -105,6 +105,29 @@ def test_dmr_fp64_growth_matches_oracle(rect):
     assert sim.log[-1] != tuple(rect) or rect == (0, 0, 10, 9)
 
 
+@pytest.mark.parametrize("rect,nth,mex,mey", [((16, 14, 21, 18), 3e16, None, None),
+                                               ((17, 15, 20, 17), 5e16, 30, 3)])
+def test_dmr_fp64_threshold_lines_match_oracle(rect, nth, mex, mey):
+    """Growth by threshold lines (Sec. III.D), free-running on both sides:
+    identical rectangles after every period (the second case clips at both
+    x edges of the domain), bit-exact masks, fields within 1e-12."""
+    w = W.small_dmr(rect=rect, growth=2, n_th=nth, m_ex=mex, m_ey=mey)
+    sim = O.sim_from_workload(w)
+    run = D.run_from_workload(w)
+    NT = w["cfg"]["steps_per_period"]
+    for p in range(3):
+        sim.advance(NT)
+        run.advance(NT)
+        assert run.get_patch() == tuple(sim.rect), (p, run.get_patch(), sim.rect)
+        assert np.array_equal(run.read("mask").T.astype(bool), sim.masks[-1]), p
+    sim.advance(5)
+    run.advance(5)
+    compare(run, sim, TOL64)
+    assert sim.log[0] != tuple(rect)
+    if mex == 30:
+        assert sim.log[0][0] == 0 and sim.log[0][2] == w["cfg"]["nx"]
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_dmr_many_strips_match_oracle(precision):
     """Meshes several warp strips wide on both levels, with strips inside

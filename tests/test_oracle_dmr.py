@@ -137,12 +137,35 @@ def test_growth_policy():
     assert O.mask_bbox(m) == (1, 2, 4, 3)
 
 
-@pytest.mark.parametrize("rect", [(3, 3, 7, 6), (0, 2, 5, 8), (4, 0, 10, 8)])
-def test_p11_naive_per_element_implementation_agrees(rect):
+def test_threshold_line_policy():
+    """Sec. III.D threshold lines: a side is hit when n > n_th at a coarse
+    node on it (corners included); hit sides jump out by m_ex (x) or m_ey
+    (y), clipped to the domain."""
+    n = np.zeros((21, 21))
+    rect = (5, 6, 12, 14)
+    assert O.line_hits(n, rect, 1.0) == (False, False, False, False)
+    n[12, 9] = 2.0                                   # on the right side
+    assert O.line_hits(n, rect, 1.0) == (False, False, True, False)
+    n[12, 9] = 1.0                                   # equal: not a hit (strict)
+    assert O.line_hits(n, rect, 1.0) == (False, False, False, False)
+    n[5, 14] = 3.0                                   # top-left corner: two sides
+    assert O.line_hits(n, rect, 1.0) == (True, False, False, True)
+    n[8, 10] = 9.0                                   # interior nodes do not count
+    n[13, 10] = 9.0                                  # nor nodes outside
+    assert O.line_hits(n, rect, 1.0) == (True, False, False, True)
+    assert O.grow_lines(rect, (True, False, False, True), 8, 4, 20, 20) == (0, 6, 12, 18)
+    assert O.grow_lines(rect, (False, True, True, False), 8, 4, 20, 20) == (5, 2, 20, 14)
+    assert O.grow_lines(rect, (True, True, True, True), 3, 2, 20, 20) == (2, 4, 15, 16)
+    assert O.grow_lines(rect, (False,) * 4, 8, 4, 20, 20) == rect
+
+
+@pytest.mark.parametrize("rect,growth", [((3, 3, 7, 6), 1), ((0, 2, 5, 8), 1), ((4, 0, 10, 8), 1),
+                                         ((4, 3, 6, 5), 2), ((5, 3, 8, 5), 2)])
+def test_p11_naive_per_element_implementation_agrees(rect, growth):
     """P11: a 10x8 coarse r=2 DMR run, a dense seed so that flags fire and the
     rectangle grows, against an independent per-element implementation."""
     cfg = W.base_cfg(nx=10, ny=8, r=2, n_lambda=8, steps_per_period=16, E0=6e6, p_torr=300.0,
-                     n_th=1e16, buffer_cells=1)
+                     n_th=1e16, buffer_cells=1, growth=growth)
     sim = O.Sim(cfg, rect=rect)
     nv = Naive(cfg, rect)
     P = sim.P
