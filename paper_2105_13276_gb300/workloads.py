@@ -121,6 +121,21 @@ def small_dmr(nx=40, ny=32, r=2, rect=(12, 10, 24, 20), precision=0, **kw):
                 seeds=[(3e17, 0.45, 0.5, 0.1, 0.1)], rect=rect, steps=None)
 
 
+def front_1p5(n_lambda, r, growth=1, precision=1):
+    """Front-velocity set-up of Sec. IV.C: a 1.5 x 1.5 wavelength domain,
+    air at 760 Torr, E0 = 5.5 MV/m at 110 GHz, Gaussian n0 = 1e16 m^-3 at
+    (0.85 Lx, 0.5 Ly) (sigma = lambda/8 here; the paper does not give it).
+    n_lambda is the coarse resolution, r the refinement factor (1: uniform);
+    the initial rectangle is lambda/4 wide around the seed."""
+    nx = int(round(1.5 * n_lambda))
+    cfg = base_cfg(nx=nx, ny=nx, r=r, n_lambda=n_lambda, steps_per_period=2 * n_lambda, E0=5.5e6,
+                   p_torr=760.0, growth=growth, precision=precision)
+    m = max(2, n_lambda // 4)
+    rect = centred_rect(nx, nx, int(0.85 * nx), nx // 2, m) if r > 1 else None
+    return dict(name="front 1.5 lambda, lambda/%d, r=%d" % (n_lambda, r), cfg=cfg,
+                seeds=[(1e16, 0.85, 0.5, 0.125, 0.125)], rect=rect, steps=None)
+
+
 def random_fields(shape, seed, scale=1.0):
     """Seeded standard-normal field values (for invariants and parity of the
     EM update with arbitrary states)."""
