@@ -470,6 +470,8 @@ __global__ void __launch_bounds__(32 * EM_WARPS) k_em(EmArgs<T> A) {
   em_segment(A, blockIdx.x);
 }
 
+constexpr int kSegStage = 256;   // segment offsets staged in shared memory up to this many
+
 // Batched EM launch: segment s (one mesh of one run) owns blocks
 // [off[s], off[s+1]); its arguments come from a table in device memory.
 template <class T>
@@ -477,14 +479,24 @@ __global__ void __launch_bounds__(32 * EM_WARPS) k_em_batch(const EmArgs<T>* __r
                                                             const int* __restrict__ off, int nseg,
                                                             long long m, int k) {
   __shared__ EmArgs<T> A;
-  __shared__ int seg;
-  if (threadIdx.x == 0) {
+  __shared__ int seg, base;
+  __shared__ int soff[kSegStage + 1];
+  const int b = (int)blockIdx.x;
+  if (nseg <= kSegStage) {
+    // one coalesced load of the offsets, then a parallel scan: the segment
+    // q with off[q] <= b < off[q+1] (empty segments never match)
+    for (int q = threadIdx.x; q <= nseg; q += blockDim.x) soff[q] = off[q];
+    __syncthreads();
+    for (int q = threadIdx.x; q < nseg; q += blockDim.x)
+      if (soff[q] <= b && b < soff[q + 1]) { seg = q; base = soff[q]; }
+  } else if (threadIdx.x == 0) {
     int lo = 0, hi = nseg - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+      if (off[mid] <= b) lo = mid; else hi = mid - 1;
     }
     seg = lo;
+    base = off[lo];
   }
   __syncthreads();
   {
@@ -495,7 +507,7 @@ __global__ void __launch_bounds__(32 * EM_WARPS) k_em_batch(const EmArgs<T>* __r
   __syncthreads();
   if (threadIdx.x == 0) em_set_level(A, m, k);
   __syncthreads();
-  em_segment(A, (int)blockIdx.x - off[seg]);
+  em_segment(A, b - base);
 }
 
 // Two independent EM steps in one launch: the coarse step A0 and the first
