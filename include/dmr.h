@@ -106,6 +106,12 @@ typedef struct dmr_config {
   int32_t m_ex, m_ey;        /* growth = 2: jumps along x and y in coarse cells
                                 [2 buffer_cells, buffer_cells]; the paper takes
                                 m_ex > m_ey (Sec. III.B) */
+  int32_t nu_model;          /* ionization frequency (Sec. II.A): 0 the air fit
+                                s_nu 5.14e11 p exp(-73 (E_eff/p)^-0.44), E_eff/p in
+                                V/(cm Torr); 1 the Townsend form s_nu gamma v_d with
+                                gamma = A p exp(-B p/E_eff), v_d = e E_eff/(m_e nu_m) */
+  double town_A, town_B;     /* nu_model = 1: A in 1/(m Torr) [1500], B in V/(m Torr)
+                                [36500] (values <= 0 select the defaults) */
 } dmr_config;
 
 /* Bytes of device workspace a run of this configuration needs; 0 if the

@@ -60,7 +60,8 @@ class Params:
 
     ``cfg`` is a plain dict with keys nx, ny, r, n_lambda, steps_per_period,
     freq, E0, p_torr and optional De, Da, beta_rec, Te, nu_scale, nu_a, n_th,
-    g_th, buffer_cells, growth, m_ex, m_ey, patch_cap_cells.  A value of None (or a
+    g_th, buffer_cells, growth, m_ex, m_ey, nu_model, town_A, town_B,
+    patch_cap_cells.  A value of None (or a
     missing key) selects the default reading.
     """
 
@@ -87,6 +88,11 @@ class Params:
         self.Te = float(g("Te") if g("Te") is not None else 300.0)
         self.nu_scale = g("nu_scale") if g("nu_scale") is not None else 1.0
         self.nu_a = float(g("nu_a") if g("nu_a") is not None else 0.0)
+        # ionization coefficient set: 0 the air fit, 1 the Townsend form with
+        # A = 15 /(cm Torr), B = 365 V/(cm Torr) by default (reading; SI here)
+        self.nu_model = int(g("nu_model") if g("nu_model") is not None else 0)
+        self.town_A = float(g("town_A") if g("town_A") is not None else 1500.0)
+        self.town_B = float(g("town_B") if g("town_B") is not None else 36500.0)
         # Sec. III.A: critical density n_c = m eps0 w^2 / e^2 (the square is
         # fixed by the quoted cutoff density ~9e20 m^-3, Sec. IV.D).
         self.n_crit = ME * EPS0 * self.omega ** 2 / QE ** 2
@@ -264,12 +270,22 @@ def accumulate_e2(P: Params, mesh: Mesh):
 # ----------------------------------------------------------------------------
 def ionization_frequency(P: Params, eeff):
     """nu_i(E_eff/p) (Sec. II.A gives nu_i - nu_a = gamma v_d with A, B, v_d
-    deferred to cited work).  Reading: the air fit
-    nu_i = s_nu 5.14e11 p exp(-73 (E_eff/p)^-0.44), E_eff/p in V/(cm Torr),
-    p in Torr; nu_i = 0 where E_eff = 0."""
-    x = eeff / (100.0 * P.p)
-    pos = np.real(x) > 0
-    xs = np.where(pos, x, 1.0)
+    deferred to cited work); nu_i = 0 where E_eff = 0.
+
+    nu_model 0 (default reading): the air fit
+      nu_i = s_nu 5.14e11 p exp(-73 (E_eff/p)^-0.44), E_eff/p in V/(cm Torr),
+      p in Torr.
+    nu_model 1 (the paper's Townsend form): nu_i = s_nu gamma v_d with
+      gamma = A p exp(-B p / E_eff) (1/m), A in 1/(m Torr), B in V/(m Torr),
+      and the drift velocity v_d = mu_e E_eff, mu_e = e / (m_e nu_m) (the
+      mobility of the model's collision frequency)."""
+    pos = np.real(eeff) > 0
+    es = np.where(pos, eeff, 1.0)
+    if P.nu_model == 1:
+        mu_e = QE / (ME * P.nu_m)
+        nu = P.nu_scale * P.town_A * P.p * np.exp(-P.town_B * P.p / es) * mu_e * es
+        return np.where(pos, nu, 0.0)
+    xs = es / (100.0 * P.p)
     return np.where(pos, P.nu_scale * 5.14e11 * P.p * np.exp(-73.0 * xs ** -0.44), 0.0)
 
 

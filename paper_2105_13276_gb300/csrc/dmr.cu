@@ -81,6 +81,8 @@ struct Derived {
       g_th, T;
   int64_t cap;
   int m_ex, m_ey;   // threshold-line jumps (growth = 2)
+  int nu_model;     // 0 air fit, 1 Townsend form
+  double town_A, town_B;
 };
 
 int derive(const dmr_config* c, Derived* d, std::string* err) {
@@ -94,6 +96,10 @@ int derive(const dmr_config* c, Derived* d, std::string* err) {
   if (c->growth < 0 || c->growth > 2) { *err = "growth must be 0, 1 or 2"; return DMR_EINVAL; }
   d->m_ex = c->m_ex >= 0 ? c->m_ex : 2 * c->buffer_cells;
   d->m_ey = c->m_ey >= 0 ? c->m_ey : c->buffer_cells;
+  if (c->nu_model != 0 && c->nu_model != 1) { *err = "nu_model must be 0 or 1"; return DMR_EINVAL; }
+  d->nu_model = c->nu_model;
+  d->town_A = c->town_A > 0 ? c->town_A : 1500.0;     // 15 /(cm Torr)
+  d->town_B = c->town_B > 0 ? c->town_B : 36500.0;    // 365 V/(cm Torr)
   d->omega = 2.0 * PI * c->freq;
   d->lam = C0 / c->freq;
   d->k = d->omega / C0;
@@ -487,7 +493,10 @@ struct Engine final : Base {
     const double w = d.omega / d.nu_m;
     q.g = 1.0 + w * w;
     q.hp = 100.0 * cfg.p_torr;
-    q.A = d.nu_scale * 5.14e11 * cfg.p_torr;
+    q.A = d.nu_model == 1 ? d.nu_scale * d.town_A * cfg.p_torr : d.nu_scale * 5.14e11 * cfg.p_torr;
+    q.model = d.nu_model;
+    q.tBp = d.town_B * cfg.p_torr;
+    q.mu_e = QE / (ME * d.nu_m);
     q.nu_m = d.nu_m; q.nu_a = d.nu_a; q.De = d.De; q.Da = d.Da;
     q.wp2c = QE * QE / (ME * EPS0);
     q.heat = QE * QE / (ME * d.nu_m);
@@ -1325,7 +1334,7 @@ struct Engine final : Base {
     const int64_t ppseg = rec.K / NT;
     const int nseg = (int)rec.ck.size();
     const dmr::Dens dc = make_dens(1), df = make_dens(r);
-    const double A1 = 5.14e11 * cfg.p_torr;
+    const double A1 = (d.nu_model == 1 ? d.town_A : 5.14e11) * cfg.p_torr;   // d nu_i / d s_nu, per unit
     int st_ = DMR_OK;
     for (int sg = nseg - 1; sg >= 0 && !st_; --sg) {
       // ---- restore the segment's start and recompute it onto the tape

@@ -274,7 +274,16 @@ __global__ void ka_rates_d(const T* n, const double* S2f, Dens d, double A1, int
   const double eeff = sqrt(e2);
   const T x = ehp_of<T>(e2, d);
   T nui = T(0), dn = T(0), per_s = T(0);
-  if (x > T(0)) {
+  if (d.model == 1) {
+    // Townsend form: nu = A p exp(-Bp/E) mu_e E, d nu/d S2 = nu (1 + Bp/E) / (2 S2)
+    const T ee = sqrt((T)e2);
+    if (ee > T(0)) {
+      const T ex = exp(-(T)d.tBp / ee);
+      nui = (T)d.A * ex * (T)d.mu_e * ee;
+      per_s = (T)A1 * ex * (T)d.mu_e * ee;
+      dn = (T)((double)nui * (1.0 + d.tBp / (double)ee) / (2.0 * s2));
+    }
+  } else if (x > T(0)) {
     const T ex = exp(T(-73.0) * pow(x, T(-0.44)));
     nui = (T)d.A * ex;
     per_s = (T)A1 * ex;

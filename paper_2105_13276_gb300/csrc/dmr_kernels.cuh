@@ -552,7 +552,7 @@ struct Dens {
   double N;          // EM samples per period on this mesh
   double g;          // 1 + (w/nu_m)^2
   double hp;         // 100 p: E_eff/p in V/(cm Torr)
-  double A;          // s_nu 5.14e11 p
+  double A;          // s_nu 5.14e11 p (air fit) or s_nu A_T p (Townsend form)
   double nu_m, nu_a, De, Da;
   double wp2c;       // e^2/(m eps0)
   double heat;       // e^2/(m nu_m): period-mean J.E = n heat E_eff^2
@@ -560,6 +560,8 @@ struct Dens {
   double dx2;        // dx^2
   double r_ei;
   double invN, invg, inv_hp;   // 1/N, 1/g, 1/hp
+  int model;                   // 0 air fit, 1 Townsend form
+  double tBp, mu_e;            // Townsend: B p (V/m), mobility e/(m_e nu_m)
 };
 
 // E_eff^2 of a node from its FP64 running E^2 sum of the period:
@@ -572,6 +574,19 @@ __device__ __forceinline__ double eeff2_of(double s2, const Dens& d) { return s2
 // precision
 template <class T>
 __device__ __forceinline__ T ehp_of(double e2, const Dens& d) { return sqrt((T)e2) * (T)d.inv_hp; }
+
+// Ionization frequency nu_i at E_eff^2 = e2 (Sec. II.A), in the run's
+// precision: the air fit of E_eff/p, or the Townsend form
+// s_nu A p exp(-B p / E_eff) mu_e E_eff; 0 where E_eff = 0
+template <class T>
+__device__ __forceinline__ T nu_ion(double e2, const Dens& d) {
+  if (d.model == 1) {
+    const T ee = sqrt((T)e2);
+    return ee > T(0) ? (T)d.A * exp(-(T)d.tBp / ee) * (T)d.mu_e * ee : T(0);
+  }
+  const T x = ehp_of<T>(e2, d);
+  return (x > T(0)) ? (T)d.A * exp(T(-73.0) * pow(x, T(-0.44))) : T(0);
+}
 
 // composite trapezoid weight of node (i, j): coarse mesh outside the
 // rectangle, fine mesh inside it
@@ -635,8 +650,7 @@ __global__ void k_rates(Mesh<T> m, Step<T> c, Dens d, Wts w, T* D, T* nu, double
     const int id = j * m.p + i;
     const double s2 = m.S2[id] + (double)node_e2(m, c, i, j);
     const double e2 = eeff2_of(s2, d);
-    const T x = ehp_of<T>(e2, d);
-    T nui = (x > T(0)) ? (T)d.A * exp(T(-73.0) * pow(x, T(-0.44))) : T(0);
+    const T nui = nu_ion<T>(e2, d);
     T n = m.n[id];
     T wp2 = n * (T)d.wp2c;
     T num = nui * (T)d.nu_m * (T)d.De + wp2 * (T)d.Da;

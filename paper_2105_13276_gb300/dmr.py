@@ -37,7 +37,8 @@ class DmrConfig(ctypes.Structure):
                 ("freq", c_double), ("E0", c_double), ("p_torr", c_double),
                 ("De", c_double), ("Da", c_double), ("beta_rec", c_double), ("Te", c_double),
                 ("nu_scale", c_double), ("nu_a", c_double), ("n_th", c_double),
-                ("g_th", c_double), ("m_ex", c_int32), ("m_ey", c_int32)]
+                ("g_th", c_double), ("m_ex", c_int32), ("m_ey", c_int32),
+                ("nu_model", c_int32), ("town_A", c_double), ("town_B", c_double)]
 
 
 class DMRError(RuntimeError):
@@ -121,6 +122,8 @@ def make_config(cfg: dict) -> DmrConfig:
     c.growth = int(1 if cfg.get("growth") is None else int(cfg["growth"]))
     c.m_ex = int(-1 if cfg.get("m_ex") is None else cfg["m_ex"])
     c.m_ey = int(-1 if cfg.get("m_ey") is None else cfg["m_ey"])
+    c.nu_model = int(cfg.get("nu_model") or 0)
+    c.town_A, c.town_B = d("town_A"), d("town_B")
     c.patch_cap_cells = int(-1 if cfg.get("patch_cap_cells") is None else cfg["patch_cap_cells"])
     c.freq, c.E0, c.p_torr = float(cfg["freq"]), float(cfg["E0"]), float(cfg["p_torr"])
     c.De, c.Da = d("De"), d("Da")

@@ -32,7 +32,8 @@ def base_cfg(**kw):
     cfg = dict(nx=64, ny=64, r=1, n_lambda=32, steps_per_period=64, freq=FREQ,
                E0=5e6, p_torr=700.0, De=None, Da=None, beta_rec=None, Te=None,
                nu_scale=None, nu_a=None, n_th=None, g_th=None, buffer_cells=4,
-               growth=True, m_ex=None, m_ey=None, patch_cap_cells=None, precision=0)
+               growth=True, m_ex=None, m_ey=None, nu_model=None, town_A=None, town_B=None,
+               patch_cap_cells=None, precision=0)
     cfg.update(kw)
     return cfg
 

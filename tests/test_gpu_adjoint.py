@@ -107,6 +107,24 @@ def test_fp64_adjoint_matches_complex_step(r):
     assert abs(dir_g / cseed - 1) < 1e-9, (dir_g, cseed)
 
 
+def test_fp64_adjoint_townsend_matches_complex_step():
+    """The adjoint with the Townsend coefficient set (nu_model = 1)."""
+    w = W.small_dmr(nu_model=1)
+    seed = O.sim_from_workload(w).fine.n.copy()
+    NT = w["cfg"]["steps_per_period"]
+    steps, K = 2 * NT, NT
+    ref = oracle_run(w, w["cfg"]["E0"], 1.0, seed, steps)
+    rng = np.random.default_rng(5)
+    target = ref.coarse.n * (1 + 0.05 * rng.standard_normal(ref.coarse.n.shape))
+    u = rng.standard_normal(seed.shape)
+    n_end, gE0, gnu, gseed = gpu_grads(w, seed, steps, K, target)
+    assert np.linalg.norm(n_end - ref.coarse.n) / np.linalg.norm(ref.coarse.n) < 1e-12
+    cE0, cnu, cseed = cs_grads(w, seed, steps, ref.log, target, u)
+    assert abs(gE0 / cE0 - 1) < 1e-9, (gE0, cE0)
+    assert abs(gnu / cnu - 1) < 1e-9, (gnu, cnu)
+    assert abs(float(np.sum(gseed * u)) / cseed - 1) < 1e-9
+
+
 def test_fp64_adjoint_matches_central_differences():
     w, seed = case(2)
     NT = w["cfg"]["steps_per_period"]

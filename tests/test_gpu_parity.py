@@ -129,6 +129,36 @@ def test_dmr_fp64_threshold_lines_match_oracle(rect, nth, mex, mey):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+def test_townsend_ionization_matches_oracle(precision):
+    """The Townsend coefficient set (nu_model = 1, Sec. II.A) on the GPU
+    against the oracle: free-running growth in FP64 (rectangles and masks
+    bit-exact, fields within 1e-12); FP32 with the oracle's log replayed."""
+    w = W.small_dmr(nu_model=1, town_A=2000.0, town_B=30000.0, precision=precision)
+    sim = O.sim_from_workload(w)
+    NT = w["cfg"]["steps_per_period"]
+    run = D.run_from_workload(w)
+    if precision:
+        ref = O.sim_from_workload(w)
+        ref.advance(3 * NT + 5)
+        run.replay_log(ref.log)
+    for p in range(3):
+        sim.advance(NT)
+        run.advance(NT)
+        assert run.get_patch() == tuple(sim.rect), p
+        if precision == 0:
+            assert np.array_equal(run.read("mask").T.astype(bool), sim.masks[-1]), p
+    sim.advance(5)
+    run.advance(5)
+    compare(run, sim, TOL64 if precision == 0 else TOL32)
+    st = run.stats()
+    assert abs(st["N_e"] / sim.N_e - 1) < (TOL64 if precision == 0 else TOL32)
+    # the coefficient set matters: the fit gives another density
+    sim_fit = O.sim_from_workload(W.small_dmr(precision=precision))
+    sim_fit.advance(3 * NT + 5)
+    assert abs(sim_fit.N_e / sim.N_e - 1) > 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_dmr_many_strips_match_oracle(precision):
     """Meshes several warp strips wide on both levels, with strips inside
     the mesh, at its edges and over the restricted region; growth

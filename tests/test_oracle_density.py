@@ -81,6 +81,32 @@ def test_ionization_magnitudes_match_paper_range():
     assert O.ionization_frequency(P, np.array([0.0]))[0] == 0.0
 
 
+def test_townsend_form_stoletov_point_and_saturation():
+    """Townsend coefficient set (Sec. II.A, gamma = A p exp(-B p/E_eff),
+    v_d = mu_e E_eff): properties of the form, not a retyped formula.
+    - ionization per volt gamma/E = nu_i/(mu_e E^2) peaks at E = B p (the
+      Stoletov point) with value A/(B e);
+    - at high field gamma saturates to A p;
+    - nu_i scales with s_nu and vanishes at E_eff = 0."""
+    cfg = W.base_cfg(nu_model=1, town_A=1500.0, town_B=36500.0, p_torr=300.0)
+    P = O.Params(cfg)
+    mu = O.QE / (O.ME * P.nu_m)
+    E = np.linspace(0.2, 5.0, 200001) * P.town_B * P.p
+    eta = O.ionization_frequency(P, E) / (mu * E * E)
+    k = int(np.argmax(eta))
+    assert abs(E[k] / (P.town_B * P.p) - 1.0) < 1e-4
+    assert abs(eta[k] / (P.town_A / (P.town_B * math.e)) - 1.0) < 1e-9
+    big = 1e6 * P.town_B * P.p
+    assert abs(O.ionization_frequency(P, np.array([big]))[0] / (mu * big) / (P.town_A * P.p) - 1) < 2e-6
+    assert O.ionization_frequency(P, np.array([0.0]))[0] == 0.0
+    P2 = O.Params(dict(cfg, nu_scale=2.5))
+    e = np.array([3e6])
+    assert abs(O.ionization_frequency(P2, e)[0] / O.ionization_frequency(P, e)[0] - 2.5) < 1e-15
+    # the default fit is unchanged by the new switch
+    Pf = O.Params(W.base_cfg(p_torr=300.0))
+    assert Pf.nu_model == 0
+
+
 def test_effective_diffusion_limits():
     """D_eff = (alpha D_e + D_a)/(1 + alpha), alpha = nu_i nu_m / w_p^2:
     free diffusion where there are no electrons, ambipolar in dense plasma,
