@@ -112,6 +112,14 @@ typedef struct dmr_config {
                                 gamma = A p exp(-B p/E_eff), v_d = e E_eff/(m_e nu_m) */
   double town_A, town_B;     /* nu_model = 1: A in 1/(m Torr) [1500], B in V/(m Torr)
                                 [36500] (values <= 0 select the defaults) */
+  int32_t boundary;          /* outer boundary of the coarse mesh: 0 first-order Mur on
+                                the scattered tangential E (Fig. 1 caption); 1 CPML of
+                                pml_cells cells backed by PEC (kappa = 1, cubic sigma
+                                grading, sigma_max = 0.8 * 4 / (eta0 dx_c)).  With CPML
+                                the fine rectangle must stay pml_cells + 2 coarse cells
+                                inside the domain (set_patch: DMR_EINVAL; growth stops
+                                there); adjoint and batched runs need boundary = 0 */
+  int32_t pml_cells;         /* CPML thickness in coarse cells [8] (values <= 0) */
 } dmr_config;
 
 /* Bytes of device workspace a run of this configuration needs; 0 if the

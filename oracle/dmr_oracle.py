@@ -61,7 +61,7 @@ class Params:
     ``cfg`` is a plain dict with keys nx, ny, r, n_lambda, steps_per_period,
     freq, E0, p_torr and optional De, Da, beta_rec, Te, nu_scale, nu_a, n_th,
     g_th, buffer_cells, growth, m_ex, m_ey, nu_model, town_A, town_B,
-    patch_cap_cells.  A value of None (or a
+    boundary, pml_cells, patch_cap_cells.  A value of None (or a
     missing key) selects the default reading.
     """
 
@@ -91,6 +91,12 @@ class Params:
         # ionization coefficient set: 0 the air fit, 1 the Townsend form with
         # A = 15 /(cm Torr), B = 365 V/(cm Torr) by default (reading; SI here)
         self.nu_model = int(g("nu_model") if g("nu_model") is not None else 0)
+        # outer boundary: 0 first-order Mur (Fig. 1 caption), 1 CPML of
+        # pml_cells coarse cells backed by PEC (the benchmark set-up names
+        # "Mur/PML"); the fine rectangle then stays pml_cells + 2 cells inside
+        self.boundary = int(g("boundary") if g("boundary") is not None else 0)
+        self.pml_cells = int(g("pml_cells") if g("pml_cells") is not None else 8)
+        self.rect_margin = self.pml_cells + 2 if self.boundary == 1 else 0
         self.town_A = float(g("town_A") if g("town_A") is not None else 1500.0)
         self.town_B = float(g("town_B") if g("town_B") is not None else 36500.0)
         # Sec. III.A: critical density n_c = m eps0 w^2 / e^2 (the square is
@@ -171,6 +177,35 @@ def incident_ey(P: Params, mesh: Mesh, m):
 # ----------------------------------------------------------------------------
 # EM step: Eqs. 1-3 with Mur / coarse-fine boundaries
 # ----------------------------------------------------------------------------
+class CPML:
+    """Convolutional PML (Roden and Gedney's recursive form, kappa = 1,
+    alpha = 0) on the outer L cells of a mesh, backed by PEC.  sigma grows as
+    sigma_max (d/L)^3 with the depth d into the layer, sigma_max =
+    0.8 (m + 1) / (eta0 dx), m = 3; per step psi <- b psi + c D with
+    b = exp(-sigma dt / eps0), c = b - 1, D the difference the curl uses at
+    the point where psi lives (cell centres for Hz, nodes for Ex, Ey).
+    Outside the layer b = 1, c = 0, so psi stays exactly 0 there."""
+
+    def __init__(self, mesh, L, dtype=np.float64):
+        nx, ny, dx, dt = mesh.nx, mesh.ny, mesh.dx, mesh.dt
+        eta0 = math.sqrt(MU0 / EPS0)
+        smax = 0.8 * 4.0 / (eta0 * dx)
+
+        def coef(pos, n):
+            d = np.maximum(np.maximum(L - pos, pos - (n - L)), 0.0) / L
+            b = np.exp(-smax * d ** 3 * dt / EPS0)
+            return b, b - 1.0
+
+        self.bxh, self.cxh = coef(np.arange(nx) + 0.5, nx)      # Hz cells, x
+        self.byh, self.cyh = coef(np.arange(ny) + 0.5, ny)      # Hz cells, y
+        self.bxn, self.cxn = coef(np.arange(nx + 1.0), nx)      # nodes, x (Ey)
+        self.byn, self.cyn = coef(np.arange(ny + 1.0), ny)      # nodes, y (Ex)
+        z = lambda a, b: np.zeros((a, b), dtype=dtype)
+        self.hx, self.hy = z(nx, ny), z(nx, ny)                 # psi of Hz (x, y)
+        self.exy = z(nx, ny + 1)                                 # psi of Ex (y)
+        self.eyx = z(nx + 1, ny)                                 # psi of Ey (x)
+
+
 def em_step(P: Params, mesh: Mesh, sides=None, bc="mur"):
     """Advance one EM step on ``mesh`` (Eqs. 1-3, Yee leapfrog, Sec. II.B).
 
@@ -182,14 +217,22 @@ def em_step(P: Params, mesh: Mesh, sides=None, bc="mur"):
     ``sides`` maps 'left','right','bottom','top' to either 'mur' (first-order
     Mur on the scattered tangential E, Fig. 1 caption) or an array holding
     the tangential E of that side at level n+1 (coarse-fine boundary values
-    from Eq. 5b).  ``bc='pec'`` zeroes the tangential E instead (used only by
-    the cavity invariants).
+    from Eq. 5b).  ``bc='pec'`` zeroes the tangential E instead (the cavity
+    invariants); ``bc='cpml'`` applies the mesh's CPML layer (``mesh.pml``)
+    and PEC behind it.
     """
     dt, dx = mesh.dt, mesh.dx
     Ex, Ey, Hz, vx, vy, n = mesh.Ex, mesh.Ey, mesh.Hz, mesh.vx, mesh.vy, mesh.n
+    pml = mesh.pml if bc == "cpml" else None
 
     # Eq. 2: dHz/dt = -(1/mu0) (dEy/dx - dEx/dy)
-    Hz -= (dt / MU0) * ((Ey[1:, :] - Ey[:-1, :]) / dx - (Ex[:, 1:] - Ex[:, :-1]) / dx)
+    if pml is None:
+        Hz -= (dt / MU0) * ((Ey[1:, :] - Ey[:-1, :]) / dx - (Ex[:, 1:] - Ex[:, :-1]) / dx)
+    else:
+        dey, dex = Ey[1:, :] - Ey[:-1, :], Ex[:, 1:] - Ex[:, :-1]
+        pml.hx[...] = pml.bxh[:, None] * pml.hx + pml.cxh[:, None] * dey
+        pml.hy[...] = pml.byh[None, :] * pml.hy + pml.cyh[None, :] * dex
+        Hz -= (dt / MU0) * ((dey + pml.hx) / dx - (dex + pml.hy) / dx)
 
     # Eq. 3: dv/dt = -e E/m - nu_m v, E = scattered + incident (total field)
     einc = incident_ey(P, mesh, mesh.m)
@@ -203,8 +246,16 @@ def em_step(P: Params, mesh: Mesh, sides=None, bc="mur"):
 
     Ex_old, Ey_old = Ex.copy(), Ey.copy()
     # Eq. 1 on interior edges: dEx/dt = (dHz/dy - Jx)/eps0, dEy/dt = (-dHz/dx - Jy)/eps0
-    Ex[:, 1:-1] += (dt / EPS0) * ((Hz[:, 1:] - Hz[:, :-1]) / dx - Jx[:, 1:-1])
-    Ey[1:-1, :] += (dt / EPS0) * (-(Hz[1:, :] - Hz[:-1, :]) / dx - Jy[1:-1, :])
+    if pml is None:
+        Ex[:, 1:-1] += (dt / EPS0) * ((Hz[:, 1:] - Hz[:, :-1]) / dx - Jx[:, 1:-1])
+        Ey[1:-1, :] += (dt / EPS0) * (-(Hz[1:, :] - Hz[:-1, :]) / dx - Jy[1:-1, :])
+    else:
+        dhy, dhx = Hz[:, 1:] - Hz[:, :-1], Hz[1:, :] - Hz[:-1, :]
+        pml.exy[:, 1:-1] = pml.byn[None, 1:-1] * pml.exy[:, 1:-1] + pml.cyn[None, 1:-1] * dhy
+        pml.eyx[1:-1, :] = pml.bxn[1:-1, None] * pml.eyx[1:-1, :] + pml.cxn[1:-1, None] * dhx
+        Ex[:, 1:-1] += (dt / EPS0) * ((dhy + pml.exy[:, 1:-1]) / dx - Jx[:, 1:-1])
+        Ey[1:-1, :] += (dt / EPS0) * (-(dhx + pml.eyx[1:-1, :]) / dx - Jy[1:-1, :])
+        bc = "pec"                               # the layer is backed by PEC
 
     if sides is None:
         sides = {s: bc for s in ("left", "right", "bottom", "top")}
@@ -403,14 +454,14 @@ def mask_bbox(mask):
     return (int(ii.min()), int(jj.min()), int(ii.max()), int(jj.max()))
 
 
-def grow_rect(rect, bbox, buffer, nx, ny):
+def grow_rect(rect, bbox, buffer, nx, ny, lo=0):
     """Growth policy: bbox of the flags widened by ``buffer`` coarse cells,
-    united with the current rectangle and clipped to the domain.  The
-    rectangle only grows (Sec. III.D)."""
+    united with the current rectangle and clipped to the domain less a
+    margin ``lo`` (the CPML layer).  The rectangle only grows (Sec. III.D)."""
     if bbox is None:
         return tuple(rect)
-    c = (max(bbox[0] - buffer, 0), max(bbox[1] - buffer, 0),
-         min(bbox[2] + buffer, nx), min(bbox[3] + buffer, ny))
+    c = (max(bbox[0] - buffer, lo), max(bbox[1] - buffer, lo),
+         min(bbox[2] + buffer, nx - lo), min(bbox[3] + buffer, ny - lo))
     return (min(rect[0], c[0]), min(rect[1], c[1]), max(rect[2], c[2]), max(rect[3], c[3]))
 
 
@@ -428,17 +479,17 @@ def line_hits(n, rect, n_th):
             bool(np.any(a[i1, j0:j1 + 1] > n_th)), bool(np.any(a[i0:i1 + 1, j1] > n_th)))
 
 
-def grow_lines(rect, hits, m_ex, m_ey, nx, ny):
+def grow_lines(rect, hits, m_ex, m_ey, nx, ny, lo=0):
     """Expansion of Sec. III.D by threshold lines: a hit on the backward or
     forward line (left, right side) moves that side outwards by m_ex coarse
     cells along x, a hit on the lower or upper line (bottom, top) by m_ey
     along y (the paper takes m_ex > m_ey); clipped to the domain, so the
     rectangle only grows."""
     left, bottom, right, top = hits
-    return (max(rect[0] - m_ex, 0) if left else rect[0],
-            max(rect[1] - m_ey, 0) if bottom else rect[1],
-            min(rect[2] + m_ex, nx) if right else rect[2],
-            min(rect[3] + m_ey, ny) if top else rect[3])
+    return (max(rect[0] - m_ex, lo) if left else rect[0],
+            max(rect[1] - m_ey, lo) if bottom else rect[1],
+            min(rect[2] + m_ex, nx - lo) if right else rect[2],
+            min(rect[3] + m_ey, ny - lo) if top else rect[3])
 
 
 # ----------------------------------------------------------------------------
@@ -468,6 +519,8 @@ class Sim:
         self.P = P
         self.dtype = dtype
         self.coarse = Mesh(P, P.nx, P.ny, 1, dtype=dtype)
+        self.coarse.pml = CPML(self.coarse, P.pml_cells, dtype) if P.boundary == 1 else None
+        self.cbc = "cpml" if P.boundary == 1 else "mur"
         self.fine = None
         self.rect = None
         self.period = 0
@@ -487,8 +540,9 @@ class Sim:
     def _make_fine(self, rect):
         P = self.P
         i0, j0, i1, j1 = rect
-        if not (0 <= i0 < i1 <= P.nx and 0 <= j0 < j1 <= P.ny):
-            raise ValueError("bad rectangle %r" % (rect,))
+        k = P.rect_margin
+        if not (k <= i0 < i1 <= P.nx - k and k <= j0 < j1 <= P.ny - k):
+            raise ValueError("bad rectangle %r (margin %d)" % (rect, k))
         if P.r * P.r * (i1 - i0) * (j1 - j0) > P.cap:
             raise CapacityError("patch %r exceeds the capacity" % (rect,))
         self.rect = rect
@@ -540,7 +594,7 @@ class Sim:
         P = self.P
         c = self.coarse
         if self.fine is None:
-            em_step(P, c)
+            em_step(P, c, bc=self.cbc)
             accumulate_e2(P, c)
         else:
             f = self.fine
@@ -548,7 +602,7 @@ class Sim:
             i0, j0, i1, j1 = self.rect
             old = {"bottom": c.Ex[:, j0].copy(), "top": c.Ex[:, j1].copy(),
                    "left": c.Ey[i0, :].copy(), "right": c.Ey[i1, :].copy()}
-            em_step(P, c)
+            em_step(P, c, bc=self.cbc)
             new = {"bottom": c.Ex[:, j0], "top": c.Ex[:, j1],
                    "left": c.Ey[i0, :], "right": c.Ey[i1, :]}
             on_edge = self._sides()
@@ -669,9 +723,10 @@ class Sim:
                 new_rect = tuple(self.replay[self.period - 1])
             elif P.growth == 2:
                 new_rect = grow_lines(self.rect, line_hits(c.n, self.rect, P.n_th),
-                                      P.m_ex, P.m_ey, P.nx, P.ny)
+                                      P.m_ex, P.m_ey, P.nx, P.ny, P.rect_margin)
             elif P.growth:
-                new_rect = grow_rect(self.rect, mask_bbox(mask), P.buffer, P.nx, P.ny)
+                new_rect = grow_rect(self.rect, mask_bbox(mask), P.buffer, P.nx, P.ny,
+                                     P.rect_margin)
             else:
                 new_rect = self.rect
             if new_rect != self.rect:

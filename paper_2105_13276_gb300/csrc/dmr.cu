@@ -83,6 +83,9 @@ struct Derived {
   int m_ex, m_ey;   // threshold-line jumps (growth = 2)
   int nu_model;     // 0 air fit, 1 Townsend form
   double town_A, town_B;
+  int boundary;     // 0 Mur, 1 CPML
+  int pml;          // CPML thickness (coarse cells)
+  int margin;       // the fine rectangle stays this many coarse cells inside
 };
 
 int derive(const dmr_config* c, Derived* d, std::string* err) {
@@ -100,6 +103,14 @@ int derive(const dmr_config* c, Derived* d, std::string* err) {
   d->nu_model = c->nu_model;
   d->town_A = c->town_A > 0 ? c->town_A : 1500.0;     // 15 /(cm Torr)
   d->town_B = c->town_B > 0 ? c->town_B : 36500.0;    // 365 V/(cm Torr)
+  if (c->boundary != 0 && c->boundary != 1) { *err = "boundary must be 0 (Mur) or 1 (CPML)"; return DMR_EINVAL; }
+  d->boundary = c->boundary;
+  d->pml = c->pml_cells > 0 ? c->pml_cells : 8;
+  d->margin = c->boundary == 1 ? d->pml + 2 : 0;
+  if (c->boundary == 1 && (2 * d->pml + 2 > c->nx || 2 * d->pml + 2 > c->ny)) {
+    *err = "the CPML layers leave no interior";
+    return DMR_EINVAL;
+  }
   d->omega = 2.0 * PI * c->freq;
   d->lam = C0 / c->freq;
   d->k = d->omega / C0;
@@ -149,6 +160,8 @@ struct Layout {
   size_t off_tab[4] = {};                 // ckx_c skx_c ckx_f skx_f
   size_t off_ph[4] = {};                  // sin/cos of the phase per step: coarse, fine
   size_t off_mask = 0, off_part[4] = {}, off_ctl = 0, off_view = 0;
+  size_t off_psi[8] = {};                 // CPML psi, parity 0 then 1: Hz (x, y), Ex (y), Ey (x)
+  size_t off_pmlc[8] = {};                // CPML b, c: x cells, y cells, x nodes, y nodes
   size_t total = 0;
 };
 
@@ -197,6 +210,12 @@ int make_layout(const dmr_config* c, const Derived& d, Layout* L, std::string* e
   L->off_part[3] = take((size_t)std::max(L->nblk_f, 1) * 8);
   L->off_ctl = take(sizeof(dmr::Ctl));
   L->off_view = take(std::max(L->cplane, L->fplane) * 8);
+  if (d.boundary == 1) {
+    for (int q = 0; q < 8; ++q) L->off_psi[q] = take(L->cplane * L->es);
+    const size_t len[8] = {(size_t)nx, (size_t)nx, (size_t)ny, (size_t)ny,
+                           (size_t)nx + 1, (size_t)nx + 1, (size_t)ny + 1, (size_t)ny + 1};
+    for (int q = 0; q < 8; ++q) L->off_pmlc[q] = take(len[q] * L->es);
+  }
   L->total = o;
   return DMR_OK;
 }
@@ -347,6 +366,8 @@ struct Engine final : Base {
   T *ckx_c = nullptr, *skx_c = nullptr, *ckx_f = nullptr, *skx_f = nullptr;
   T* ph[4] = {};             // sin, cos of w t per step of a period: coarse, fine
   uint8_t* mask = nullptr;
+  T* psi[2][4] = {};         // CPML psi by parity: Hz (x, y), Ex (y), Ey (x)
+  T* pmlc[8] = {};           // CPML b, c: x cells, y cells, x nodes, y nodes
   double* part[4] = {};
   dmr::Ctl* ctl = nullptr;
   double* view = nullptr;
@@ -374,6 +395,10 @@ struct Engine final : Base {
     ckx_f = at<T>(L.off_tab[2]); skx_f = at<T>(L.off_tab[3]);
     for (int q = 0; q < 4; ++q) ph[q] = at<T>(L.off_ph[q]);
     mask = at<uint8_t>(L.off_mask);
+    if (d.boundary == 1) {
+      for (int q = 0; q < 4; ++q) { psi[0][q] = at<T>(L.off_psi[q]); psi[1][q] = at<T>(L.off_psi[4 + q]); }
+      for (int q = 0; q < 8; ++q) pmlc[q] = at<T>(L.off_pmlc[q]);
+    }
     for (int q = 0; q < 4; ++q) part[q] = at<double>(L.off_part[q]);
     ctl = at<dmr::Ctl>(L.off_ctl);
     view = at<double>(L.off_view);
@@ -416,6 +441,32 @@ struct Engine final : Base {
       T* dcs = ph[rr == 1 ? 1 : 3];
       if ((s = ck(cudaMemcpyAsync(dsn, ps.data(), N * sizeof(T), cudaMemcpyHostToDevice, st), "upload phases"))) return s;
       if ((s = ck(cudaMemcpyAsync(dcs, pcv.data(), N * sizeof(T), cudaMemcpyHostToDevice, st), "upload phases"))) return s;
+    }
+    if (d.boundary == 1) {
+      // CPML coefficients (the oracle's formula): sigma = smax (depth/L)^3,
+      // b = exp(-sigma dt / eps0), c = b - 1
+      const double smax = 0.8 * 4.0 / (std::sqrt(MU0 / EPS0) * d.dxc);
+      const int Lc = d.pml;
+      // n entries at positions q + shift (cell centres 0.5, nodes 0) of a
+      // mesh extent cells long
+      auto coef = [&](int n, double shift, int extent, T* bd, T* cd) -> int {
+        std::vector<T> bv(n), cv(n);
+        for (int q = 0; q < n; ++q) {
+          const double pos = q + shift;
+          const double dep = std::max(std::max(Lc - pos, pos - (extent - Lc)), 0.0) / Lc;
+          const double bb = std::exp(-smax * dep * dep * dep * d.dtc / EPS0);
+          bv[q] = (T)bb;
+          cv[q] = (T)(bb - 1.0);
+        }
+        int e = ck(cudaMemcpyAsync(bd, bv.data(), n * sizeof(T), cudaMemcpyHostToDevice, st), "upload CPML");
+        if (!e) e = ck(cudaMemcpyAsync(cd, cv.data(), n * sizeof(T), cudaMemcpyHostToDevice, st), "upload CPML");
+        if (!e) e = ck(cudaStreamSynchronize(st), "CPML sync");
+        return e;
+      };
+      if ((s = coef(cfg.nx, 0.5, cfg.nx, pmlc[0], pmlc[1]))) return s;
+      if ((s = coef(cfg.ny, 0.5, cfg.ny, pmlc[2], pmlc[3]))) return s;
+      if ((s = coef(cfg.nx + 1, 0.0, cfg.nx, pmlc[4], pmlc[5]))) return s;
+      if ((s = coef(cfg.ny + 1, 0.0, cfg.ny, pmlc[6], pmlc[7]))) return s;
     }
     return ck(cudaStreamSynchronize(st), "init sync");
   }
@@ -530,12 +581,23 @@ struct Engine final : Base {
     return pts * (11.0 * (double)L.es + (accum ? 16.0 : 0.0));
   }
 
+  // coarse EM launches compile the CPML terms in only for CPML runs
+  void go_em(int nb, const dmr::EmArgs<T>& A) const {
+    if (A.pml.on) dmr::k_em<T, true><<<nb, 32 * dmr::EM_WARPS, 0, st>>>(A);
+    else dmr::k_em<T, false><<<nb, 32 * dmr::EM_WARPS, 0, st>>>(A);
+  }
+  void go_em2(int nb, const dmr::EmArgs<T>& A0, const dmr::EmArgs<T>& A1) const {
+    if (A0.pml.on) dmr::k_em2<T, true><<<nb, 32 * dmr::EM_WARPS, 0, st>>>(A0, A1);
+    else dmr::k_em2<T, false><<<nb, 32 * dmr::EM_WARPS, 0, st>>>(A0, A1);
+  }
+
   dmr::EmArgs<T> em_args(const dmr::Mesh<T>& src, T* const* dst, const dmr::Step<T>& c,
                          const dmr::Bnd<T>& b, const dmr::Restr<T>& R) const {
     dmr::EmArgs<T> A;
     A.m = src;
     A.dEx = dst[0]; A.dEy = dst[1]; A.dHz = dst[2]; A.dvx = dst[3]; A.dvy = dst[4];
     A.c = c; A.b = b; A.R = R;
+    A.pml = dmr::Pml<T>{};
     A.rows = em_rows(src.nx, src.ny);
     A.gx = (src.nx + 1 + dmr::STRIP_W - 1) / dmr::STRIP_W;
     const int sy = (src.ny + 1 + A.rows - 1) / A.rows;
@@ -570,10 +632,19 @@ struct Engine final : Base {
     }
     if (Ac) {
       dmr::Bnd<T> bc{};
-      for (int q = 0; q < 4; ++q) bc.mode[q] = dmr::BC_MUR;
+      for (int q = 0; q < 4; ++q) bc.mode[q] = d.boundary == 1 ? dmr::BC_PEC : dmr::BC_MUR;
       bc.r = 1;
       *Ac = em_args(src, cdst, sc, bc, R);
       Ac->kind = 0; Ac->N = NT; Ac->r = 1; Ac->ps = ph[0]; Ac->pc = ph[1];
+      if (d.boundary == 1) {
+        dmr::Pml<T>& P = Ac->pml;
+        P.on = 1;
+        P.L = d.pml;
+        P.hx = psi[cp][0]; P.hy = psi[cp][1]; P.exy = psi[cp][2]; P.eyx = psi[cp][3];
+        P.dhx = psi[cp ^ 1][0]; P.dhy = psi[cp ^ 1][1]; P.dexy = psi[cp ^ 1][2]; P.deyx = psi[cp ^ 1][3];
+        P.bxh = pmlc[0]; P.cxh = pmlc[1]; P.byh = pmlc[2]; P.cyh = pmlc[3];
+        P.bxn = pmlc[4]; P.cxn = pmlc[5]; P.byn = pmlc[6]; P.cyn = pmlc[7];
+      }
     }
     if (!Af || !has_fine) return;
     dmr::Bnd<T> bf{};
@@ -634,7 +705,7 @@ struct Engine final : Base {
     const double cbytes = em_bytes((double)(C.nx + 1) * (C.ny + 1), acc_c);
     if (!has_fine) {
       int h = tbeg(0, cbytes);
-      dmr::k_em<T><<<Ac.nblk + Ac.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Ac);
+      go_em(Ac.nblk + Ac.ncfb, Ac);
       tend(h);
       counted(1);
       flip_coarse();
@@ -648,12 +719,12 @@ struct Engine final : Base {
       if (k > 1) em_args_for(k, mlev, cp0, fpar, rvalid, nullptr, &Af);
       if (k == 1) {
         int h = tbeg(0, cbytes + em_bytes(fn, acc_f));
-        dmr::k_em2<T><<<Ac.nblk + Ac.ncfb + Af.nblk + Af.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Ac, Af);
+        go_em2(Ac.nblk + Ac.ncfb + Af.nblk + Af.ncfb, Ac, Af);
         tend(h);
         flip_coarse();
       } else {
         int h = tbeg(1, em_bytes(fn, acc_f));
-        dmr::k_em<T><<<Af.nblk + Af.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Af);
+        go_em(Af.nblk + Af.ncfb, Af);
         tend(h);
       }
       counted(1);
@@ -776,14 +847,16 @@ struct Engine final : Base {
       }
     } else if (cfg.growth == 2) {
       // threshold lines (Sec. III.D): a hit side jumps out by m_ex / m_ey
-      if (hc.side & 1) nr[0] = std::max(rect[0] - d.m_ex, 0);
-      if (hc.side & 2) nr[1] = std::max(rect[1] - d.m_ey, 0);
-      if (hc.side & 4) nr[2] = std::min(rect[2] + d.m_ex, cfg.nx);
-      if (hc.side & 8) nr[3] = std::min(rect[3] + d.m_ey, cfg.ny);
+      const int k = d.margin;   // CPML: the rectangle stays out of the layer
+      if (hc.side & 1) nr[0] = std::max(rect[0] - d.m_ex, k);
+      if (hc.side & 2) nr[1] = std::max(rect[1] - d.m_ey, k);
+      if (hc.side & 4) nr[2] = std::min(rect[2] + d.m_ex, cfg.nx - k);
+      if (hc.side & 8) nr[3] = std::min(rect[3] + d.m_ey, cfg.ny - k);
     } else if (cfg.growth == 1 && hc.nflag > 0) {
       const int b = cfg.buffer_cells;
-      const int c4[4] = {std::max(hc.bbox[0] - b, 0), std::max(hc.bbox[1] - b, 0),
-                         std::min(hc.bbox[2] + b, cfg.nx), std::min(hc.bbox[3] + b, cfg.ny)};
+      const int k = d.margin;
+      const int c4[4] = {std::max(hc.bbox[0] - b, k), std::max(hc.bbox[1] - b, k),
+                         std::min(hc.bbox[2] + b, cfg.nx - k), std::min(hc.bbox[3] + b, cfg.ny - k)};
       nr[0] = std::min(rect[0], c4[0]);
       nr[1] = std::min(rect[1], c4[1]);
       nr[2] = std::max(rect[2], c4[2]);
@@ -794,9 +867,11 @@ struct Engine final : Base {
   }
 
   int check_rect(const int* nr) {
-    if (!(0 <= nr[0] && nr[0] < nr[2] && nr[2] <= cfg.nx && 0 <= nr[1] && nr[1] < nr[3] &&
-          nr[3] <= cfg.ny))
-      return fail(DMR_EINVAL, fmt("bad rectangle (%d,%d,%d,%d)", nr[0], nr[1], nr[2], nr[3]));
+    const int k = d.margin;
+    if (!(k <= nr[0] && nr[0] < nr[2] && nr[2] <= cfg.nx - k && k <= nr[1] && nr[1] < nr[3] &&
+          nr[3] <= cfg.ny - k))
+      return fail(DMR_EINVAL, fmt("bad rectangle (%d,%d,%d,%d)%s", nr[0], nr[1], nr[2], nr[3],
+                                  k ? " (it must stay out of the CPML layer)" : ""));
     if (has_fine && !(nr[0] <= rect[0] && nr[1] <= rect[1] && nr[2] >= rect[2] && nr[3] >= rect[3]))
       return fail(DMR_EINVAL, "the rectangle can only grow");
     const int64_t cells = (int64_t)cfg.r * (nr[2] - nr[0]) * (int64_t)cfg.r * (nr[3] - nr[1]);
@@ -1053,6 +1128,7 @@ struct Engine final : Base {
 
   int adj_record(int64_t n, int64_t K, void* ckpt, size_t bytes) override {
     const int NT = cfg.steps_per_period;
+    if (d.boundary != 0) return fail(DMR_EINVAL, "the adjoint needs the Mur boundary (boundary = 0)");
     if (n <= 0 || K <= 0 || n % NT || K % NT)
       return fail(DMR_EINVAL, "steps and checkpoint interval must be positive multiples of steps_per_period");
     if (m % NT) return fail(DMR_ESTATE, "recording starts at a period boundary");
@@ -1184,7 +1260,7 @@ struct Engine final : Base {
     const int cp0 = cpar;
     dmr::EmArgs<T> Ac, Af;
     em_args_for(1, m, cpar, fpar, rvalid, &Ac, nullptr);
-    dmr::k_em<T><<<Ac.nblk + Ac.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Ac);
+    go_em(Ac.nblk + Ac.ncfb, Ac);
     counted(1);
     flip_coarse();
     R->cvx = tape_copy(C.vx, cplane_b());
@@ -1195,7 +1271,7 @@ struct Engine final : Base {
         R->fEx.push_back(tape_copy(F[cur].Ex, fb));
         R->fEy.push_back(tape_copy(F[cur].Ey, fb));
         em_args_for(k, m, cp0, fpar, rvalid, nullptr, &Af);
-        dmr::k_em<T><<<Af.nblk + Af.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Af);
+        go_em(Af.nblk + Af.ncfb, Af);
         counted(1);
         flip_fine();
         R->fvx.push_back(tape_copy(F[cur].vx, fb));
@@ -1563,9 +1639,9 @@ struct Engine final : Base {
       em_args_for(1, m, cpar, fpar, has_fine, &Ac, has_fine ? &Af : nullptr);
       auto launch = [&]() {
         if (has_fine)
-          dmr::k_em2<T><<<Ac.nblk + Ac.ncfb + Af.nblk + Af.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Ac, Af);
+          go_em2(Ac.nblk + Ac.ncfb + Af.nblk + Af.ncfb, Ac, Af);
         else
-          dmr::k_em<T><<<Ac.nblk + Ac.ncfb, 32 * dmr::EM_WARPS, 0, st>>>(Ac);
+          go_em(Ac.nblk + Ac.ncfb, Ac);
       };
       float ms = 0.f;
       if (int s_ = ck(graph_time(st, launch, kTrialLaunches, &ms), "autotune trial")) return s_;
@@ -1955,6 +2031,7 @@ int batch_check(const dmr_config* cfgs, int n, std::vector<Derived>* ds, std::ve
       *err = "runs of a batch share precision, r and steps_per_period";
       return DMR_EINVAL;
     }
+    if ((*ds)[q].boundary != 0) { *err = fmt("run %d: batched runs need the Mur boundary", q); return DMR_EINVAL; }
     tot += up((*ls)[q].total, 256);
   }
   if (cfgs[0].steps_per_period % 2 != 0 || (cfgs[0].r > 1 && cfgs[0].r % 2 != 0)) {

@@ -16,7 +16,7 @@
 namespace dmr {
 
 enum { SIDE_LEFT = 0, SIDE_RIGHT = 1, SIDE_BOTTOM = 2, SIDE_TOP = 3 };
-enum { BC_MUR = 0, BC_CFB = 1 };
+enum { BC_MUR = 0, BC_CFB = 1, BC_PEC = 2 };
 
 template <class T>
 struct Mesh {
@@ -59,7 +59,7 @@ struct Restr {
 // being read, so a fine sub-step need not wait for the coarse step.
 template <class T>
 struct Bnd {
-  int mode[4];              // BC_MUR or BC_CFB per side
+  int mode[4];              // BC_MUR, BC_CFB or BC_PEC (behind a CPML layer) per side
   const T* old_line[4];     // coarse tangential E at level n (strided)
   const T* new_line[4];     // coarse tangential E at level n+1 (strided)
   int stride[4];
@@ -232,6 +232,19 @@ __device__ __forceinline__ T cfb_blend(const Bnd<T>& b, T lo, T xp, T n0, T n1) 
 constexpr int STRIP_W = 30;
 constexpr int EM_WARPS = 4;   // warps per block (consecutive strips in y)
 
+// CPML layer of the coarse mesh (Roden-Gedney recursion, kappa = 1): psi of
+// the Hz curl terms along x and y at the cells, of the Ex (y) and Ey (x)
+// curl terms at the edges, double-buffered like the fields (read level n,
+// write level n+1); b, c per cell / node column and row (b = 1, c = 0
+// outside the layer, where psi stays 0).
+template <class T>
+struct Pml {
+  int on, L;
+  const T *hx, *hy, *exy, *eyx;   // level n
+  T *dhx, *dhy, *dexy, *deyx;      // level n+1
+  const T *bxh, *cxh, *byh, *cyh, *bxn, *cxn, *byn, *cyn;
+};
+
 // Everything one EM step of one mesh needs; `gx` strips across x, `nblk`
 // blocks (each EM_WARPS strips stacked in y).
 template <class T>
@@ -241,6 +254,7 @@ struct EmArgs {
   Step<T> c;
   Bnd<T> b;
   Restr<T> R;
+  Pml<T> pml;
   int rows, gx, nblk;   // strips: rows per warp, strips across x, blocks
   int ncfb;             // blocks that write the coarse-fine boundary E (Eq. 5b)
   // batched launches: the level-dependent fields (phase, E^2 sample, Eq. 5b
@@ -315,19 +329,20 @@ __device__ __forceinline__ void em_cfb(const EmArgs<T>& A, int blk) {
   else A.dEy[q * p + nfx] = v;
 }
 
-template <class T>
+template <class T, bool PML>
 __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk);
 
 // Blocks of one mesh's EM step: the coarse-fine side blocks first (the
 // longest dependent chain of the launch, so they are dispatched first), then
 // the strips.
-template <class T>
+// PML: compile the CPML terms in (coarse launches of CPML runs only)
+template <class T, bool PML = false>
 __device__ __forceinline__ void em_segment(const EmArgs<T>& A, int blk) {
   if (blk < A.ncfb) em_cfb(A, blk);
-  else em_strips(A, blk - A.ncfb);
+  else em_strips<T, PML>(A, blk - A.ncfb);
 }
 
-template <class T>
+template <class T, bool PML>
 __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
   const Mesh<T>& m = A.m;
   T* __restrict__ dEx = A.dEx;
@@ -348,6 +363,11 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
   if (j0 > ny) return;                       // whole warp leaves together
   const int j1 = min(j0 + rows, ny + 1);     // node rows [j0, j1)
   const bool own = lane >= 1 && lane <= STRIP_W && i <= nx;
+  // CPML (warp-uniform): the strip's columns or rows reach into the layer
+  const Pml<T>& P = A.pml;
+  const int c0 = bx * STRIP_W;
+  const bool pw = PML && P.on && (c0 - 1 <= P.L || c0 + STRIP_W >= nx - P.L || j0 - 1 <= P.L ||
+                           j0 + rows >= ny - P.L);
   const bool xcol = i >= 0 && i < nx;        // column has Ex / Hz
   const bool ycol = i >= 0 && i <= nx;       // column has Ey / n
   const T inc = ycol ? incident(c, i) : T(0);
@@ -363,7 +383,18 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
     const T eym = ycol ? load_ey(m, R, i, jm) : T(0);
     const T hzo = xcol ? m.Hz[jm * p + i] : T(0);
     const T eyr = __shfl_down_sync(0xffffffffu, eym, 1);
-    if (xcol) hzp = hzo - c.ch * ((eyr - eym) - (exc - exm));
+    if (xcol) {
+      if (pw) {
+        // the CPML-corrected H of row j0-1 (its owner stores psi)
+        const int q = jm * p + i;
+        const T dey = eyr - eym, dex = exc - exm;
+        const T px = P.bxh[i] * P.hx[q] + P.cxh[i] * dey;
+        const T py = P.byh[jm] * P.hy[q] + P.cyh[jm] * dex;
+        hzp = hzo - c.ch * ((dey + px) - (dex + py));
+      } else {
+        hzp = hzo - c.ch * ((eyr - eym) - (exc - exm));
+      }
+    }
     exp_ = exm;
     eyp = eym;
   }
@@ -392,7 +423,20 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
     // ---- H (Eq. 2)
     const T eyr = __shfl_down_sync(0xffffffffu, eyc, 1);
     T hz = T(0);
-    if (xcol && j < ny) hz = hzo - c.ch * ((eyr - eyc) - (exn - exc));
+    if (xcol && j < ny) {
+      if (pw) {
+        const T dey = eyr - eyc, dex = exn - exc;
+        const T px = P.bxh[i] * P.hx[id] + P.cxh[i] * dey;
+        const T py = P.byh[j] * P.hy[id] + P.cyh[j] * dex;
+        if (own) {
+          P.dhx[id] = px;
+          P.dhy[id] = py;
+        }
+        hz = hzo - c.ch * ((dey + px) - (dex + py));
+      } else {
+        hz = hzo - c.ch * ((eyr - eyc) - (exn - exc));
+      }
+    }
     const T hzl = __shfl_up_sync(0xffffffffu, hz, 1);
     const T exl = __shfl_up_sync(0xffffffffu, exc, 1);
     const T ncr = __shfl_down_sync(0xffffffffu, nc, 1);
@@ -418,7 +462,15 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
         if (j > 0 && j < ny) {
           const T v = c.va * vxo - c.vb * exc;
           dvx[id] = v;
-          const T en = exc + c.ce * (hz - hzp) + c.cj * (nc + ncr) * v;
+          T en;
+          if (pw) {
+            const T dh = hz - hzp;
+            const T pe = P.byn[j] * P.exy[id] + P.cyn[j] * dh;
+            P.dexy[id] = pe;
+            en = exc + c.ce * (dh + pe) + c.cj * (nc + ncr) * v;
+          } else {
+            en = exc + c.ce * (hz - hzp) + c.cj * (nc + ncr) * v;
+          }
           dEx[id] = en;
           if (j == 1 && b.mode[SIDE_BOTTOM] == BC_MUR) {
             dvx[i] = c.va * m.vx[i] - c.vb * exp_;
@@ -432,6 +484,10 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
         } else {
           const int sd = (j == 0) ? SIDE_BOTTOM : SIDE_TOP;
           if (b.mode[sd] == BC_CFB) dvx[id] = c.va * vxo - c.vb * exc;  // E: em_cfb
+          if (b.mode[sd] == BC_PEC) {
+            dvx[id] = c.va * vxo - c.vb * exc;
+            dEx[id] = T(0);
+          }
         }
       }
       // ---- y edge (i, j)
@@ -439,7 +495,15 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
         if (i > 0 && i < nx) {
           const T v = c.va * vyo - c.vb * (eyc + inc);
           dvy[id] = v;
-          const T en = eyc - c.ce * (hz - hzl) + c.cj * (nc + nn) * v;
+          T en;
+          if (pw) {
+            const T dh = hz - hzl;
+            const T pe = P.bxn[i] * P.eyx[id] + P.cxn[i] * dh;
+            P.deyx[id] = pe;
+            en = eyc - c.ce * (dh + pe) + c.cj * (nc + nn) * v;
+          } else {
+            en = eyc - c.ce * (hz - hzl) + c.cj * (nc + nn) * v;
+          }
           dEy[id] = en;
           if (i == 1 && b.mode[SIDE_LEFT] == BC_MUR) {
             const int ib = j * p;
@@ -454,6 +518,10 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
         } else {
           const int sd = (i == 0) ? SIDE_LEFT : SIDE_RIGHT;
           if (b.mode[sd] == BC_CFB) dvy[id] = c.va * vyo - c.vb * (eyc + inc);  // E: em_cfb
+          if (b.mode[sd] == BC_PEC) {
+            dvy[id] = c.va * vyo - c.vb * (eyc + inc);
+            dEy[id] = T(0);
+          }
         }
       }
     }
@@ -465,9 +533,9 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
   }
 }
 
-template <class T>
+template <class T, bool PML = false>
 __global__ void __launch_bounds__(32 * EM_WARPS) k_em(EmArgs<T> A) {
-  em_segment(A, blockIdx.x);
+  em_segment<T, PML>(A, blockIdx.x);
 }
 
 constexpr int kSegStage = 256;   // segment offsets staged in shared memory up to this many
@@ -514,11 +582,11 @@ __global__ void __launch_bounds__(32 * EM_WARPS) k_em_batch(const EmArgs<T>* __r
 // fine sub-step A1, whose coarse boundary values are recomputed.  The fine
 // blocks come first in the grid (their side blocks carry the launch's
 // longest dependent chain).
-template <class T>
+template <class T, bool PML = false>
 __global__ void __launch_bounds__(32 * EM_WARPS) k_em2(EmArgs<T> A0, EmArgs<T> A1) {
   const int n1 = A1.nblk + A1.ncfb;   // the fine sub-step's blocks first
   if ((int)blockIdx.x < n1) em_segment(A1, blockIdx.x);
-  else em_segment(A0, blockIdx.x - n1);
+  else em_segment<T, PML>(A0, blockIdx.x - n1);
 }
 
 // a8: coarse E edges of the closed rectangle (except tangential edges of

@@ -38,7 +38,8 @@ class DmrConfig(ctypes.Structure):
                 ("De", c_double), ("Da", c_double), ("beta_rec", c_double), ("Te", c_double),
                 ("nu_scale", c_double), ("nu_a", c_double), ("n_th", c_double),
                 ("g_th", c_double), ("m_ex", c_int32), ("m_ey", c_int32),
-                ("nu_model", c_int32), ("town_A", c_double), ("town_B", c_double)]
+                ("nu_model", c_int32), ("town_A", c_double), ("town_B", c_double),
+                ("boundary", c_int32), ("pml_cells", c_int32)]
 
 
 class DMRError(RuntimeError):
@@ -124,6 +125,8 @@ def make_config(cfg: dict) -> DmrConfig:
     c.m_ey = int(-1 if cfg.get("m_ey") is None else cfg["m_ey"])
     c.nu_model = int(cfg.get("nu_model") or 0)
     c.town_A, c.town_B = d("town_A"), d("town_B")
+    c.boundary = int(cfg.get("boundary") or 0)
+    c.pml_cells = int(cfg.get("pml_cells") or -1)
     c.patch_cap_cells = int(-1 if cfg.get("patch_cap_cells") is None else cfg["patch_cap_cells"])
     c.freq, c.E0, c.p_torr = float(cfg["freq"]), float(cfg["E0"]), float(cfg["p_torr"])
     c.De, c.Da = d("De"), d("Da")

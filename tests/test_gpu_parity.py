@@ -158,6 +158,52 @@ def test_townsend_ionization_matches_oracle(precision):
     assert abs(sim_fit.N_e / sim.N_e - 1) > 1e-6
 
 
+@pytest.mark.parametrize("r,precision", [(1, 0), (2, 0), (2, 1)])
+def test_cpml_boundary_matches_oracle(r, precision):
+    """CPML outer boundary (boundary = 1): uniform and DMR runs against the
+    oracle.  FP64 free-running (rectangle logs equal, growth held pml_cells
+    + 2 cells inside), FP32 with the oracle's log replayed."""
+    if r == 1:
+        w = W.small_dmr(nx=70, ny=50, r=1, rect=None, boundary=1, pml_cells=6, precision=precision)
+    else:
+        w = W.small_dmr(boundary=1, pml_cells=4, precision=precision)
+    sim = O.sim_from_workload(w)
+    NT = w["cfg"]["steps_per_period"]
+    run = D.run_from_workload(w)
+    steps = 4 * NT + 7
+    if precision:
+        ref = O.sim_from_workload(w)
+        ref.advance(steps)
+        run.replay_log(ref.log)
+    sim.advance(steps)
+    run.advance(steps)
+    if r > 1:
+        assert run.get_patch() == tuple(sim.rect)
+        k = 4 + 2
+        i0, j0, i1, j1 = sim.rect
+        assert k <= i0 and k <= j0 and i1 <= 40 - k and j1 <= 32 - k
+    compare(run, sim, TOL64 if precision == 0 else TOL32)
+    # the layer is active: the scattered field differs from a Mur run's
+    mur = O.sim_from_workload(dict(w, cfg=dict(w["cfg"], boundary=0)))
+    mur.advance(steps)
+    assert np.abs(mur.coarse.Ey - sim.coarse.Ey).max() > 1e-6 * np.abs(sim.coarse.Ey).max()
+
+
+def test_cpml_rejections():
+    w = W.small_dmr(boundary=1, pml_cells=4)
+    run = D.Run(w["cfg"])
+    with pytest.raises(D.DMRError) as e:
+        run.set_patch((3, 10, 24, 20))          # inside the layer's margin
+    assert e.value.code == D.EINVAL
+    run.set_patch(w["rect"])
+    NT = w["cfg"]["steps_per_period"]
+    with pytest.raises(D.DMRError) as e:
+        run.adjoint_record(2 * NT, NT)
+    assert e.value.code == D.EINVAL
+    with pytest.raises(D.DMRError):
+        D.batch_from_workloads([w, W.small_dmr()])
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_dmr_many_strips_match_oracle(precision):
     """Meshes several warp strips wide on both levels, with strips inside
