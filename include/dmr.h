@@ -228,10 +228,13 @@ int dmr_sync(const dmr_ctx* ctx);
  * changing the run -- 20 back-to-back copies of the launch are captured in a
  * CUDA graph and replayed, as the periods are; they write only next-level
  * buffers that the next step rewrites in full -- keeps the fastest; returns
- * the choice and the per-candidate mean launch times (ms). */
+ * the choice and the per-candidate mean launch times (ms).  With r >= 2 a
+ * second pass times fine sub-step 2 alone (no E^2 sample) for the same
+ * targets and keeps the fastest for the fine sub-steps that have launches of
+ * their own. */
 int dmr_autotune(dmr_ctx* ctx, int32_t* warps_per_sm, double trial_ms[5]);
 
-/* Set the strip height of the EM launches directly, as a warps-per-SM target
+/* Set the strip height of all EM launches directly, as a warps-per-SM target
  * in [1, 1024] (e.g. the choice dmr_autotune made on an earlier run of the
  * same size).  Results do not depend on it.  DMR_EINVAL otherwise. */
 int dmr_set_launch_shape(dmr_ctx* ctx, int32_t warps_per_sm);

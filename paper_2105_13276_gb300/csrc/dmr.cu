@@ -477,11 +477,16 @@ struct Engine final : Base {
   // (about 48 per SM); small meshes get 1-2 rows per warp so a launch costs
   // about one memory latency, large ones up to 64 (the warm-up row is 1/rows)
   int warps_per_sm = 48;     // strip-height policy (the batch autotuner may change it)
-  int em_rows(int nx, int ny) const {
-    const long long sx = (nx + 1 + dmr::STRIP_W - 1) / dmr::STRIP_W;
-    const long long target = (long long)num_sms * warps_per_sm;
+  int warps_per_sm_fine = 48;   // the same for the fine sub-steps after the first (own launches)
+  // rows per warp of an EM launch over an nx x ny mesh with sw-column strips;
+  // a multiple of rr (the fine mesh sums Ey over the r rows of a coarse row)
+  int em_rows(int nx, int ny, int sw, int rr, int wps) const {
+    const long long sx = (nx + 1 + sw - 1) / sw;
+    const long long target = (long long)num_sms * wps;
     long long rows = (sx * (ny + 1) + target - 1) / target;
-    return (int)std::min<long long>(64, std::max<long long>(1, rows));
+    rows = std::min<long long>(64, std::max<long long>(1, rows));
+    rows = (rows + rr - 1) / rr * rr;
+    return (int)std::min<long long>(rows, 64 - 64 % rr);
   }
 
 
@@ -584,6 +589,7 @@ struct Engine final : Base {
   // coarse EM launches compile the CPML terms in only for CPML runs
   void go_em(int nb, const dmr::EmArgs<T>& A) const {
     if (A.pml.on) dmr::k_em<T, true><<<nb, 32 * dmr::EM_WARPS, 0, st>>>(A);
+    else if (A.W.on) dmr::k_em<T, false, true><<<nb, 32 * dmr::EM_WARPS, 0, st>>>(A);
     else dmr::k_em<T, false><<<nb, 32 * dmr::EM_WARPS, 0, st>>>(A);
   }
   void go_em2(int nb, const dmr::EmArgs<T>& A0, const dmr::EmArgs<T>& A1) const {
@@ -591,15 +597,20 @@ struct Engine final : Base {
     else dmr::k_em2<T, false><<<nb, 32 * dmr::EM_WARPS, 0, st>>>(A0, A1);
   }
 
+  // rr: strips of a multiple of rr columns and rows per warp a multiple of rr
+  // (the last fine sub-step of a coarse step, which writes the a8 means); 1
+  // otherwise
   dmr::EmArgs<T> em_args(const dmr::Mesh<T>& src, T* const* dst, const dmr::Step<T>& c,
-                         const dmr::Bnd<T>& b, const dmr::Restr<T>& R) const {
+                         const dmr::Bnd<T>& b, int rr = 1, int wps = 0) const {
     dmr::EmArgs<T> A;
     A.m = src;
     A.dEx = dst[0]; A.dEy = dst[1]; A.dHz = dst[2]; A.dvx = dst[3]; A.dvy = dst[4];
-    A.c = c; A.b = b; A.R = R;
+    A.c = c; A.b = b;
     A.pml = dmr::Pml<T>{};
-    A.rows = em_rows(src.nx, src.ny);
-    A.gx = (src.nx + 1 + dmr::STRIP_W - 1) / dmr::STRIP_W;
+    A.W = dmr::RestrW<T>{};
+    A.sw = dmr::STRIP_W - dmr::STRIP_W % rr;
+    A.rows = em_rows(src.nx, src.ny, A.sw, rr, wps > 0 ? wps : warps_per_sm);
+    A.gx = (src.nx + 1 + A.sw - 1) / A.sw;
     const int sy = (src.ny + 1 + A.rows - 1) / A.rows;
     A.nblk = A.gx * ((sy + dmr::EM_WARPS - 1) / dmr::EM_WARPS);
     A.ncfb = 0;   // blocks per coarse-fine side (em_cfb)
@@ -621,20 +632,16 @@ struct Engine final : Base {
     dmr::Mesh<T> src = C;
     src.Ex = cE[cp][0]; src.Ey = cE[cp][1]; src.Hz = cE[cp][2]; src.vx = cE[cp][3]; src.vy = cE[cp][4];
     T* const* cdst = cE[cp ^ 1];
-    dmr::Restr<T> R{};
+    // the coarse arrays already hold the fine->coarse mean under the rectangle
+    // (written by the last fine sub-step of the previous coarse step, a8), so
+    // the coarse step reads plain arrays
+    (void)rv;
     const dmr::Mesh<T> fsrc = fine_at(fp);
-    if (has_fine && rv) {
-      R.on = 1;
-      R.I0 = rect[0]; R.J0 = rect[1]; R.I1 = rect[2]; R.J1 = rect[3]; R.r = r;
-      restr_bounds(&R.jlo, &R.jhi, &R.ilo, &R.ihi);
-      R.fEx = fsrc.Ex; R.fEy = fsrc.Ey; R.fp = fsrc.p;   // fine level n (k = 1: the step's start)
-      R.rinv = (T)(1.0 / (double)r);
-    }
     if (Ac) {
       dmr::Bnd<T> bc{};
       for (int q = 0; q < 4; ++q) bc.mode[q] = d.boundary == 1 ? dmr::BC_PEC : dmr::BC_MUR;
       bc.r = 1;
-      *Ac = em_args(src, cdst, sc, bc, R);
+      *Ac = em_args(src, cdst, sc, bc);
       Ac->kind = 0; Ac->N = NT; Ac->r = 1; Ac->ps = ph[0]; Ac->pc = ph[1];
       if (d.boundary == 1) {
         dmr::Pml<T>& P = Ac->pml;
@@ -672,7 +679,6 @@ struct Engine final : Base {
     }
     bf.cm = src;
     bf.cc = sc;
-    bf.cR = R;
     bf.cps = ph[0]; bf.cpc = ph[1]; bf.cN = NT;
     const int64_t mf = (int64_t)r * mlev + (k - 1);
     dmr::Step<T> sf = make_step(r, mf, (mf % ((int64_t)r * NT)) != 0);
@@ -680,9 +686,20 @@ struct Engine final : Base {
     bf.recompute = k == 1 ? 1 : 0;
     T* fdst[5] = {fineE(cur, fp ^ 1, 0), fineE(cur, fp ^ 1, 1), fineE(cur, fp ^ 1, 2),
                   fineE(cur, fp ^ 1, 3), fineE(cur, fp ^ 1, 4)};
-    const dmr::Restr<T> none{};
-    *Af = em_args(fsrc, fdst, sf, bf, none);
+    // the last sub-step's strips align with the coarse cells (a8 column groups and row sums)
+    // sub-steps after the first run alone, with their own strip height
+    *Af = em_args(fsrc, fdst, sf, bf, k == r ? r : 1, k > 1 ? warps_per_sm_fine : warps_per_sm);
     Af->kind = 1; Af->N = r * NT; Af->r = r; Af->ps = ph[2]; Af->pc = ph[3];
+    if (k == r) {
+      // a8: the last sub-step writes the mean of r collinear fine edges into
+      // the coarse E^{n+1} (the coarse step's output buffer)
+      dmr::RestrW<T>& W = Af->W;
+      W.on = 1;
+      W.cEx = cdst[0]; W.cEy = cdst[1]; W.cp = C.p;
+      W.I0 = rect[0]; W.J0 = rect[1]; W.I1 = rect[2]; W.J1 = rect[3]; W.r = r;
+      restr_bounds(&W.jlo, &W.jhi, &W.ilo, &W.ihi);
+      W.rinv = (T)(1.0 / (double)r);
+    }
   }
 
   // fine mesh view with E/H/v of parity fp
@@ -723,7 +740,9 @@ struct Engine final : Base {
         tend(h);
         flip_coarse();
       } else {
-        int h = tbeg(1, em_bytes(fn, acc_f));
+        // the last sub-step also writes the coarse E means under the rectangle (a8)
+        const double wb = k == r ? 2.0 * (double)L.es * (rect[2] - rect[0] + 1) * (rect[3] - rect[1] + 1) : 0.0;
+        int h = tbeg(1, em_bytes(fn, acc_f) + wb);
         go_em(Af.nblk + Af.ncfb, Af);
         tend(h);
       }
@@ -734,26 +753,10 @@ struct Engine final : Base {
     return launched("EM step");
   }
 
-  // write the fine->coarse E transfer into the coarse arrays (the EM kernel
-  // reads it on the fly; the period end, reads and growth need it stored)
-  void materialize_restriction() {
-    if (!has_fine || !rvalid) return;
-    int jlo, jhi, ilo, ihi;
-    restr_bounds(&jlo, &jhi, &ilo, &ihi);
-    const dim3 gr((rect[2] - rect[0] + 1 + BX - 1) / BX, (rect[3] - rect[1] + 1 + BY - 1) / BY);
-    const int h = tbeg(2, (double)(rect[2] - rect[0] + 1) * (rect[3] - rect[1] + 1) *
-                              (double)(2 * cfg.r + 2) * (double)L.es);
-    dmr::k_restrict<T><<<gr, dim3(BX, BY), 0, st>>>(C, F[cur], rect[0], rect[1], rect[2], rect[3],
-                                                    cfg.r, (T)(1.0 / (double)cfg.r), jlo, jhi, ilo, ihi);
-    tend(h);
-    counted(1);
-  }
-
   // continuity step, totals and flags at the end of a period (coarse level mlev)
   int launch_period_end(int64_t mlev) {
     const int r = cfg.r;
     const dim3 blk(BX, BY);
-    materialize_restriction();
     int h = tbeg(3, 0.0);
     dmr::Wts wc{cfg.nx, cfg.ny, has_fine ? 1 : 0, rect[0], rect[1], rect[2], rect[3]};
     dmr::Dens dc = make_dens(1);
@@ -1041,10 +1044,6 @@ struct Engine final : Base {
     if (int s = dims(field, level, &rows, &cols, &es)) return fail(s, "no such field / level");
     if (bytes < (size_t)rows * cols * es) return fail(DMR_ECAPACITY, "destination too small");
     const int p = field == DMR_FIELD_MASK ? cols : (level == 0 ? C.p : F[cur].p);
-    if (level == 0 && field != DMR_FIELD_MASK) {
-      materialize_restriction();
-      if (int e = launched("restriction")) return e;
-    }
     const void* src = field_ptr(field, level);
     if (field == DMR_FIELD_S2 && m % cfg.steps_per_period != 0) {
       // S2 holds the levels before the current one; add the current level so
@@ -1254,7 +1253,6 @@ struct Engine final : Base {
     for (int k = 0; k < 4; ++k) R->rect[k] = rect[k];
     R->fine = has_fine;
     R->rvalid = rvalid;
-    materialize_restriction();
     R->cEx = tape_copy(C.Ex, cplane_b());
     R->cEy = tape_copy(C.Ey, cplane_b());
     const int cp0 = cpar;
@@ -1290,7 +1288,6 @@ struct Engine final : Base {
     P->cur_b = cur;
     P->fine = has_fine;
     P->rvalid = rvalid;
-    materialize_restriction();
     P->cEx = tape_copy(C.Ex, cplane_b());
     P->cEy = tape_copy(C.Ey, cplane_b());
     P->nc = tape_copy(C.n, cplane_b());
@@ -1622,6 +1619,7 @@ struct Engine final : Base {
   // repeating it leaves the run unchanged.
   void set_shape(int wps) override {
     warps_per_sm = wps;
+    warps_per_sm_fine = wps;
     drop_graph();
   }
 
@@ -1650,6 +1648,30 @@ struct Engine final : Base {
       if (ms < best) { best = ms; best_w = cand[c]; }
     }
     warps_per_sm = best_w;
+    if (has_fine && cfg.r >= 2) {
+      // fine sub-step 2 alone, as it runs (reads the present fine state,
+      // writes the next-level buffers and adds its E^2 sample): the strip
+      // height of the later sub-steps.  The sample goes into S2, so S2 is
+      // kept in the idle fine set (rewritten at the next growth) and put back.
+      const size_t s2b = (size_t)(F[cur].ny + 1) * (size_t)F[cur].p * sizeof(double);
+      if (int s_ = ck(cudaMemcpyAsync(fS2[cur ^ 1], fS2[cur], s2b, cudaMemcpyDeviceToDevice, st),
+                      "autotune: keep S2")) return s_;
+      double best_f = 1e30;
+      int best_fw = warps_per_sm_fine;
+      for (int c = 0; c < 5; ++c) {
+        warps_per_sm_fine = cand[c];
+        dmr::EmArgs<T> Af;
+        em_args_for(2, m, cpar, fpar, true, nullptr, &Af);
+        auto launch = [&]() { go_em(Af.nblk + Af.ncfb, Af); };
+        float ms = 0.f;
+        if (int s_ = ck(graph_time(st, launch, kTrialLaunches, &ms), "autotune trial (fine)")) return s_;
+        launches += 4 * kTrialLaunches;
+        if (ms < best_f) { best_f = ms; best_fw = cand[c]; }
+      }
+      warps_per_sm_fine = best_fw;
+      if (int s_ = ck(cudaMemcpyAsync(fS2[cur], fS2[cur ^ 1], s2b, cudaMemcpyDeviceToDevice, st),
+                      "autotune: restore S2")) return s_;
+    }
     drop_graph();
     if (wps_out) *wps_out = best_w;
     return launched("autotune");
@@ -1842,7 +1864,10 @@ struct Batch final : BatchBase {
 
   int launch_em(const Tab& t, int64_t level, int k) {
     if (t.nseg == 0 || t.nblk == 0) return 0;
-    dmr::k_em_batch<T><<<t.nblk, 32 * dmr::EM_WARPS, 0, st>>>(t.args, t.off, t.nseg, (long long)level, k);
+    if (k > 1 && k == r)   // the last fine sub-step writes the fine->coarse E mean
+      dmr::k_em_batch<T, true><<<t.nblk, 32 * dmr::EM_WARPS, 0, st>>>(t.args, t.off, t.nseg, (long long)level, k);
+    else
+      dmr::k_em_batch<T><<<t.nblk, 32 * dmr::EM_WARPS, 0, st>>>(t.args, t.off, t.nseg, (long long)level, k);
     return 1;
   }
 
@@ -1988,7 +2013,7 @@ struct Batch final : BatchBase {
     double best = 1e30;
     int best_w = 48;
     for (int c = 0; c < 5; ++c) {
-      for (auto* e : runs) e->warps_per_sm = cand[c];
+      for (auto* e : runs) e->warps_per_sm = e->warps_per_sm_fine = cand[c];
       if (int s = build_tables()) return s;
       const Tab& t = t1[0][m & 1];   // steady tables (see Engine::autotune)
       float ms = 0.f;
@@ -1997,7 +2022,7 @@ struct Batch final : BatchBase {
       launches += 4 * 5;
       if (tune_ms[c] < best) { best = tune_ms[c]; best_w = cand[c]; }
     }
-    for (auto* e : runs) e->warps_per_sm = best_w;
+    for (auto* e : runs) e->warps_per_sm = e->warps_per_sm_fine = best_w;
     tuned_wps = best_w;
     return build_tables();
   }

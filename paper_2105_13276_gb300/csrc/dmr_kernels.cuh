@@ -39,23 +39,26 @@ struct Step {
   int accum;             // add |E_total|^2 of this level to S2
 };
 
-// Fine -> coarse transfer read on the fly (a8): while the coarse step loads
-// E^n, each coarse edge of the restriction set takes the mean of its r
-// collinear fine edges (the fine arrays hold level n after the sub-steps).
+// Fine -> coarse transfer on the producer side (a8): the last fine sub-step
+// of a coarse step, which computes the fine E^{n+1}, also writes the mean of
+// each r collinear fine edges into the coarse E^{n+1} arrays (the coarse
+// step's output, so the next coarse step reads plain arrays).  Ex: a shuffle
+// over the r lanes of a column group; Ey: a running sum over r rows.  The
+// sums are taken in the order q = 0 .. r-1, times 1/r.
 template <class T>
-struct Restr {
+struct RestrW {
   int on;
+  T *cEx, *cEy;             // coarse E^{n+1}
+  int cp;                   // coarse row pitch
   int I0, J0, I1, J1, r;
-  int jlo, jhi, ilo, ihi;   // Ex rows [jlo, jhi], Ey columns [ilo, ihi]
-  const T *fEx, *fEy;
-  int fp;
-  T rinv;                   // 1/r (exact for r a power of two)
+  int jlo, jhi, ilo, ihi;   // coarse Ex rows [jlo, jhi], Ey columns [ilo, ihi]
+  T rinv;
 };
 
 // Coarse-fine boundary (Eq. 5b) for the fine mesh: per side, Mur or the
 // coarse tangential-E line before (old) and after (new) the coarse step.
 // With `recompute`, the new coarse values are evaluated from the coarse
-// level-n state (cm, cc, cR) with the coarse step's own arithmetic instead of
+// level-n state (cm, cc) with the coarse step's own arithmetic instead of
 // being read, so a fine sub-step need not wait for the coarse step.
 template <class T>
 struct Bnd {
@@ -71,7 +74,6 @@ struct Bnd {
   int recompute;
   Mesh<T> cm;
   Step<T> cc;
-  Restr<T> cR;
   // batched launches: sin/cos of the coarse phase per step of a period
   const T *cps, *cpc;
   int cN;
@@ -114,33 +116,16 @@ __device__ __forceinline__ T node_e2(const Mesh<T>& m, const Step<T>& c, int i, 
 
 constexpr int TX = 32, TY = 8;   // 2-D thread block of the node-wise kernels
 
+// E at an edge, 0 off the mesh
 template <class T>
-__device__ __forceinline__ T restricted_ex(const Restr<T>& R, int i, int j) {
-  const T* f = R.fEx + (size_t)(R.r * (j - R.J0)) * R.fp + R.r * (i - R.I0);
-  T acc = f[0];
-  for (int q = 1; q < R.r; ++q) acc = acc + f[q];
-  return acc * R.rinv;
-}
-
-template <class T>
-__device__ __forceinline__ T restricted_ey(const Restr<T>& R, int i, int j) {
-  const T* f = R.fEy + (size_t)(R.r * (j - R.J0)) * R.fp + R.r * (i - R.I0);
-  T acc = f[0];
-  for (int q = 1; q < R.r; ++q) acc = acc + f[(size_t)q * R.fp];
-  return acc * R.rinv;
-}
-
-template <class T>
-__device__ __forceinline__ T load_ex(const Mesh<T>& m, const Restr<T>& R, int i, int j) {
+__device__ __forceinline__ T load_ex(const Mesh<T>& m, int i, int j) {
   if (i < 0 || i >= m.nx || j < 0 || j > m.ny) return T(0);
-  if (R.on && i >= R.I0 && i < R.I1 && j >= R.jlo && j <= R.jhi) return restricted_ex(R, i, j);
   return m.Ex[j * m.p + i];
 }
 
 template <class T>
-__device__ __forceinline__ T load_ey(const Mesh<T>& m, const Restr<T>& R, int i, int j) {
+__device__ __forceinline__ T load_ey(const Mesh<T>& m, int i, int j) {
   if (i < 0 || i > m.nx || j < 0 || j >= m.ny) return T(0);
-  if (R.on && i >= R.ilo && i <= R.ihi && j >= R.J0 && j < R.J1) return restricted_ey(R, i, j);
   return m.Ey[j * m.p + i];
 }
 
@@ -151,9 +136,9 @@ __device__ __forceinline__ T coarse_new_ex(const Bnd<T>& b, int i, int J) {
   const Mesh<T>& m = b.cm;
   const Step<T>& c = b.cc;
   const int p = m.p;
-  const T exm = load_ex(m, b.cR, i, J - 1), exc = load_ex(m, b.cR, i, J), exn = load_ex(m, b.cR, i, J + 1);
-  const T eym = load_ey(m, b.cR, i, J - 1), eyc = load_ey(m, b.cR, i, J);
-  const T eymr = load_ey(m, b.cR, i + 1, J - 1), eyr = load_ey(m, b.cR, i + 1, J);
+  const T exm = load_ex(m, i, J - 1), exc = load_ex(m, i, J), exn = load_ex(m, i, J + 1);
+  const T eym = load_ey(m, i, J - 1), eyc = load_ey(m, i, J);
+  const T eymr = load_ey(m, i + 1, J - 1), eyr = load_ey(m, i + 1, J);
   const T hzp = m.Hz[(J - 1) * p + i] - c.ch * ((eymr - eym) - (exc - exm));
   const T hz = m.Hz[J * p + i] - c.ch * ((eyr - eyc) - (exn - exc));
   const T v = c.va * m.vx[J * p + i] - c.vb * exc;
@@ -165,9 +150,9 @@ __device__ __forceinline__ T coarse_new_ey(const Bnd<T>& b, int I, int j) {
   const Mesh<T>& m = b.cm;
   const Step<T>& c = b.cc;
   const int p = m.p;
-  const T eyl = load_ey(m, b.cR, I - 1, j), eyc = load_ey(m, b.cR, I, j), eyr = load_ey(m, b.cR, I + 1, j);
-  const T exl = load_ex(m, b.cR, I - 1, j), exln = load_ex(m, b.cR, I - 1, j + 1);
-  const T exc = load_ex(m, b.cR, I, j), exn = load_ex(m, b.cR, I, j + 1);
+  const T eyl = load_ey(m, I - 1, j), eyc = load_ey(m, I, j), eyr = load_ey(m, I + 1, j);
+  const T exl = load_ex(m, I - 1, j), exln = load_ex(m, I - 1, j + 1);
+  const T exc = load_ex(m, I, j), exn = load_ex(m, I, j + 1);
   const T hzl = m.Hz[j * p + I - 1] - c.ch * ((eyc - eyl) - (exln - exl));
   const T hz = m.Hz[j * p + I] - c.ch * ((eyr - eyc) - (exn - exc));
   const T v = c.va * m.vy[j * p + I] - c.vb * (eyc + incident(c, I));
@@ -222,8 +207,9 @@ __device__ __forceinline__ T cfb_blend(const Bnd<T>& b, T lo, T xp, T n0, T n1) 
 // neighbouring E^n, H^{n-1/2}, v^{n-1/2} while those are being advanced.
 //
 // Warp strips: lane L of a warp holds node column i = c0 - 1 + L with
-// c0 = STRIP_W * strip; lanes 1..STRIP_W own their columns, lane 0 and lane 31
-// are halo columns that only load and (lane 0) compute H for their neighbour.
+// c0 = sw * strip (sw = STRIP_W, or the largest multiple of r up to it on the
+// fine mesh); lanes 1..sw own their columns, lane 0 and lane sw + 1 are halo
+// columns that only load and (lane 0) compute H for their neighbour.
 // The warp marches up `rows` node rows, carrying the previous row's E^n, new
 // H, density and Ey^n in registers; every x-neighbour comes by shuffle, so
 // there is no shared memory and no block barrier.  A Mur side's boundary edge
@@ -231,6 +217,10 @@ __device__ __forceinline__ T cfb_blend(const Bnd<T>& b, T lo, T xp, T n0, T n1) 
 // levels.  Each element is read once and written once: 60 B per cell (FP32).
 constexpr int STRIP_W = 30;
 constexpr int EM_WARPS = 4;   // warps per block (consecutive strips in y)
+// resident EM blocks per SM the register allocation must allow: a 512^2
+// coarse step with its fine sub-step is one wave of ~1200 blocks at 9 per SM
+template <class T>
+constexpr int kEmMinBlocks = sizeof(T) == 4 ? 9 : 6;
 
 // CPML layer of the coarse mesh (Roden-Gedney recursion, kappa = 1): psi of
 // the Hz curl terms along x and y at the cells, of the Ex (y) and Ey (x)
@@ -253,8 +243,9 @@ struct EmArgs {
   T *dEx, *dEy, *dHz, *dvx, *dvy;
   Step<T> c;
   Bnd<T> b;
-  Restr<T> R;
   Pml<T> pml;
+  RestrW<T> W;
+  int sw;               // owned columns per strip (STRIP_W; a multiple of r on the fine mesh)
   int rows, gx, nblk;   // strips: rows per warp, strips across x, blocks
   int ncfb;             // blocks that write the coarse-fine boundary E (Eq. 5b)
   // batched launches: the level-dependent fields (phase, E^2 sample, Eq. 5b
@@ -329,20 +320,22 @@ __device__ __forceinline__ void em_cfb(const EmArgs<T>& A, int blk) {
   else A.dEy[q * p + nfx] = v;
 }
 
-template <class T, bool PML>
+template <class T, bool PML, bool WR>
 __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk);
 
 // Blocks of one mesh's EM step: the coarse-fine side blocks first (the
 // longest dependent chain of the launch, so they are dispatched first), then
 // the strips.
 // PML: compile the CPML terms in (coarse launches of CPML runs only)
-template <class T, bool PML = false>
+// WR: compile the producer-side fine->coarse transfer in (launches of the
+// last fine sub-step of a coarse step only)
+template <class T, bool PML = false, bool WR = false>
 __device__ __forceinline__ void em_segment(const EmArgs<T>& A, int blk) {
   if (blk < A.ncfb) em_cfb(A, blk);
-  else em_strips<T, PML>(A, blk - A.ncfb);
+  else em_strips<T, PML, WR>(A, blk - A.ncfb);
 }
 
-template <class T, bool PML>
+template <class T, bool PML, bool WR>
 __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
   const Mesh<T>& m = A.m;
   T* __restrict__ dEx = A.dEx;
@@ -352,35 +345,36 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
   T* __restrict__ dvy = A.dvy;
   const Step<T>& c = A.c;
   const Bnd<T>& b = A.b;
-  const Restr<T>& R = A.R;
   const int rows = A.rows;
   const int lane = threadIdx.x & 31;
   const int bx = blk % A.gx, byb = blk / A.gx;
   const int sy = byb * EM_WARPS + (threadIdx.x >> 5);
   const int p = m.p, nx = m.nx, ny = m.ny;
-  const int i = bx * STRIP_W - 1 + lane;
+  const int sw = A.sw;
+  const int i = bx * sw - 1 + lane;
   const int j0 = sy * rows;
   if (j0 > ny) return;                       // whole warp leaves together
   const int j1 = min(j0 + rows, ny + 1);     // node rows [j0, j1)
-  const bool own = lane >= 1 && lane <= STRIP_W && i <= nx;
+  const bool own = lane >= 1 && lane <= sw && i <= nx;
   // CPML (warp-uniform): the strip's columns or rows reach into the layer
   const Pml<T>& P = A.pml;
-  const int c0 = bx * STRIP_W;
-  const bool pw = PML && P.on && (c0 - 1 <= P.L || c0 + STRIP_W >= nx - P.L || j0 - 1 <= P.L ||
+  const int c0 = bx * sw;
+  const bool pw = PML && P.on && (c0 - 1 <= P.L || c0 + sw >= nx - P.L || j0 - 1 <= P.L ||
                            j0 + rows >= ny - P.L);
-  const bool xcol = i >= 0 && i < nx;        // column has Ex / Hz
-  const bool ycol = i >= 0 && i <= nx;       // column has Ey / n
+  const bool live = lane <= sw + 1;          // lanes past the right halo idle
+  const bool xcol = live && i >= 0 && i < nx;    // column has Ex / Hz
+  const bool ycol = live && i >= 0 && i <= nx;   // column has Ey / n
   const T inc = ycol ? incident(c, i) : T(0);
   const T inc0 = incident(c, 0), incn = incident(c, nx);
   // ---- carried state for row j: Ex^n(j), Ex^n(j-1), Ey^n(j-1), Hz^{n+1/2}(j-1), n(j)
   T exc = T(0), exp_ = T(0), eyp = T(0), hzp = T(0), nc = T(0);
-  if (xcol) exc = load_ex(m, R, i, j0);
+  if (xcol) exc = load_ex(m, i, j0);
   if (ycol) nc = m.n[j0 * p + i];
   if (j0 > 0) {
     // H of row j0-1, needed by the Ex update of row j0
     const int jm = j0 - 1;
-    const T exm = xcol ? load_ex(m, R, i, jm) : T(0);
-    const T eym = ycol ? load_ey(m, R, i, jm) : T(0);
+    const T exm = xcol ? load_ex(m, i, jm) : T(0);
+    const T eym = ycol ? load_ey(m, i, jm) : T(0);
     const T hzo = xcol ? m.Hz[jm * p + i] : T(0);
     const T eyr = __shfl_down_sync(0xffffffffu, eym, 1);
     if (xcol) {
@@ -404,8 +398,8 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
     Row q;
     const int id = j * p + i;
     const bool in = j < ny;
-    q.exn = (xcol && in) ? load_ex(m, R, i, j + 1) : T(0);
-    q.eyc = (ycol && in) ? load_ey(m, R, i, j) : T(0);
+    q.exn = (xcol && in) ? load_ex(m, i, j + 1) : T(0);
+    q.eyc = (ycol && in) ? load_ey(m, i, j) : T(0);
     q.hzo = (xcol && in) ? m.Hz[id] : T(0);
     q.vxo = xcol ? m.vx[id] : T(0);
     q.vyo = (ycol && in) ? m.vy[id] : T(0);
@@ -414,6 +408,15 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
     return q;
   };
   Row nxt = load_row(j0);
+  // a8 on the producer side: the column tests are fixed per lane; the row
+  // phase jq = j mod r and the coarse row Jc = J0 + j / r advance with j
+  // (j0 is a multiple of r), so the loop divides by nothing
+  const int rw = WR ? A.W.r : 1;
+  const bool hx = WR && own && i < nx && (i % rw) == 0;                  // head of an Ex group
+  const int Ic = WR ? A.W.I0 + (i > 0 ? i / rw : 0) : 0;
+  const bool hy = hx && i > 0 && Ic >= A.W.ilo && Ic <= A.W.ihi;        // restricted Ey column
+  int jq = 0, Jc = WR ? A.W.J0 + j0 / rw : 0;
+  T eacc = T(0), eaccL = T(0), eaccR = T(0);   // Ey sums over the r rows of a coarse row
   for (int j = j0; j < j1; ++j) {
     const int id = j * p + i;
     const Row cur = nxt;
@@ -443,6 +446,7 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
     const T eyl = __shfl_up_sync(0xffffffffu, eyc, 1);
     const T vyl = __shfl_up_sync(0xffffffffu, vyo, 1);
     const T vyr = __shfl_down_sync(0xffffffffu, vyo, 1);
+    T exw = T(0), exw0 = T(0), exwN = T(0), eyw = T(0), eywL = T(0), eywR = T(0);   // new E (a8)
     if (own) {
       if (i < nx && j < ny) dHz[id] = hz;
       // ---- S2 += |E^n|^2 at node (i, j)
@@ -472,14 +476,17 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
             en = exc + c.ce * (hz - hzp) + c.cj * (nc + ncr) * v;
           }
           dEx[id] = en;
+          exw = en;
           if (j == 1 && b.mode[SIDE_BOTTOM] == BC_MUR) {
             dvx[i] = c.va * m.vx[i] - c.vb * exp_;
-            dEx[i] = exc + c.mur * (en - exp_);
+            exw0 = exc + c.mur * (en - exp_);
+            dEx[i] = exw0;
           }
           if (j == ny - 1 && b.mode[SIDE_TOP] == BC_MUR) {
             const int ib = ny * p + i;
             dvx[ib] = c.va * m.vx[ib] - c.vb * exn;
-            dEx[ib] = exc + c.mur * (en - exn);
+            exwN = exc + c.mur * (en - exn);
+            dEx[ib] = exwN;
           }
         } else {
           const int sd = (j == 0) ? SIDE_BOTTOM : SIDE_TOP;
@@ -505,15 +512,18 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
             en = eyc - c.ce * (hz - hzl) + c.cj * (nc + nn) * v;
           }
           dEy[id] = en;
+          eyw = en;
           if (i == 1 && b.mode[SIDE_LEFT] == BC_MUR) {
             const int ib = j * p;
             dvy[ib] = c.va * vyl - c.vb * (eyl + inc0);
-            dEy[ib] = eyc + c.mur * (en - eyl);
+            eywL = eyc + c.mur * (en - eyl);
+            dEy[ib] = eywL;
           }
           if (i == nx - 1 && b.mode[SIDE_RIGHT] == BC_MUR) {
             const int ib = j * p + nx;
             dvy[ib] = c.va * vyr - c.vb * (eyr + incn);
-            dEy[ib] = eyc + c.mur * (en - eyr);
+            eywR = eyc + c.mur * (en - eyr);
+            dEy[ib] = eywR;
           }
         } else {
           const int sd = (i == 0) ? SIDE_LEFT : SIDE_RIGHT;
@@ -525,6 +535,36 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
         }
       }
     }
+    if (WR && A.W.on) {
+      // a8 on the producer side (last fine sub-step of a coarse step)
+      const RestrW<T>& Wr = A.W;
+      if (j > 0 && j < ny && jq == 0) {
+        T acc = exw;
+        for (int q = 1; q < rw; ++q) acc = acc + __shfl_down_sync(0xffffffffu, exw, q);
+        if (hx && Jc >= Wr.jlo && Jc <= Wr.jhi) Wr.cEx[Jc * Wr.cp + Ic] = acc * Wr.rinv;
+      }
+      if (j == 1 && b.mode[SIDE_BOTTOM] == BC_MUR) {     // fine row 0 (Mur), coarse row J0
+        T acc = exw0;
+        for (int q = 1; q < rw; ++q) acc = acc + __shfl_down_sync(0xffffffffu, exw0, q);
+        if (hx) Wr.cEx[Wr.J0 * Wr.cp + Ic] = acc * Wr.rinv;
+      }
+      if (j == ny - 1 && b.mode[SIDE_TOP] == BC_MUR) {   // fine row ny (Mur), coarse row J1
+        T acc = exwN;
+        for (int q = 1; q < rw; ++q) acc = acc + __shfl_down_sync(0xffffffffu, exwN, q);
+        if (hx) Wr.cEx[Wr.J1 * Wr.cp + Ic] = acc * Wr.rinv;
+      }
+      if (j < ny) {
+        eacc = jq == 0 ? eyw : eacc + eyw;
+        eaccL = jq == 0 ? eywL : eaccL + eywL;
+        eaccR = jq == 0 ? eywR : eaccR + eywR;
+        if (jq == rw - 1) {
+          if (hy) Wr.cEy[Jc * Wr.cp + Ic] = eacc * Wr.rinv;
+          if (own && i == 1 && b.mode[SIDE_LEFT] == BC_MUR) Wr.cEy[Jc * Wr.cp + Wr.I0] = eaccL * Wr.rinv;
+          if (own && i == nx - 1 && b.mode[SIDE_RIGHT] == BC_MUR) Wr.cEy[Jc * Wr.cp + Wr.I1] = eaccR * Wr.rinv;
+        }
+      }
+      if (++jq == rw) { jq = 0; ++Jc; }
+    }
     exp_ = exc;
     exc = exn;
     eyp = eyc;
@@ -533,17 +573,17 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
   }
 }
 
-template <class T, bool PML = false>
-__global__ void __launch_bounds__(32 * EM_WARPS) k_em(EmArgs<T> A) {
-  em_segment<T, PML>(A, blockIdx.x);
+template <class T, bool PML = false, bool WR = false>
+__global__ void __launch_bounds__(32 * EM_WARPS, kEmMinBlocks<T>) k_em(EmArgs<T> A) {
+  em_segment<T, PML, WR>(A, blockIdx.x);
 }
 
 constexpr int kSegStage = 256;   // segment offsets staged in shared memory up to this many
 
 // Batched EM launch: segment s (one mesh of one run) owns blocks
 // [off[s], off[s+1]); its arguments come from a table in device memory.
-template <class T>
-__global__ void __launch_bounds__(32 * EM_WARPS) k_em_batch(const EmArgs<T>* __restrict__ tab,
+template <class T, bool WR = false>
+__global__ void __launch_bounds__(32 * EM_WARPS, 5) k_em_batch(const EmArgs<T>* __restrict__ tab,
                                                             const int* __restrict__ off, int nseg,
                                                             long long m, int k) {
   __shared__ EmArgs<T> A;
@@ -575,7 +615,7 @@ __global__ void __launch_bounds__(32 * EM_WARPS) k_em_batch(const EmArgs<T>* __r
   __syncthreads();
   if (threadIdx.x == 0) em_set_level(A, m, k);
   __syncthreads();
-  em_segment(A, b - base);
+  em_segment<T, false, WR>(A, b - base);
 }
 
 // Two independent EM steps in one launch: the coarse step A0 and the first
@@ -583,34 +623,10 @@ __global__ void __launch_bounds__(32 * EM_WARPS) k_em_batch(const EmArgs<T>* __r
 // blocks come first in the grid (their side blocks carry the launch's
 // longest dependent chain).
 template <class T, bool PML = false>
-__global__ void __launch_bounds__(32 * EM_WARPS) k_em2(EmArgs<T> A0, EmArgs<T> A1) {
+__global__ void __launch_bounds__(32 * EM_WARPS, kEmMinBlocks<T>) k_em2(EmArgs<T> A0, EmArgs<T> A1) {
   const int n1 = A1.nblk + A1.ncfb;   // the fine sub-step's blocks first
   if ((int)blockIdx.x < n1) em_segment(A1, blockIdx.x);
   else em_segment<T, PML>(A0, blockIdx.x - n1);
-}
-
-// a8: coarse E edges of the closed rectangle (except tangential edges of
-// interior sides) = mean of the r collinear fine edges.  Grid over the
-// rectangle's coarse nodes.
-template <class T>
-__global__ void k_restrict(Mesh<T> c, Mesh<T> f, int I0, int J0, int I1, int J1, int r, T rinv,
-                           int jlo, int jhi, int ilo, int ihi) {
-  const int i = I0 + blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = J0 + blockIdx.y * blockDim.y + threadIdx.y;
-  if (i > I1 || j > J1) return;
-  const int fa = r * (i - I0), fb = r * (j - J0);
-  if (i < I1 && j >= jlo && j <= jhi) {
-    const T* s = f.Ex + (size_t)fb * f.p + fa;
-    T acc = s[0];
-    for (int q = 1; q < r; ++q) acc = acc + s[q];
-    c.Ex[j * c.p + i] = acc * rinv;
-  }
-  if (j < J1 && i >= ilo && i <= ihi) {
-    const T* s = f.Ey + (size_t)fb * f.p + fa;
-    T acc = s[0];
-    for (int q = 1; q < r; ++q) acc = acc + s[(size_t)q * f.p];
-    c.Ey[j * c.p + i] = acc * rinv;
-  }
 }
 
 // ----------------------------------------------------------------------------

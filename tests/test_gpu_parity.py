@@ -361,11 +361,14 @@ def test_timing_counts_launches():
     run.advance(64)
     kt = run.kernel_times()
     assert kt["fine_em"][1] == 64 and kt["fine_em"][0] > 0
-    # algorithmic bytes: 60 B per fine node per FP32 sub-step (44 B without an E^2 sample)
+    # algorithmic bytes: 60 B per fine node per FP32 sub-step (44 B without an
+    # E^2 sample), plus the coarse Ex, Ey means the last sub-step writes under
+    # the rectangle (8 B per coarse node)
     ms, n, nbytes = kt["fine_em"]
     fr = run.get_patch()
     pts = (2 * (fr[2] - fr[0]) + 1) * (2 * (fr[3] - fr[1]) + 1)
-    assert n == 64 and nbytes <= 64 * pts * 60
+    cpts = (fr[2] - fr[0] + 1) * (fr[3] - fr[1] + 1)
+    assert n == 64 and nbytes <= 64 * (pts * 60 + cpts * 8)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
