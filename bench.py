@@ -502,7 +502,7 @@ def run_ours(args):
 
     # timed run: no per-kernel instrumentation.  The dominant kernel is the
     # first EM launch of a coarse step (k_em2: coarse step + first fine
-    # sub-step, about two thirds of the period in the ncu launch list); its
+    # sub-step, about half of the period in the ncu launch list); its
     # duration is taken from the autotuner's graph replays of that launch on
     # the run's stream, at the start and at the end of the timed run.
     run = D.run_from_workload(w, device=dev)
