@@ -586,15 +586,33 @@ struct Engine final : Base {
     return pts * (11.0 * (double)L.es + (accum ? 16.0 : 0.0));
   }
 
-  // coarse EM launches compile the CPML terms in only for CPML runs
-  void go_em(int nb, const dmr::EmArgs<T>& A) const {
-    if (A.pml.on) dmr::k_em<T, true><<<nb, 32 * dmr::EM_WARPS, 0, st>>>(A);
-    else if (A.W.on) dmr::k_em<T, false, true><<<nb, 32 * dmr::EM_WARPS, 0, st>>>(A);
-    else dmr::k_em<T, false><<<nb, 32 * dmr::EM_WARPS, 0, st>>>(A);
+  // An EM launch that directly follows another EM launch on the stream may
+  // start (as a programmatic dependent launch) while that one finishes: its
+  // kernel waits for it before touching memory (pdl_enter).  Not used after
+  // any other stream operation, nor while per-kernel events are recorded.
+  template <class... P, class... A>
+  void launch_em_kernel(void (*kern)(P...), int nb, bool pdl, A&&... args) const {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(nb);
+    lc.blockDim = dim3(32 * dmr::EM_WARPS);
+    lc.dynamicSmemBytes = 0;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = pdl ? at : nullptr;
+    lc.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&lc, kern, std::forward<A>(args)...);
   }
-  void go_em2(int nb, const dmr::EmArgs<T>& A0, const dmr::EmArgs<T>& A1) const {
-    if (A0.pml.on) dmr::k_em2<T, true><<<nb, 32 * dmr::EM_WARPS, 0, st>>>(A0, A1);
-    else dmr::k_em2<T, false><<<nb, 32 * dmr::EM_WARPS, 0, st>>>(A0, A1);
+  // coarse EM launches compile the CPML terms in only for CPML runs
+  void go_em(int nb, const dmr::EmArgs<T>& A, bool pdl = false) const {
+    if (A.pml.on) launch_em_kernel(dmr::k_em<T, true>, nb, pdl, A);
+    else if (A.W.on) launch_em_kernel(dmr::k_em<T, false, true>, nb, pdl, A);
+    else launch_em_kernel(dmr::k_em<T, false>, nb, pdl, A);
+  }
+  void go_em2(int nb, const dmr::EmArgs<T>& A0, const dmr::EmArgs<T>& A1, bool pdl = false) const {
+    if (A0.pml.on) launch_em_kernel(dmr::k_em2<T, true>, nb, pdl, A0, A1);
+    else launch_em_kernel(dmr::k_em2<T, false>, nb, pdl, A0, A1);
   }
 
   // rr: strips of a multiple of rr columns and rows per warp a multiple of rr
@@ -710,6 +728,10 @@ struct Engine final : Base {
     return f;
   }
 
+  // true right after an EM launch on the stream (nothing else in between)
+  bool last_em = false;
+  bool pdl_next() const { return last_em && !timing; }
+
   // one coarse step from level mlev.  The coarse step (reading the restricted
   // E of the previous step on the fly) and the first fine sub-step (which
   // evaluates the coarse E^{n+1} on its boundary lines itself) are
@@ -722,8 +744,9 @@ struct Engine final : Base {
     const double cbytes = em_bytes((double)(C.nx + 1) * (C.ny + 1), acc_c);
     if (!has_fine) {
       int h = tbeg(0, cbytes);
-      go_em(Ac.nblk + Ac.ncfb, Ac);
+      go_em(Ac.nblk + Ac.ncfb, Ac, pdl_next());
       tend(h);
+      last_em = true;
       counted(1);
       flip_coarse();
       return launched("coarse EM");
@@ -736,16 +759,17 @@ struct Engine final : Base {
       if (k > 1) em_args_for(k, mlev, cp0, fpar, rvalid, nullptr, &Af);
       if (k == 1) {
         int h = tbeg(0, cbytes + em_bytes(fn, acc_f));
-        go_em2(Ac.nblk + Ac.ncfb + Af.nblk + Af.ncfb, Ac, Af);
+        go_em2(Ac.nblk + Ac.ncfb + Af.nblk + Af.ncfb, Ac, Af, pdl_next());
         tend(h);
         flip_coarse();
       } else {
         // the last sub-step also writes the coarse E means under the rectangle (a8)
         const double wb = k == r ? 2.0 * (double)L.es * (rect[2] - rect[0] + 1) * (rect[3] - rect[1] + 1) : 0.0;
         int h = tbeg(1, em_bytes(fn, acc_f) + wb);
-        go_em(Af.nblk + Af.ncfb, Af);
+        go_em(Af.nblk + Af.ncfb, Af, pdl_next());
         tend(h);
       }
+      last_em = true;
       counted(1);
       flip_fine();
     }
@@ -757,6 +781,7 @@ struct Engine final : Base {
   int launch_period_end(int64_t mlev) {
     const int r = cfg.r;
     const dim3 blk(BX, BY);
+    last_em = false;
     int h = tbeg(3, 0.0);
     dmr::Wts wc{cfg.nx, cfg.ny, has_fine ? 1 : 0, rect[0], rect[1], rect[2], rect[3]};
     dmr::Dens dc = make_dens(1);
@@ -939,6 +964,7 @@ struct Engine final : Base {
   int advance(int64_t n) override {
     if (n < 0) return fail(DMR_EINVAL, "negative step count");
     const int NT = cfg.steps_per_period;
+    last_em = false;   // other work may have been queued on the stream since
     while (n > 0) {
       if (graphs && m % NT == 0 && n >= NT) {
         // a graph holds the buffer parities it was captured with
@@ -947,6 +973,7 @@ struct Engine final : Base {
           if (int s = capture()) return s;
         }
         if (int s = ck(cudaGraphLaunch(gexec, st), "cudaGraphLaunch")) return s;
+        last_em = false;
         launches += graph_nodes;
         m += NT;
         n -= NT;
@@ -978,6 +1005,7 @@ struct Engine final : Base {
     const int c0 = cpar, f0 = fpar;
     const bool rv0 = rvalid;
     int s = DMR_OK;
+    last_em = false;   // the graph's first launch follows the previous replay's copy
     for (int q = 0; q < NT && !s; ++q) s = launch_coarse_step(m + q);
     if (!s) s = launch_period_end(m + NT);
     capturing = false;

@@ -215,6 +215,15 @@ __device__ __forceinline__ T cfb_blend(const Bnd<T>& b, T lo, T xp, T n0, T n1) 
 // there is no shared memory and no block barrier.  A Mur side's boundary edge
 // is advanced by the owner of the adjacent interior edge, which holds both E
 // levels.  Each element is read once and written once: 60 B per cell (FP32).
+// Programmatic dependent launch: an EM kernel lets the next EM launch of the
+// stream be scheduled as soon as all its blocks have started, and waits for
+// the previous one to complete (and its writes to be visible) before it
+// touches memory.  Launched without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 constexpr int STRIP_W = 30;
 constexpr int EM_WARPS = 4;   // warps per block (consecutive strips in y)
 // resident EM blocks per SM the register allocation must allow: a 512^2
@@ -575,6 +584,7 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
 
 template <class T, bool PML = false, bool WR = false>
 __global__ void __launch_bounds__(32 * EM_WARPS, kEmMinBlocks<T>) k_em(EmArgs<T> A) {
+  pdl_enter();
   em_segment<T, PML, WR>(A, blockIdx.x);
 }
 
@@ -624,6 +634,7 @@ __global__ void __launch_bounds__(32 * EM_WARPS, 5) k_em_batch(const EmArgs<T>* 
 // longest dependent chain).
 template <class T, bool PML = false>
 __global__ void __launch_bounds__(32 * EM_WARPS, kEmMinBlocks<T>) k_em2(EmArgs<T> A0, EmArgs<T> A1) {
+  pdl_enter();
   const int n1 = A1.nblk + A1.ncfb;   // the fine sub-step's blocks first
   if ((int)blockIdx.x < n1) em_segment(A1, blockIdx.x);
   else em_segment<T, PML>(A0, blockIdx.x - n1);
