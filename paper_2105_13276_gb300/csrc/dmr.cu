@@ -478,13 +478,20 @@ struct Engine final : Base {
   // about one memory latency, large ones up to 64 (the warm-up row is 1/rows)
   int warps_per_sm = 48;     // strip-height policy (the batch autotuner may change it)
   int warps_per_sm_fine = 48;   // the same for the fine sub-steps after the first (own launches)
+  bool in_batch = false;        // a run of a batch (its launches go through segment tables)
   // rows per warp of an EM launch over an nx x ny mesh with sw-column strips;
-  // a multiple of rr (the fine mesh sums Ey over the r rows of a coarse row)
+  // a multiple of rr, or 1 (the last fine sub-step sums Ey over the r rows of
+  // a coarse row)
   int em_rows(int nx, int ny, int sw, int rr, int wps) const {
     const long long sx = (nx + 1 + sw - 1) / sw;
     const long long target = (long long)num_sms * wps;
     long long rows = (sx * (ny + 1) + target - 1) / target;
     rows = std::min<long long>(64, std::max<long long>(1, rows));
+    // one row per warp stays one row when r divides the warps of a block
+    // (the block's warps then sum Ey in groups of r, em_strips); not in a
+    // batch, whose blocks each stage their segment's arguments first, so
+    // halving the rows there doubles that work
+    if (rr > 1 && rows == 1 && dmr::EM_WARPS % rr == 0 && !in_batch) return 1;
     rows = (rows + rr - 1) / rr * rr;
     return (int)std::min<long long>(rows, 64 - 64 % rr);
   }
@@ -2122,6 +2129,7 @@ int batch_make(const dmr_config* cfgs, int n, const std::vector<Derived>& ds,
     e->L = ls[q];
     e->ws = ws + o;
     e->st = st;
+    e->in_batch = true;
     o += up(ls[q].total, 256);
     b->runs.push_back(e);
     if (int s = e->init()) { *err = fmt("run %d: %s", q, e->err.c_str()); delete b; return s; }

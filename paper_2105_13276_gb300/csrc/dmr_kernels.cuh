@@ -424,7 +424,10 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
   const bool hx = WR && own && i < nx && (i % rw) == 0;                  // head of an Ex group
   const int Ic = WR ? A.W.I0 + (i > 0 ? i / rw : 0) : 0;
   const bool hy = hx && i > 0 && Ic >= A.W.ilo && Ic <= A.W.ihi;        // restricted Ey column
-  int jq = 0, Jc = WR ? A.W.J0 + j0 / rw : 0;
+  // one row per warp (r dividing EM_WARPS): the r rows of a coarse row belong
+  // to r consecutive warps of the block, which sum Ey through shared memory
+  const bool cross = WR && rows == 1 && rw > 1;
+  int jq = cross ? j0 % rw : 0, Jc = WR ? A.W.J0 + j0 / rw : 0;
   T eacc = T(0), eaccL = T(0), eaccR = T(0);   // Ey sums over the r rows of a coarse row
   for (int j = j0; j < j1; ++j) {
     const int id = j * p + i;
@@ -562,7 +565,31 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
         for (int q = 1; q < rw; ++q) acc = acc + __shfl_down_sync(0xffffffffu, exwN, q);
         if (hx) Wr.cEx[Wr.J1 * Wr.cp + Ic] = acc * Wr.rinv;
       }
-      if (j < ny) {
+      if (j < ny && cross) {
+        // the group's rows are all below ny (ny and the group start are
+        // multiples of r), so all r warps of the group arrive here
+        __shared__ T sey[EM_WARPS][32], slr[EM_WARPS][2];
+        const int wq = threadIdx.x >> 5, w0 = wq - jq;
+        sey[wq][lane] = eyw;
+        if (own && i == 1) slr[wq][0] = eywL;
+        if (own && i == nx - 1) slr[wq][1] = eywR;
+        asm volatile("bar.sync %0, %1;" :: "r"(1 + w0 / rw), "r"(32 * rw) : "memory");
+        if (jq == rw - 1) {
+          eacc = sey[w0][lane];
+          for (int q = 1; q < rw; ++q) eacc = eacc + sey[w0 + q][lane];
+          if (hy) Wr.cEy[Jc * Wr.cp + Ic] = eacc * Wr.rinv;
+          if (own && i == 1 && b.mode[SIDE_LEFT] == BC_MUR) {
+            eaccL = slr[w0][0];
+            for (int q = 1; q < rw; ++q) eaccL = eaccL + slr[w0 + q][0];
+            Wr.cEy[Jc * Wr.cp + Wr.I0] = eaccL * Wr.rinv;
+          }
+          if (own && i == nx - 1 && b.mode[SIDE_RIGHT] == BC_MUR) {
+            eaccR = slr[w0][1];
+            for (int q = 1; q < rw; ++q) eaccR = eaccR + slr[w0 + q][1];
+            Wr.cEy[Jc * Wr.cp + Wr.I1] = eaccR * Wr.rinv;
+          }
+        }
+      } else if (j < ny) {
         eacc = jq == 0 ? eyw : eacc + eyw;
         eaccL = jq == 0 ? eywL : eaccL + eywL;
         eaccR = jq == 0 ? eywR : eaccR + eywR;
