@@ -150,17 +150,27 @@ def em_launch_bytes(cfg, rect, es):
     return 11 * es * nodes
 
 
+def kernel_source_sha():
+    """SHA-256 of the kernel source with // comments and blank lines removed
+    (a comment edit is not a kernel change)."""
+    import hashlib
+    import re
+    root = os.path.dirname(os.path.abspath(__file__))
+    text = open(os.path.join(root, "paper_2105_13276_gb300", "csrc", "dmr_kernels.cuh")).read()
+    lines = [re.sub(r"//.*", "", ln).rstrip() for ln in text.splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln).encode()).hexdigest()
+
+
 def recorded_traffic(kernel):
     """DRAM bytes per launch from the committed ncu counters of this kernel,
     or None when the kernel source changed since that capture."""
-    import hashlib
     root = os.path.dirname(os.path.abspath(__file__))
     try:
         rec = json.load(open(os.path.join(root, "profiles", "ncu_counters.json")))[kernel]
-        src = open(os.path.join(root, "paper_2105_13276_gb300", "csrc", "dmr_kernels.cuh"), "rb").read()
+        sha = kernel_source_sha()
     except (OSError, ValueError, KeyError):
         return None
-    if hashlib.sha256(src).hexdigest() != rec.get("kernels_sha256"):
+    if sha != rec.get("kernels_sha256"):
         return None
     return rec.get("dram_bytes_per_launch")
 

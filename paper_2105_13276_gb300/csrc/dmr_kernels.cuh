@@ -199,6 +199,15 @@ __device__ __forceinline__ T cfb_blend(const Bnd<T>& b, T lo, T xp, T n0, T n1) 
   return (one - b.frac) * lo + b.frac * ln;
 }
 
+// Programmatic dependent launch: an EM kernel lets the next EM launch of the
+// stream be scheduled as soon as all its blocks have started, and waits for
+// the previous one to complete (and its writes to be visible) before it
+// touches memory.  Launched without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // One EM step on one mesh, fused (a1-a6 + a5 of the level being left):
 //   Hz^{n+1/2} from E^n (Eq. 2); S2 += |E^n_total|^2 at the nodes when c.accum;
 //   v^{n+1/2} (Eq. 3); E^{n+1} on interior edges (Eq. 1); Mur on domain sides;
@@ -212,18 +221,11 @@ __device__ __forceinline__ T cfb_blend(const Bnd<T>& b, T lo, T xp, T n0, T n1) 
 // columns that only load and (lane 0) compute H for their neighbour.
 // The warp marches up `rows` node rows, carrying the previous row's E^n, new
 // H, density and Ey^n in registers; every x-neighbour comes by shuffle, so
-// there is no shared memory and no block barrier.  A Mur side's boundary edge
+// there is no shared memory and no block barrier (except in the last fine
+// sub-step at one row per warp, whose warps sum the coarse Ey means in groups
+// through shared memory).  A Mur side's boundary edge
 // is advanced by the owner of the adjacent interior edge, which holds both E
 // levels.  Each element is read once and written once: 60 B per cell (FP32).
-// Programmatic dependent launch: an EM kernel lets the next EM launch of the
-// stream be scheduled as soon as all its blocks have started, and waits for
-// the previous one to complete (and its writes to be visible) before it
-// touches memory.  Launched without the attribute both are no-ops.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
 constexpr int STRIP_W = 30;
 constexpr int EM_WARPS = 4;   // warps per block (consecutive strips in y)
 // resident EM blocks per SM the register allocation must allow: a 512^2
