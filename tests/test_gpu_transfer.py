@@ -28,14 +28,15 @@ def _built():
     D.load()
 
 
-def fine_mean(run, r, dtype):
-    """Expected coarse Ex, Ey on the transfer set from the fine arrays."""
+def fine_mean(run, r, dtype, nx=NX, ny=NY):
+    """Expected coarse Ex, Ey on the transfer set from the fine arrays (coarse
+    mesh nx x ny cells)."""
     I0, J0, I1, J1 = run.get_patch()
     fex, fey = run.read("Ex", 1), run.read("Ey", 1)          # [row, column]
     jlo = J0 if J0 == 0 else J0 + 1
-    jhi = J1 if J1 == NY else J1 - 1
+    jhi = J1 if J1 == ny else J1 - 1
     ilo = I0 if I0 == 0 else I0 + 1
-    ihi = I1 if I1 == NX else I1 - 1
+    ihi = I1 if I1 == nx else I1 - 1
     rinv = dtype(1.0 / r)
     ex = {}
     for J in range(jlo, jhi + 1):
@@ -90,3 +91,27 @@ def test_dmr_r3_r4_match_oracle(r, rect):
             o = getattr(mesh, name)
             rel = np.linalg.norm(g - o) / max(np.linalg.norm(o), 1e-300)
             assert rel < 1e-12, (level, name, rel)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("r", [2, 4])
+@pytest.mark.parametrize("wps", [1, 1024])
+def test_coarse_holds_fine_mean_many_rows(precision, r, wps):
+    """A larger rectangle: at a low warps-per-SM target the last sub-step's
+    warps cover several rows (Ey summed in the warp), at a high one a single
+    row (Ey summed across the warps of a block)."""
+    nx, ny = 120, 96
+    w = W.small_dmr(nx=nx, ny=ny, r=r, rect=(20, 16, 100, 80), precision=precision)
+    w["seeds"] = [(3e17, 0.5, 0.5, 0.1, 0.1)]
+    run = D.run_from_workload(w)
+    run.set_graphs(True)
+    run.set_launch_shape(wps)
+    dtype = np.float32 if precision == 1 else np.float64
+    for steps in (5, 38):
+        run.advance(steps)
+        (I0, J0, I1, J1), ex, ey = fine_mean(run, r, dtype, nx, ny)
+        cex, cey = run.read("Ex", 0), run.read("Ey", 0)
+        for J, v in ex.items():
+            assert np.array_equal(cex[J, I0:I1], v), ("Ex", J)
+        for I, v in ey.items():
+            assert np.array_equal(cey[J0:J1, I], v), ("Ey", I)
