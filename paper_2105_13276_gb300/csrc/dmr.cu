@@ -739,10 +739,12 @@ struct Engine final : Base {
   bool last_em = false;
   bool pdl_next() const { return last_em && !timing; }
 
-  // one coarse step from level mlev.  The coarse step (reading the restricted
-  // E of the previous step on the fly) and the first fine sub-step (which
-  // evaluates the coarse E^{n+1} on its boundary lines itself) are
-  // independent and share one launch; fine sub-steps 2..r follow.
+  // one coarse step from level mlev.  The coarse step (reading the coarse E,
+  // which under the rectangle holds the fine mean the previous step's last
+  // sub-step wrote) and the first fine sub-step (which evaluates the coarse
+  // E^{n+1} on its boundary lines itself) are independent and share one
+  // launch; fine sub-steps 2..r follow, the last writing the new fine mean
+  // into the coarse E^{n+1}.
   int launch_coarse_step(int64_t mlev) {
     const int NT = cfg.steps_per_period, r = cfg.r;
     const bool acc_c = (mlev % NT) != 0;
