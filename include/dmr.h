@@ -295,7 +295,7 @@ int dmr_batch_advance(dmr_batch* b, int64_t n_coarse_steps);
 int dmr_batch_set_graphs(dmr_batch* b, int enable);
 
 /* Autotuner (at a period boundary): times the batched EM launch for five
- * strip heights (warps-per-SM targets 8, 16, 32, 48, 96) on the present
+ * strip heights (warps-per-SM targets 1, 2, 4, 8, 16) on the present
  * state without changing it (5 copies per CUDA graph replay), keeps the
  * fastest; returns the choice and the per-candidate mean launch times (ms). */
 int dmr_batch_autotune(dmr_batch* b, int32_t* warps_per_sm, double trial_ms[5]);

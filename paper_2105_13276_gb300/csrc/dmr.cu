@@ -2046,7 +2046,7 @@ struct Batch final : BatchBase {
   int autotune() override {
     if (int s = check_state()) return s;
     if (m % NT != 0) return fail(DMR_ESTATE, "autotune at a period boundary");
-    const int cand[5] = {8, 16, 32, 48, 96};
+    const int cand[5] = {1, 2, 4, 8, 16};   // batches favour long strips (fewer blocks to stage)
     double best = 1e30;
     int best_w = 48;
     for (int c = 0; c < 5; ++c) {

@@ -25,7 +25,8 @@ FIELDS = {"Ex": 0, "Ey": 1, "Hz": 2, "vx": 3, "vy": 4, "n": 5, "S2": 6, "mask": 
 STATS = ["t", "R", "fine_cells", "N_e", "P_abs", "W_abs", "periods", "coarse_steps", "n_max",
          "flags"]
 # strip heights the autotuners try, as warps-per-SM targets (trial_ms order)
-TUNE_WPS = (8, 16, 32, 48, 96)
+TUNE_WPS = (8, 16, 32, 48, 96)          # dmr_autotune candidates (warps per SM)
+TUNE_WPS_BATCH = (1, 2, 4, 8, 16)       # dmr_batch_autotune candidates
 
 C0 = 299792458.0
 

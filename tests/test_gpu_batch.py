@@ -114,7 +114,7 @@ def test_autotune_keeps_state_and_results():
     a.advance(32)
     b.advance(32)
     wps, ms = b.autotune()
-    assert wps in D.TUNE_WPS and len(ms) == len(D.TUNE_WPS) and all(t > 0 for t in ms)
+    assert wps in D.TUNE_WPS_BATCH and len(ms) == len(D.TUNE_WPS_BATCH) and all(t > 0 for t in ms)
     a.advance(2 * 32 + 5)
     b.advance(2 * 32 + 5)
     for q in range(len(ws)):
