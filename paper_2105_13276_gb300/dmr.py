@@ -8,7 +8,6 @@ fallback.
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_int32, c_int64, c_size_t, c_void_p
 

@@ -14,7 +14,6 @@ executed every other test before it.
 """
 import ctypes
 
-import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
