@@ -2,8 +2,9 @@
 every coarse step writes into the coarse arrays: after any step the coarse E
 edges of the transfer set hold the mean of their r collinear fine edges, bit
 for bit (the same sum, q = 0 .. r-1, times 1/r, in the run's precision), for
-every refinement factor and for rectangle sides inside the domain and on its
-edges (Mur); and runs with r = 3 and r = 4 match the FP64 oracle."""
+every refinement factor (strip widths 30, 28 and 24, one or several rows per
+warp) and for rectangle sides inside the domain and on its edges (Mur); and
+runs with r = 3, 4 and 8 match the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -56,7 +57,7 @@ def fine_mean(run, r, dtype, nx=NX, ny=NY):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("r", [2, 3, 4])
+@pytest.mark.parametrize("r", [2, 3, 4, 5, 8])
 @pytest.mark.parametrize("rect", [(12, 10, 24, 20), (0, 0, 14, 12), (26, 20, 40, 32)])
 def test_coarse_holds_fine_mean(precision, r, rect):
     w = W.small_dmr(nx=NX, ny=NY, r=r, rect=rect, precision=precision)
@@ -74,9 +75,9 @@ def test_coarse_holds_fine_mean(precision, r, rect):
     assert run.get_patch() != tuple(rect)      # grew on the way
 
 
-@pytest.mark.parametrize("r", [3, 4])
+@pytest.mark.parametrize("r", [3, 4, 8])
 @pytest.mark.parametrize("rect", [(12, 10, 24, 20), (0, 0, 14, 12)])
-def test_dmr_r3_r4_match_oracle(r, rect):
+def test_dmr_r3_r4_r8_match_oracle(r, rect):
     w = W.small_dmr(nx=NX, ny=NY, r=r, rect=rect)
     run = D.run_from_workload(w)
     run.set_graphs(True)
