@@ -1266,10 +1266,32 @@ struct Engine final : Base {
     tape_used += up(bytes, 256);
     return d;
   }
+  // Tape copies are queued and issued together by flush_tape() (one gather
+  // launch instead of a copy call each).  The recording issues the flush
+  // before any launch that overwrites a queued source.
+  dmr::TapeJobs tjobs{};
+  size_t tjob_max16 = 0;
   const T* tape_copy(const void* src, size_t bytes) {
     T* d = reinterpret_cast<T*>(tape_slot(bytes));
-    if (d) cudaMemcpyAsync(d, src, bytes, cudaMemcpyDeviceToDevice, st);
+    if (!d) return d;
+    if (bytes % 16 != 0 || ((uintptr_t)src % 16) != 0) {
+      cudaMemcpyAsync(d, src, bytes, cudaMemcpyDeviceToDevice, st);
+      return d;
+    }
+    if (tjobs.n == dmr::kTapeJobs) flush_tape();
+    tjobs.src[tjobs.n] = reinterpret_cast<const int4*>(src);
+    tjobs.dst[tjobs.n] = reinterpret_cast<int4*>(d);
+    tjobs.n16[tjobs.n] = (long long)(bytes / 16);
+    tjob_max16 = std::max(tjob_max16, bytes / 16);
+    ++tjobs.n;
     return d;
+  }
+  void flush_tape() {
+    if (tjobs.n == 0) return;
+    const int gx = (int)std::min<size_t>(256, (tjob_max16 + 255) / 256);
+    dmr::ka_tape_gather<<<dim3(std::max(gx, 1), tjobs.n), 256, 0, st>>>(tjobs);
+    tjobs.n = 0;
+    tjob_max16 = 0;
   }
   double* tape_alloc_d(size_t bytes) { return reinterpret_cast<double*>(tape_slot(bytes)); }
 
@@ -1300,6 +1322,8 @@ struct Engine final : Base {
     flip_coarse();
     R->cvx = tape_copy(C.vx, cplane_b());
     R->cvy = tape_copy(C.vy, cplane_b());
+    // queued copies: coarse E^n and v^{n+1/2} stay in place until the next
+    // coarse step; the fine input of sub-step k until sub-step k+1
     if (has_fine) {
       const size_t fb = fplane_b(rect);
       for (int k = 1; k <= r; ++k) {
@@ -1311,8 +1335,11 @@ struct Engine final : Base {
         flip_fine();
         R->fvx.push_back(tape_copy(F[cur].vx, fb));
         R->fvy.push_back(tape_copy(F[cur].vy, fb));
+        flush_tape();
       }
       rvalid = true;
+    } else {
+      flush_tape();
     }
     ++m;
     (void)NT;
@@ -1343,6 +1370,7 @@ struct Engine final : Base {
             F[cur], make_step(cfg.r, (int64_t)cfg.r * m, true), s2f);
       P->S2f = s2f;
     }
+    flush_tape();   // before the period end rewrites n
     if (int s = launch_period_end(m)) return s;
     if (int s = period_end_host()) return s;
     P->expanded = has_fine && (rect[0] != P->rect_b[0] || rect[1] != P->rect_b[1] ||

@@ -19,6 +19,25 @@
 
 namespace dmr {
 
+// Tape copies of a recorded step in one launch: job q copies n16[q] 16-byte
+// words from src[q] to dst[q] (blockIdx.y = job, grid-stride along x).
+constexpr int kTapeJobs = 16;
+struct TapeJobs {
+  const int4* src[kTapeJobs];
+  int4* dst[kTapeJobs];
+  long long n16[kTapeJobs];
+  int n;
+};
+
+__global__ void ka_tape_gather(TapeJobs J) {
+  const int q = blockIdx.y;
+  if (q >= J.n) return;
+  const int4* __restrict__ s = J.src[q];
+  int4* __restrict__ d = J.dst[q];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < J.n16[q]; k += stride) d[k] = s[k];
+}
+
 template <class T>
 struct AdjM {
   const T *aEx_in, *aEy_in;   // adjoint of E^{l+1}
