@@ -385,3 +385,24 @@ def test_autotune_leaves_run_unchanged(precision):
     for level in (0, 1):
         for name in FIELDS + ("S2",):
             assert np.array_equal(a.read(name, level), b.read(name, level)), (level, name)
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_launch_modes_mixed_in_one_run(graphs):
+    """Per-kernel timing switches the programmatic dependent launches off;
+    switching it on and off between steps, mid-period and across periods,
+    and reading state in between, gives the bits of an undisturbed run."""
+    w = W.small_dmr(precision=1)
+    ref = D.run_from_workload(w)
+    run = D.run_from_workload(w)
+    ref.set_graphs(graphs)
+    run.set_graphs(graphs)
+    for q, steps in enumerate((5, 27, 40, 32, 9)):
+        run.set_timing(q % 2 == 0)
+        run.advance(steps)
+        ref.advance(steps)
+        run.read("Ex", 0)
+    assert run.get_patch() == ref.get_patch()
+    for level in (0, 1):
+        for name in FIELDS + ("S2",):
+            assert np.array_equal(run.read(name, level), ref.read(name, level)), (level, name)
