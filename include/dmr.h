@@ -202,8 +202,10 @@ int dmr_set_graphs(dmr_ctx* ctx, int enable);
  * launch.  enable is a bit mask of the kernel classes to time (bit k for
  * class k; -1 for all; 0 switches timing off); each call resets the sums.
  * Classes: 0 EM step (the coarse step together with the first fine
- * sub-step), 1 later fine sub-steps, 2 fine->coarse E transfer written to
- * the coarse arrays, 3 period-end kernels, 4 growth.
+ * sub-step), 1 later fine sub-steps (the last also writes the fine->coarse E
+ * transfer into the coarse arrays), 2 kept for compatibility (no launches),
+ * 3 period-end kernels, 4 growth.  While timing is on, EM launches do not
+ * overlap (no programmatic dependent launch).
  * dmr_kernel_time returns, for a class, the summed device time in ms, the
  * number of timed launches and the algorithmic bytes those launches had to
  * move (each array element read and written once; 0 for classes 3 and 4);
