@@ -420,8 +420,9 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
   };
   Row nxt = load_row(j0);
   // a8 on the producer side: the column tests are fixed per lane; the row
-  // phase jq = j mod r and the coarse row Jc = J0 + j / r advance with j
-  // (j0 is a multiple of r), so the loop divides by nothing
+  // phase jq = j mod r and the coarse row Jc = J0 + j / r are set once and
+  // advance with j, so the loop divides by nothing.  An Ex group's r columns
+  // are consecutive lanes of one strip (strip width a multiple of r).
   const int rw = WR ? A.W.r : 1;
   const bool hx = WR && own && i < nx && (i % rw) == 0;                  // head of an Ex group
   const int Ic = WR ? A.W.I0 + (i > 0 ? i / rw : 0) : 0;
@@ -569,7 +570,8 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
       }
       if (j < ny && cross) {
         // the group's rows are all below ny (ny and the group start are
-        // multiples of r), so all r warps of the group arrive here
+        // multiples of r), so all r warps of the group arrive here; named
+        // barrier 1 + group index (barrier 0 is __syncthreads'), 32 r threads
         __shared__ T sey[EM_WARPS][32], slr[EM_WARPS][2];
         const int wq = threadIdx.x >> 5, w0 = wq - jq;
         sey[wq][lane] = eyw;
