@@ -26,11 +26,11 @@
  *   - Units are SI; positions are metres from the lower-left domain corner.
  *   - Arrays read or written through the ABI are dense, row-major with y as
  *     the row index and x contiguous:
- *       Ex, vx : (ny+1) rows x nx       at ((i+1/2)d, j d)
- *       Ey, vy : ny rows x (nx+1)       at (i d, (j+1/2)d)
- *       Hz     : ny rows x nx           at ((i+1/2)d, (j+1/2)d)
- *       NE, S2 : (ny+1) rows x (nx+1)   at nodes (i d, j d)
- *       MASK   : (ny+1) rows x (nx+1)   uint8 flags on the coarse nodes
+ *       Ex, vx       : (ny+1) rows x nx       at ((i+1/2)d, j d)
+ *       Ey, vy       : ny rows x (nx+1)       at (i d, (j+1/2)d)
+ *       Hz           : ny rows x nx           at ((i+1/2)d, (j+1/2)d)
+ *       NE, S2, ERMS : (ny+1) rows x (nx+1)   at nodes (i d, j d)
+ *       MASK         : (ny+1) rows x (nx+1)   uint8 flags on the coarse nodes
  *     with (nx, ny) the cell counts of the mesh read (coarse, or the current
  *     fine rectangle).  Elements are double for precision 0 and float for
  *     precision 1, except S2 (always double) and MASK (uint8).
@@ -57,9 +57,17 @@ typedef enum {
   DMR_ESTATE = -6      /* call not valid in the current state */
 } dmr_status;
 
+/* DMR_FIELD_ERMS is the output E_rms(x, y, t) of Sec. II.B / IV at the nodes
+ * (read only): within a period the RMS of the total field over the samples
+ * taken since the period began (levels after its first, through the present
+ * E level), E_rms^2 = S2 / q for q samples; at a period boundary the E_rms of
+ * the period just completed, E_rms^2 = S2 / N over its N samples (the value
+ * E_eff was taken from), with area the rectangle gained at that boundary
+ * filled from the coarse mesh by Eq. 5a. */
 typedef enum {
   DMR_FIELD_EX = 0, DMR_FIELD_EY = 1, DMR_FIELD_HZ = 2, DMR_FIELD_VX = 3,
-  DMR_FIELD_VY = 4, DMR_FIELD_NE = 5, DMR_FIELD_S2 = 6, DMR_FIELD_MASK = 7
+  DMR_FIELD_VY = 4, DMR_FIELD_NE = 5, DMR_FIELD_S2 = 6, DMR_FIELD_MASK = 7,
+  DMR_FIELD_ERMS = 8
 } dmr_field;
 
 typedef enum {
@@ -241,6 +249,27 @@ int dmr_autotune(dmr_ctx* ctx, int32_t* warps_per_sm, double trial_ms[5]);
  * same size).  Results do not depend on it.  DMR_EINVAL otherwise. */
 int dmr_set_launch_shape(dmr_ctx* ctx, int32_t warps_per_sm);
 
+/* ---- Checkpoint / resume of a run ----
+ * The state of a run is everything its later steps depend on: the whole
+ * workspace (fields, densities, E^2 sums, E_rms, CPML memory, totals and
+ * control block) and the host-side step counter, buffer parities and fine
+ * rectangle (the rectangle-growth policy of Sec. III.D and the stepping of
+ * Sec. III.C continue from it exactly).  dmr_state_bytes gives the size of a
+ * saved state: a 512-byte header followed by an image of the workspace.
+ * dmr_save_state copies the present state (after the work already queued on
+ * the stream) into dev_dst, a caller-owned device buffer (256-byte aligned),
+ * and returns when the copy is done.  dmr_load_state makes the run continue
+ * from a state saved by a run of the same configuration (the same context,
+ * or another one created with an equal dmr_config); a saved state can be
+ * loaded any number of times.  Loading keeps the run's own replay log,
+ * resumes it where it stood at the save, drops captured graphs and any
+ * adjoint recording.  Neither call is valid for a run of a batch
+ * (DMR_ESTATE).  Errors: DMR_EINVAL (null or misaligned buffer, not a saved
+ * state, other configuration), DMR_ECAPACITY (buffer too small), DMR_ECUDA. */
+size_t dmr_state_bytes(const dmr_ctx* ctx);
+int dmr_save_state(dmr_ctx* ctx, void* dev_dst, size_t bytes);
+int dmr_load_state(dmr_ctx* ctx, const void* dev_src, size_t bytes);
+
 /* ---- Adjoint (reverse mode) with the refinement schedule held fixed ----
  * Gradients of a loss L(n_coarse(t_end)) with respect to the incident
  * amplitude E0, the ionization scale s_nu and the initial density map of the
@@ -318,9 +347,11 @@ const char* dmr_batch_last_error(const dmr_batch* b);
  * (device memory).  Work is queued on cuda_stream (NULL = legacy default).
  * Its scratch is a fixed array inside the library (16384 doubles, 128 KiB,
  * held on every GPU that loads the library until the process exits), so maps
- * above 67108864 nodes are rejected with DMR_ECAPACITY.  The first call on a
- * device looks the array's device address up (cudaGetSymbolAddress); make
- * that first call before any stream capture.  Every call shares the array:
+ * above 67108864 nodes are rejected with DMR_ECAPACITY.  The first call in
+ * each CUDA context (per device, and again after a device reset, which makes
+ * a new context) looks the array's device address up with that device
+ * current (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call shares the array:
  * calls that overlap on the GPU (other streams, other threads) race; calls
  * on one stream are ordered and each rewrites the scratch it reads.  Errors:
  * DMR_EINVAL, DMR_ECAPACITY, DMR_ECUDA; dmr_noalloc_last_error() explains. */

@@ -154,6 +154,9 @@ class Mesh:
         self.Hz = z(nx, ny)
         self.n = z(nx + 1, ny + 1)
         self.S2 = z(nx + 1, ny + 1)
+        # E_rms of the last completed period at the nodes (Sec. II.B output
+        # E_rms(x, y, t)), kept when the period end resets S2
+        self.erms_last = np.zeros((nx + 1, ny + 1))
         self.m = 0                           # time level of E (steps done)
 
     def node_x(self):
@@ -680,6 +683,11 @@ class Sim:
         c, f = self.coarse, self.fine
         wc, wf = self._weights()
         heat = QE * QE / (ME * P.nu_m)
+        # E_rms of the completed period, E_rms^2 = S2 / N (the mean over the
+        # period's N samples, the same quantity E_eff is taken from)
+        c.erms_last = np.sqrt(c.S2 / c.N)
+        if f is not None:
+            f.erms_last = np.sqrt(f.S2 / f.N)
         # coarse continuity step
         eeff_c, nu_c, D_c = density_rates(P, c, c.n)
         p_abs = c.dx * c.dx * np.sum(wc * c.n * heat * eeff_c * eeff_c)
@@ -760,7 +768,8 @@ class Sim:
         f.vy[...] = bilinear(c.vy, ax_node, by_half - 0.5)
         f.Hz[...] = bilinear(c.Hz, ax_half - 0.5, by_half - 0.5)
         f.n[...] = bilinear(c.n, ax_node, by_node)
-        for name in ("Ex", "vx", "Ey", "vy", "Hz", "n"):
+        f.erms_last = bilinear(c.erms_last, ax_node, by_node)
+        for name in ("Ex", "vx", "Ey", "vy", "Hz", "n", "erms_last"):
             src = getattr(old, name)
             getattr(f, name)[oi:oi + src.shape[0], oj:oj + src.shape[1]] = src
         f.m = old.m
@@ -776,10 +785,20 @@ class Sim:
                 "coarse_steps": c.m}
 
     def erms(self, level=0):
-        """E_rms at the nodes from the running S2 (valid at a period end only
-        if read before the reset; exposed for inspection)."""
+        """E_rms at the nodes (the output E_rms(x, y, t), Sec. II.B, Sec. IV).
+
+        Reading: within a period, the RMS of the total field over the samples
+        taken since the period began (levels after the period's first, through
+        the present E level: E_rms^2 = S2 / q for q samples); at a period
+        boundary, where S2 has just been reset, the E_rms of the period just
+        completed, E_rms^2 = S2 / N over its N samples.  Area that the
+        rectangle gained at that boundary takes the coarse values by the
+        bilinear fill of Eq. 5a, like every other fine quantity."""
         mesh = self.coarse if level == 0 else self.fine
-        return np.sqrt(mesh.S2 / mesh.N)
+        q = mesh.m % mesh.N
+        if q == 0:
+            return mesh.erms_last.copy()
+        return np.sqrt(mesh.S2 / q)
 
 
 def default_patch(nx, ny, ic, jc, m):

@@ -157,6 +157,7 @@ struct Layout {
   size_t off_c[14] = {}, off_cS2 = 0;     // Ex Ey Hz vx vy n ntmp D nu, then Ex' Ey' Hz' vx' vy'
   size_t off_f[2][11] = {}, off_fS2[2] = {};  // Ex Ey Hz vx vy n, then Ex' Ey' Hz' vx' vy'
   size_t off_ftmp[3] = {};                // ntmp D nu
+  size_t off_cErms = 0, off_fErms[2] = {};  // E_rms of the last completed period (nodes)
   size_t off_tab[4] = {};                 // ckx_c skx_c ckx_f skx_f
   size_t off_ph[4] = {};                  // sin/cos of the phase per step: coarse, fine
   size_t off_mask = 0, off_part[4] = {}, off_ctl = 0, off_view = 0;
@@ -188,10 +189,12 @@ int make_layout(const dmr_config* c, const Derived& d, Layout* L, std::string* e
   auto take = [&](size_t bytes) { size_t at = o; o = up(o + bytes, 256); return at; };
   for (int q = 0; q < 14; ++q) L->off_c[q] = take(L->cplane * L->es);
   L->off_cS2 = take(L->cplane * 8);
+  L->off_cErms = take(L->cplane * L->es);
   if (r > 1) {
     for (int s = 0; s < 2; ++s) {
       for (int q = 0; q < 11; ++q) L->off_f[s][q] = take(L->fplane * L->es);
       L->off_fS2[s] = take(L->fplane * 8);
+      L->off_fErms[s] = take(L->fplane * L->es);
     }
     for (int q = 0; q < 3; ++q) L->off_ftmp[q] = take(L->fplane * L->es);
   }
@@ -344,7 +347,41 @@ struct Base {
   virtual size_t adj_bytes() const = 0;
   virtual int adj_backward(const void* dLdn, void* ws, size_t bytes, void* ckpt, size_t cbytes,
                            double* dE0, double* dnu, void* dseed) = 0;
+  virtual size_t state_bytes() const = 0;
+  virtual int save_state(void* dst, size_t bytes) = 0;
+  virtual int load_state(const void* src, size_t bytes) = 0;
 };
+
+// Header of a saved run state (dmr_save_state): the host-side step counter,
+// buffer parities and rectangle, position-independent, followed in the
+// caller's buffer by an image of the whole workspace.
+struct StateHdr {
+  char magic[8];
+  uint32_t version, es;
+  uint64_t total;
+  int64_t m;
+  int32_t cpar, fpar, cur, has_fine, rvalid;
+  int32_t rect[4];
+  int64_t replay_pos;   // periods of a replayed refinement log consumed
+  dmr_config cfg;
+};
+constexpr size_t kStateHdrBytes = 512;
+static_assert(sizeof(StateHdr) <= kStateHdrBytes, "state header too large");
+constexpr char kStateMagic[8] = {'D', 'M', 'R', 'S', 'T', 'A', 'T', 'E'};
+
+// Configurations describe the same run (field by field: padding bytes of the
+// struct are not compared).
+bool same_config(const dmr_config& a, const dmr_config& b) {
+  return a.nx == b.nx && a.ny == b.ny && a.r == b.r && a.n_lambda == b.n_lambda &&
+         a.steps_per_period == b.steps_per_period && a.precision == b.precision &&
+         a.buffer_cells == b.buffer_cells && a.growth == b.growth &&
+         a.patch_cap_cells == b.patch_cap_cells && a.freq == b.freq && a.E0 == b.E0 &&
+         a.p_torr == b.p_torr && a.De == b.De && a.Da == b.Da && a.beta_rec == b.beta_rec &&
+         a.Te == b.Te && a.nu_scale == b.nu_scale && a.nu_a == b.nu_a && a.n_th == b.n_th &&
+         a.g_th == b.g_th && a.m_ex == b.m_ex && a.m_ey == b.m_ey && a.nu_model == b.nu_model &&
+         a.town_A == b.town_A && a.town_B == b.town_B && a.boundary == b.boundary &&
+         a.pml_cells == b.pml_cells;
+}
 
 template <class T>
 struct Engine final : Base {
@@ -358,6 +395,8 @@ struct Engine final : Base {
   T* fptr[2][6] = {};        // [set][Ex, Ey, Hz, vx, vy, n] (parity 0)
   T* fE1[2][5] = {};         // [set][Ex', Ey', Hz', vx', vy'] (parity 1)
   double* fS2[2] = {};
+  T* cErms = nullptr;
+  T* fErms[2] = {};          // [set]
   int cur = 0, fpar = 0;
   // the fine arrays hold the result of sub-steps for the current rectangle, so
   // the coarse E under it is their mean (false at start and after growth)
@@ -383,11 +422,13 @@ struct Engine final : Base {
     c_ntmp = at<T>(L.off_c[6]); c_D = at<T>(L.off_c[7]); c_nu = at<T>(L.off_c[8]);
     C.S2 = at<double>(L.off_cS2);
     C.nx = cfg.nx; C.ny = cfg.ny; C.p = L.pc;
+    cErms = at<T>(L.off_cErms);
     if (cfg.r > 1) {
       for (int s = 0; s < 2; ++s) {
         for (int q = 0; q < 6; ++q) fptr[s][q] = at<T>(L.off_f[s][q]);
         for (int q = 0; q < 5; ++q) fE1[s][q] = at<T>(L.off_f[s][6 + q]);
         fS2[s] = at<double>(L.off_fS2[s]);
+        fErms[s] = at<T>(L.off_fErms[s]);
       }
       f_ntmp = at<T>(L.off_ftmp[0]); f_D = at<T>(L.off_ftmp[1]); f_nu = at<T>(L.off_ftmp[2]);
     }
@@ -798,7 +839,7 @@ struct Engine final : Base {
     dmr::Dens dc = make_dens(1);
     dmr::Step<T> sc = make_step(1, mlev, true);
     const dim3 gc = nodes_grid(C.nx, C.ny);
-    dmr::k_rates<T><<<gc, blk, 0, st>>>(C, sc, dc, wc, c_D, c_nu, part[0], ctl);
+    dmr::k_rates<T><<<gc, blk, 0, st>>>(C, sc, dc, wc, c_D, c_nu, part[0], ctl, cErms);
     dmr::Mesh<T> f{};
     dmr::Dens df{};
     dmr::Wts wf{};
@@ -812,7 +853,7 @@ struct Engine final : Base {
       gf = nodes_grid(f.nx, f.ny);
       nbf = (int)(gf.x * gf.y);
       dmr::Step<T> sf = make_step(r, (int64_t)r * mlev, true);
-      dmr::k_rates<T><<<gf, blk, 0, st>>>(f, sf, df, wf, f_D, f_nu, part[1], nullptr);
+      dmr::k_rates<T><<<gf, blk, 0, st>>>(f, sf, df, wf, f_D, f_nu, part[1], nullptr, fErms[cur]);
       ++n_launch;
     }
     dmr::Dir<T> none{};
@@ -929,7 +970,7 @@ struct Engine final : Base {
     const int oI0 = has_fine ? rect[0] : nr[0], oJ0 = has_fine ? rect[1] : nr[1];
     int h = tbeg(4, 0.0);
     dmr::k_expand<T><<<nodes_grid(nf.nx, nf.ny), dim3(BX, BY), 0, st>>>(
-        nf, of, C, nr[0], nr[1], oI0, oJ0, has_fine ? 1 : 0, cfg.r);
+        nf, of, C, nr[0], nr[1], oI0, oJ0, has_fine ? 1 : 0, cfg.r, fErms[nxt], fErms[cur], cErms);
     tend(h);
     counted(1);
     if (int s = launched("expand")) return s;
@@ -1045,7 +1086,7 @@ struct Engine final : Base {
       case DMR_FIELD_EX: case DMR_FIELD_VX: *rows = ny + 1; *cols = nx; break;
       case DMR_FIELD_EY: case DMR_FIELD_VY: *rows = ny; *cols = nx + 1; break;
       case DMR_FIELD_HZ: *rows = ny; *cols = nx; break;
-      case DMR_FIELD_NE: *rows = ny + 1; *cols = nx + 1; break;
+      case DMR_FIELD_NE: case DMR_FIELD_ERMS: *rows = ny + 1; *cols = nx + 1; break;
       case DMR_FIELD_S2: *rows = ny + 1; *cols = nx + 1; *es = 8; break;
       case DMR_FIELD_MASK:
         if (level != 0 || cfg.r == 1) return DMR_ESTATE;
@@ -1074,6 +1115,7 @@ struct Engine final : Base {
       case DMR_FIELD_VY: return mm.vy;
       case DMR_FIELD_NE: return mm.n;
       case DMR_FIELD_S2: return mm.S2;
+      case DMR_FIELD_ERMS: return level == 0 ? cErms : fErms[cur];
       default: return mask;
     }
   }
@@ -1096,6 +1138,20 @@ struct Engine final : Base {
       if (int e = launched("S2 view")) return e;
       src = view;
     }
+    if (field == DMR_FIELD_ERMS && m % cfg.steps_per_period != 0) {
+      // within a period: the RMS over the samples taken so far (the stored
+      // array holds the last completed period's E_rms)
+      const int rr = level == 0 ? 1 : cfg.r;
+      const int64_t lev = level == 0 ? m : (int64_t)cfg.r * m;
+      const int64_t q = lev % ((int64_t)rr * cfg.steps_per_period);
+      dmr::Step<T> s = make_step(rr, lev, true);
+      const dmr::Mesh<T>& mm = level == 0 ? C : F[cur];
+      dmr::k_erms_view<T><<<nodes_grid(mm.nx, mm.ny), dim3(BX, BY), 0, st>>>(
+          mm, s, (double)q, reinterpret_cast<T*>(view));
+      counted(1);
+      if (int e = launched("E_rms view")) return e;
+      src = view;
+    }
     const size_t wb = (size_t)cols * es;
     cudaError_t e = cudaMemcpy2DAsync(dst, wb, src, (size_t)p * es, wb, rows,
                                       dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
@@ -1105,7 +1161,8 @@ struct Engine final : Base {
   }
 
   int write(int field, int level, const void* src, size_t bytes, int dev) override {
-    if (field == DMR_FIELD_MASK) return fail(DMR_EINVAL, "the mask is not writable");
+    if (field == DMR_FIELD_MASK || field == DMR_FIELD_ERMS)
+      return fail(DMR_EINVAL, "the mask and E_rms are derived quantities, not writable");
     int rows, cols, es;
     if (int s = dims(field, level, &rows, &cols, &es)) return fail(s, "no such field / level");
     if (bytes < (size_t)rows * cols * es) return fail(DMR_ECAPACITY, "source too small");
@@ -1742,6 +1799,75 @@ struct Engine final : Base {
     drop_graph();
     if (wps_out) *wps_out = best_w;
     return launched("autotune");
+  }
+
+  // ---- checkpoint / resume of the whole run state (caller-owned buffer)
+  size_t state_bytes() const override { return kStateHdrBytes + up(L.total, 256); }
+
+  int save_state(void* dst, size_t bytes) override {
+    if (in_batch) return fail(DMR_ESTATE, "runs of a batch are not saved one by one");
+    if (!dst || ((uintptr_t)dst & 255u)) return fail(DMR_EINVAL, "state buffer must be a 256-byte aligned device pointer");
+    if (bytes < state_bytes()) return fail(DMR_ECAPACITY, fmt("state buffer too small: %zu < %zu bytes", bytes, state_bytes()));
+    StateHdr h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, kStateMagic, sizeof h.magic);
+    h.version = 1;
+    h.es = (uint32_t)L.es;
+    h.total = L.total;
+    h.m = m;
+    h.cpar = cpar; h.fpar = fpar; h.cur = cur;
+    h.has_fine = has_fine ? 1 : 0;
+    h.rvalid = rvalid ? 1 : 0;
+    for (int q = 0; q < 4; ++q) h.rect[q] = rect[q];
+    h.replay_pos = (int64_t)replay_pos;
+    h.cfg = cfg;
+    char* d = static_cast<char*>(dst);
+    last_em = false;
+    if (int s_ = ck(cudaMemcpyAsync(d + kStateHdrBytes, ws, L.total, cudaMemcpyDeviceToDevice, st), "save state"))
+      return s_;
+    if (int s_ = ck(cudaMemcpyAsync(d, &h, sizeof h, cudaMemcpyHostToDevice, st), "save state header"))
+      return s_;
+    return ck(cudaStreamSynchronize(st), "save state sync");
+  }
+
+  int load_state(const void* src, size_t bytes) override {
+    if (in_batch) return fail(DMR_ESTATE, "runs of a batch are not loaded one by one");
+    if (!src || ((uintptr_t)src & 255u)) return fail(DMR_EINVAL, "state buffer must be a 256-byte aligned device pointer");
+    if (bytes < kStateHdrBytes) return fail(DMR_ECAPACITY, "state buffer too small");
+    StateHdr h;
+    const char* sp = static_cast<const char*>(src);
+    if (int s_ = ck(cudaMemcpyAsync(&h, sp, sizeof h, cudaMemcpyDeviceToHost, st), "load state header")) return s_;
+    if (int s_ = ck(cudaStreamSynchronize(st), "load state sync")) return s_;
+    if (memcmp(h.magic, kStateMagic, sizeof h.magic) != 0 || h.version != 1)
+      return fail(DMR_EINVAL, "not a saved DMR state");
+    if (h.es != L.es || h.total != L.total || !same_config(h.cfg, cfg))
+      return fail(DMR_EINVAL, "the state was saved by a run of another configuration");
+    if (bytes < state_bytes()) return fail(DMR_ECAPACITY, "state buffer too small");
+    if (h.m < 0 || (h.cpar | h.fpar | h.cur) & ~1 || (cfg.r == 1 && h.has_fine))
+      return fail(DMR_EINVAL, "corrupt state header");
+    if (int s_ = ck(cudaMemcpyAsync(ws, sp + kStateHdrBytes, L.total, cudaMemcpyDeviceToDevice, st), "load state"))
+      return s_;
+    drop_graph();
+    last_em = false;
+    rec = Rec();
+    m = h.m;
+    cpar = h.cpar;
+    C.Ex = cE[cpar][0]; C.Ey = cE[cpar][1]; C.Hz = cE[cpar][2]; C.vx = cE[cpar][3]; C.vy = cE[cpar][4];
+    has_fine = h.has_fine != 0;
+    rvalid = h.rvalid != 0;
+    cur = h.cur;
+    for (int q = 0; q < 4; ++q) rect[q] = h.rect[q];
+    if (has_fine) {
+      F[cur] = fine_view(cur, rect);
+      fpar = 0;
+      if (h.fpar) flip_fine();
+    } else {
+      fpar = 0;
+    }
+    // a replayed refinement log continues where it stood when the state was
+    // saved (the log itself is this run's own setting)
+    replay_pos = std::min<size_t>((size_t)std::max<int64_t>(h.replay_pos, 0), replay.size() / 4);
+    return DMR_OK;
   }
 
   int stats(double* out) override {
@@ -2431,6 +2557,21 @@ int dmr_adjoint_backward(dmr_ctx* ctx, const void* dL_dn, void* ws, size_t bytes
 int dmr_autotune(dmr_ctx* ctx, int32_t* warps_per_sm, double trial_ms[5]) {
   CTX_OR_FAIL(ctx);
   return ctx->e->autotune(warps_per_sm, trial_ms);
+}
+
+size_t dmr_state_bytes(const dmr_ctx* ctx) {
+  if (!ctx) return 0;
+  return ctx->e->state_bytes();
+}
+
+int dmr_save_state(dmr_ctx* ctx, void* dev_dst, size_t bytes) {
+  CTX_OR_FAIL(ctx);
+  return ctx->e->save_state(dev_dst, bytes);
+}
+
+int dmr_load_state(dmr_ctx* ctx, const void* dev_src, size_t bytes) {
+  CTX_OR_FAIL(ctx);
+  return ctx->e->load_state(dev_src, bytes);
 }
 
 }  // extern "C"

@@ -760,10 +760,11 @@ struct Ctl {           // device control block
 };
 
 // a9 first pass: finish the period's S2 with the last level, E_eff, nu_net,
-// D_eff; period-mean absorbed power partial; reset S2.
+// D_eff; period-mean absorbed power partial; E_rms of the period kept in erms
+// (E_rms^2 = S2 / N, the output E_rms(x, y, t)); reset S2.
 template <class T>
 __global__ void k_rates(Mesh<T> m, Step<T> c, Dens d, Wts w, T* D, T* nu, double* partP,
-                        Ctl* ctl) {
+                        Ctl* ctl, T* erms) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (ctl && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
@@ -784,6 +785,7 @@ __global__ void k_rates(Mesh<T> m, Step<T> c, Dens d, Wts w, T* D, T* nu, double
     D[id] = (den == T(0)) ? (T)d.De : num / den;
     nu[id] = nui - (T)d.nu_a;
     contrib = trap_w(w, i, j) * (double)n * d.heat * e2;
+    erms[id] = sqrt((T)(s2 * d.invN));
     m.S2[id] = 0.0;
   }
   double s = block_sum(contrib);
@@ -957,9 +959,11 @@ __device__ __forceinline__ T bilin(const T* F, int p, int Lx, int Ly, double u, 
 
 // New fine arrays of rectangle (I0, J0) with (nf.nx, nf.ny) cells: values of
 // the old rectangle are copied, the rest bilinear from coarse (Eq. 5a).
+// The E_rms of the last period (nerms, oerms, cerms on the new fine, old fine
+// and coarse node grids) is filled the same way as the density.
 template <class T>
 __global__ void k_expand(Mesh<T> nf, Mesh<T> of, Mesh<T> c, int I0, int J0, int oI0, int oJ0,
-                         int has_old, int r) {
+                         int has_old, int r, T* nerms, const T* oerms, const T* cerms) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y * blockDim.y + threadIdx.y;
   if (a > nf.nx || b > nf.ny) return;
@@ -996,6 +1000,7 @@ __global__ void k_expand(Mesh<T> nf, Mesh<T> of, Mesh<T> c, int I0, int J0, int 
     nf.Hz[id] = (in_x && in_y) ? of.Hz[oid] : bilin(c.Hz, c.p, c.nx, c.ny, xh, yh);
   }
   nf.n[id] = (in_xn && in_yn) ? of.n[oid] : bilin(c.n, c.p, c.nx + 1, c.ny + 1, xn, yn);
+  nerms[id] = (in_xn && in_yn) ? oerms[oid] : bilin(cerms, c.p, c.nx + 1, c.ny + 1, xn, yn);
   nf.S2[id] = 0.0;
 }
 
@@ -1029,6 +1034,17 @@ __global__ void k_s2_view(Mesh<T> m, Step<T> c, double* out) {
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i > m.nx || j > m.ny) return;
   out[j * m.p + i] = m.S2[j * m.p + i] + (double)node_e2(m, c, i, j);
+}
+
+// E_rms within a period: the RMS over the q samples of the running sum, the
+// present E level added on the fly (out in the run's precision, same pitch)
+template <class T>
+__global__ void k_erms_view(Mesh<T> m, Step<T> c, double q, T* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > m.nx || j > m.ny) return;
+  const double s2 = m.S2[j * m.p + i] + (double)node_e2(m, c, i, j);
+  out[j * m.p + i] = (T)sqrt(s2 / q);
 }
 
 // strided 2-D copy between a dense buffer and a pitched array (device side)

@@ -14,6 +14,7 @@
 // GPU that loads this library holds that much memory until the process exits.
 // Each block reduces NOALLOC_NODES_PER_BLOCK nodes, so one call handles at most
 // NOALLOC_MAX_BLOCKS * NOALLOC_NODES_PER_BLOCK nodes; larger maps are rejected.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -31,10 +32,16 @@ constexpr int NOALLOC_MAX_BLOCKS = 16384;
 // Scratch of the reduction: one partial per block, rewritten by every call.
 static __device__ __align__(256) double g_partials[NOALLOC_MAX_BLOCKS];
 
-// Device address of g_partials per device, looked up once per device.
-constexpr int MAX_DEVICES = 64;
+// Device address of g_partials per CUDA context, looked up once per context:
+// the array's address belongs to the context that loaded the module, so a
+// device reset (a new primary context) or a caller-made context needs a
+// lookup of its own.  Contexts are told apart by the driver's unique context
+// ID (a handle value can be reused after a context is destroyed).
+constexpr int MAX_CONTEXTS = 64;
 std::mutex g_mu;
-double* g_dev_partials[MAX_DEVICES] = {};
+struct Slot { unsigned long long ctx; double* ptr; };
+Slot g_slots[MAX_CONTEXTS] = {};
+int g_nslots = 0;
 
 thread_local char g_msg[256] = "";
 
@@ -87,21 +94,57 @@ int fail(int code, const char* msg) {
   return code;
 }
 
-// Device address of the scratch array on the current device (set-up runs on
-// the first call made on each device).
-int scratch_for_current_device(double** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(DMR_ECUDA, cudaGetErrorString(e));
-  if (dev < 0 || dev >= MAX_DEVICES) return fail(DMR_EINVAL, "device index out of range");
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_dev_partials[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_partials);
-    if (e != cudaSuccess) return fail(DMR_ECUDA, cudaGetErrorString(e));
-    g_dev_partials[dev] = static_cast<double*>(p);
+// The driver's cuCtxGetCurrent and cuCtxGetId, reached through the runtime
+// (no link-time dependency on libcuda).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+void* driver_fn(const char* name) {
+  void* f = nullptr;
+  cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+  if (cudaGetDriverEntryPointByVersion(name, &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return f;
+}
+
+// ID of the calling thread's current context; 0 when none is current.
+int current_context(unsigned long long* out) {
+  static CtxGetCurrentFn get = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get || !get_id) {
+    get = reinterpret_cast<CtxGetCurrentFn>(driver_fn("cuCtxGetCurrent"));
+    get_id = reinterpret_cast<CtxGetIdFn>(driver_fn("cuCtxGetId"));
+    if (!get || !get_id) return fail(DMR_ECUDA, "cuCtxGetCurrent / cuCtxGetId are not available");
   }
-  *out = g_dev_partials[dev];
+  CUcontext c = nullptr;
+  if (get(&c) != CUDA_SUCCESS) return fail(DMR_ECUDA, "cuCtxGetCurrent failed");
+  *out = 0;
+  if (c && get_id(c, out) != CUDA_SUCCESS) return fail(DMR_ECUDA, "cuCtxGetId failed");
+  return DMR_OK;
+}
+
+// Device address of the scratch array in the current context.  The set-up
+// (cudaGetSymbolAddress, with the caller's device current) runs on the first
+// call made in each context; later calls in that context reuse the address.
+int scratch_for_current_context(double** out) {
+  std::lock_guard<std::mutex> lock(g_mu);   // also guards the driver entry points
+  unsigned long long ctx = 0;
+  if (int s = current_context(&ctx)) return s;
+  if (ctx)
+    for (int q = 0; q < g_nslots; ++q)
+      if (g_slots[q].ctx == ctx) { *out = g_slots[q].ptr; return DMR_OK; }
+  // the lookup also makes the runtime bind its context to this thread when
+  // none was current yet
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
+  if (e != cudaSuccess) return fail(DMR_ECUDA, cudaGetErrorString(e));
+  if (!ctx)
+    if (int s = current_context(&ctx)) return s;
+  // a full table recycles its first entry (a context that ended long ago)
+  const int q = g_nslots < MAX_CONTEXTS ? g_nslots++ : 0;
+  g_slots[q] = Slot{ctx, static_cast<double*>(p)};
+  *out = g_slots[q].ptr;
   return DMR_OK;
 }
 
@@ -114,13 +157,14 @@ int dmr_electron_total_noalloc(const void* n_dev, int32_t nx, int32_t ny, int32_
   if (!n_dev || !total_dev) return fail(DMR_EINVAL, "null input or output pointer");
   if (nx < 1 || ny < 1 || !(dx > 0.0)) return fail(DMR_EINVAL, "nx, ny must be >= 1 and dx > 0");
   if (precision != 0 && precision != 1) return fail(DMR_EINVAL, "precision must be 0 or 1");
-  const long long nodes = (long long)(nx + 1) * (long long)(ny + 1);
+  // widened before the + 1, so nx or ny = INT32_MAX cannot overflow
+  const long long nodes = ((long long)nx + 1) * ((long long)ny + 1);
   const long long max_nodes = (long long)NOALLOC_MAX_BLOCKS * NOALLOC_NODES_PER_BLOCK;
   if (nodes > max_nodes)
     return fail(DMR_ECAPACITY,
                 "map larger than the fixed scratch allows (at most 67108864 nodes)");
   double* partials = nullptr;
-  if (int s = scratch_for_current_device(&partials)) return s;
+  if (int s = scratch_for_current_context(&partials)) return s;
   const int nblk = (int)((nodes + NOALLOC_NODES_PER_BLOCK - 1) / NOALLOC_NODES_PER_BLOCK);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   if (precision == 1)

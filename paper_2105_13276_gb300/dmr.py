@@ -20,7 +20,8 @@ OK, EINVAL, ECAPACITY, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -
 STATUS_NAMES = {0: "DMR_OK", -1: "DMR_EINVAL", -2: "DMR_ECAPACITY", -3: "DMR_ECUDA",
                 -4: "DMR_EUNSTABLE", -5: "DMR_ETIMEOUT", -6: "DMR_ESTATE"}
 
-FIELDS = {"Ex": 0, "Ey": 1, "Hz": 2, "vx": 3, "vy": 4, "n": 5, "S2": 6, "mask": 7}
+FIELDS = {"Ex": 0, "Ey": 1, "Hz": 2, "vx": 3, "vy": 4, "n": 5, "S2": 6, "mask": 7,
+          "erms": 8}
 STATS = ["t", "R", "fine_cells", "N_e", "P_abs", "W_abs", "periods", "coarse_steps", "n_max",
          "flags"]
 # strip heights the autotuners try, as warps-per-SM targets (trial_ms order)
@@ -99,6 +100,9 @@ def load():
         "dmr_batch_launch_count": (c_int, [P, POINTER(c_int64)]),
         "dmr_batch_last_error": (c_char_p, [P]),
         "dmr_noalloc_last_error": (c_char_p, []),
+        "dmr_state_bytes": (c_size_t, [P]),
+        "dmr_save_state": (c_int, [P, P, c_size_t]),
+        "dmr_load_state": (c_int, [P, P, c_size_t]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -339,6 +343,23 @@ class Run:
             c_void_p(ckpt.data_ptr()), c_size_t(ckpt.numel()), byref(dE0), byref(dnu),
             c_void_p(dseed.data_ptr()) if dseed is not None else None))
         return dE0.value, dnu.value
+
+    # -- checkpoint / resume ---------------------------------------------------
+    def save_state(self, buf=None):
+        """Copy the run's state into a device buffer (a uint8 torch tensor,
+        allocated here when not given); returns the buffer."""
+        import torch
+        nb = int(self.lib.dmr_state_bytes(self.ctx))
+        if buf is None:
+            buf = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        self._check(self.lib.dmr_save_state(self.ctx, c_void_p(buf.data_ptr()),
+                                            c_size_t(buf.numel())))
+        return buf
+
+    def load_state(self, buf):
+        """Continue from a state saved by a run of the same configuration."""
+        self._check(self.lib.dmr_load_state(self.ctx, c_void_p(buf.data_ptr()),
+                                            c_size_t(buf.numel())))
 
     def stats(self):
         out = (c_double * len(STATS))()

@@ -20,6 +20,12 @@ from paper_2105_13276_gb300 import adjoint as A  # noqa: E402
 from paper_2105_13276_gb300 import dmr as D  # noqa: E402
 from paper_2105_13276_gb300 import workloads as W  # noqa: E402
 
+# FP64 GPU adjoint against the oracle's complex-step derivative (exact to
+# rounding): relative error bound of the parity gate
+TOL_ADJ64 = 1e-10
+# FP32 forward and backward against the same FP64 reference
+TOL_ADJ32 = 5e-5
+
 
 @pytest.fixture(scope="module", autouse=True)
 def _built():
@@ -101,10 +107,10 @@ def test_fp64_adjoint_matches_complex_step(r):
     n_end, gE0, gnu, gseed = gpu_grads(w, seed, steps, K, target)
     assert np.linalg.norm(n_end - ref.coarse.n) / np.linalg.norm(ref.coarse.n) < 1e-12
     cE0, cnu, cseed = cs_grads(w, seed, steps, log, target, u)
-    assert abs(gE0 / cE0 - 1) < 1e-9, (gE0, cE0)
-    assert abs(gnu / cnu - 1) < 1e-9, (gnu, cnu)
     dir_g = float(np.sum(gseed * u))
-    assert abs(dir_g / cseed - 1) < 1e-9, (dir_g, cseed)
+    errs = (abs(gE0 / cE0 - 1), abs(gnu / cnu - 1), abs(dir_g / cseed - 1))
+    print("FP64 adjoint vs complex step, r=%d (E0, s_nu, seed dir):" % r, errs)
+    assert max(errs) <= TOL_ADJ64, errs
 
 
 def test_fp64_adjoint_townsend_matches_complex_step():
@@ -120,9 +126,9 @@ def test_fp64_adjoint_townsend_matches_complex_step():
     n_end, gE0, gnu, gseed = gpu_grads(w, seed, steps, K, target)
     assert np.linalg.norm(n_end - ref.coarse.n) / np.linalg.norm(ref.coarse.n) < 1e-12
     cE0, cnu, cseed = cs_grads(w, seed, steps, ref.log, target, u)
-    assert abs(gE0 / cE0 - 1) < 1e-9, (gE0, cE0)
-    assert abs(gnu / cnu - 1) < 1e-9, (gnu, cnu)
-    assert abs(float(np.sum(gseed * u)) / cseed - 1) < 1e-9
+    errs = (abs(gE0 / cE0 - 1), abs(gnu / cnu - 1), abs(float(np.sum(gseed * u)) / cseed - 1))
+    print("FP64 adjoint vs complex step, Townsend (E0, s_nu, seed dir):", errs)
+    assert max(errs) <= TOL_ADJ64, errs
 
 
 def test_fp64_adjoint_matches_central_differences():
@@ -153,7 +159,7 @@ def test_fp64_adjoint_matches_central_differences():
 
 def test_fp32_adjoint_close_to_fp64_reference():
     """FP32 forward and backward against the FP64 complex-step reference:
-    the error is reported, and bounded loosely (not a parity gate)."""
+    the error is printed and bounded at about ten times its measured size."""
     w, seed = case(2)
     NT = w["cfg"]["steps_per_period"]
     steps = 2 * NT
@@ -165,4 +171,63 @@ def test_fp32_adjoint_close_to_fp64_reference():
     cE0, cnu, cseed = cs_grads(w, seed, steps, ref.log, target, u)
     errs = (abs(gE0 / cE0 - 1), abs(gnu / cnu - 1), abs(float(np.sum(gseed * u)) / cseed - 1))
     print("FP32 adjoint relative errors (E0, s_nu, seed dir):", errs)
-    assert max(errs) < 5e-2
+    # measured 1.1e-6, 1.1e-6, 5.6e-6 on a GB300: gated at about ten times that
+    assert max(errs) < TOL_ADJ32, errs
+
+
+def test_fp64_adjoint_at_the_benchmark_geometry_matches_central_differences():
+    """The adjoint workload's geometry (coarse 512^2 at lambda/32, r = 2, the
+    65 x 65-node seed map, checkpoints every 256 coarse steps) over four
+    checkpoint segments in FP64: dL/dE0, dL/ds_nu and the derivative along a
+    random seed-map direction against GPU central differences (h = 1e-6
+    relative) of the same forward with its refinement schedule replayed."""
+    w = W.dmr_512_r2(precision=0)
+    cfg = dict(w["cfg"], precision=0)
+    NT = cfg["steps_per_period"]
+    K, steps = 4 * NT, 16 * NT
+    base = D.run_from_workload(w)
+    seed = base.read("n", 1)                              # [j, i] layout of the device map
+    del base
+    pert = W.adjoint_target_map(seed.shape)
+    fwd = D.Run(cfg)
+    fwd.set_patch(w["rect"])
+    fwd.write("n", 1, seed * pert)
+    fwd.advance(steps)
+    target = fwd.read("n")
+    log_run = D.Run(cfg)
+    log_run.set_patch(w["rect"])
+    log_run.write("n", 1, seed)
+    log = []
+    for _ in range(steps // NT):
+        log_run.advance(NT)
+        log.append(log_run.get_patch())
+    rng = np.random.default_rng(11)
+    u = seed * rng.standard_normal(seed.shape)            # a relative seed-map direction
+
+    E0 = torch.tensor(float(cfg["E0"]), dtype=torch.float64, requires_grad=True)
+    nu = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    sm = torch.tensor(seed, dtype=torch.float64, device="cuda", requires_grad=True)
+    n_end = A.dmr_density(E0, nu, sm, cfg, w["rect"], steps, K)
+    tg = torch.tensor(target, dtype=torch.float64, device="cuda")
+    L = ((n_end - tg) ** 2).sum()
+    L.backward()
+    gE0, gnu = E0.grad.item(), nu.grad.item()
+    gdir = float(np.sum(sm.grad.cpu().numpy() * u))
+
+    def loss(E0_, nu_, seed_):
+        run = D.Run(dict(cfg, E0=E0_, nu_scale=nu_))
+        run.set_patch(w["rect"])
+        run.write("n", 1, seed_)
+        run.replay_log(log)
+        run.advance(steps)
+        return float(np.sum((run.read("n") - target) ** 2))
+
+    e0 = cfg["E0"]
+    h = 1e-6
+    fd = ((loss(e0 * (1 + h), 1.0, seed) - loss(e0 * (1 - h), 1.0, seed)) / (2 * h * e0),
+          (loss(e0, 1.0 + h, seed) - loss(e0, 1.0 - h, seed)) / (2 * h),
+          (loss(e0, 1.0, seed + h * u) - loss(e0, 1.0, seed - h * u)) / (2 * h))
+    errs = (abs(fd[0] / gE0 - 1), abs(fd[1] / gnu - 1), abs(fd[2] / gdir - 1))
+    print("FP64 adjoint at 512^2, 16 periods, K = 256 vs central differences "
+          "(E0, s_nu, seed dir):", errs)
+    assert max(errs) < 1e-5, (errs, fd, (gE0, gnu, gdir))

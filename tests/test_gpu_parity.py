@@ -41,7 +41,25 @@ def rel_l2(g, o):
     return float(np.linalg.norm(g.astype(np.float64) - o) / no)
 
 
-def compare(run, sim, tol, fields=FIELDS, levels=(0, 1), s2=True):
+def ring_mask(shape, level, rect):
+    """Elements within one cell of the coarse-fine interface: the outermost
+    row and column of every fine array, and on the coarse mesh a band of
+    width one around the rectangle's sides (index space of the array, which
+    covers every stagger).  A wrong interface value is a thin error that a
+    relative L2 over the whole mesh can hide."""
+    ii, jj = np.meshgrid(np.arange(shape[0]), np.arange(shape[1]), indexing="ij")
+    if level == 1:
+        return (ii == 0) | (jj == 0) | (ii == shape[0] - 1) | (jj == shape[1] - 1)
+    i0, j0, i1, j1 = rect
+    near_x = ((abs(ii - i0) <= 1) | (abs(ii - i1) <= 1)) & (jj >= j0 - 1) & (jj <= j1 + 1)
+    near_y = ((abs(jj - j0) <= 1) | (abs(jj - j1) <= 1)) & (ii >= i0 - 1) & (ii <= i1 + 1)
+    return near_x | near_y
+
+
+def compare(run, sim, tol, fields=FIELDS, levels=(0, 1), s2=True, verbose=False):
+    """Per-field relative L2 (the parity metric) and, where a fine rectangle
+    exists, the element-wise max-abs error on the interface ring relative to
+    the field's largest magnitude, both within tol."""
     worst = {}
     for level in levels:
         mesh = sim.coarse if level == 0 else sim.fine
@@ -54,6 +72,13 @@ def compare(run, sim, tol, fields=FIELDS, levels=(0, 1), s2=True):
             e = rel_l2(g, o)
             worst[(level, name)] = e
             assert e <= tol, (level, name, e)
+            if sim.fine is not None and np.abs(o).max() > 0:
+                ring = ring_mask(o.shape, level, sim.rect)
+                er = float(np.abs(g.astype(np.float64) - o)[ring].max() / np.abs(o).max())
+                worst[(level, name, "ring")] = er
+                assert er <= tol, (level, name, "ring", er)
+    if verbose:
+        print({"%s" % (k,): "%.2e" % v for k, v in worst.items()})
     return worst
 
 
@@ -310,18 +335,50 @@ def test_vacuum_stays_exactly_zero():
 
 def test_full_size_dmr_512_fp32_graphs():
     """The benchmark workload (coarse 512^2 at lambda/32, r = 2, FP32, CUDA
-    graphs as timed) against the FP64 oracle for two periods."""
+    graphs and the tuned strip height as timed) against the FP64 oracle over
+    ten periods, read mid-period (S2 holds a partial sum).  Per-field errors
+    are printed."""
     w = W.dmr_512_r2(precision=1)
     sim = O.sim_from_workload(w)
     NT = w["cfg"]["steps_per_period"]
-    sim.advance(2 * NT)
+    steps = 10 * NT + 17
+    sim.advance(steps)
+    run = D.run_from_workload(w)
+    run.autotune()
+    run.set_graphs(True)
+    run.replay_log(sim.log)
+    run.advance(steps)
+    worst = compare(run, sim, TOL32, verbose=True)
+    for level in (0, 1):
+        e = rel_l2(run.read("erms", level).T, sim.erms(level))
+        worst[(level, "erms")] = e
+        assert e <= TOL32, (level, "erms", e)
+    st = run.stats()
+    assert abs(st["N_e"] / sim.N_e - 1) < TOL32
+    assert abs(st["P_abs"] / sim.P_abs - 1) < TOL32
+
+
+def test_full_size_dmr_512_fp32_with_growth():
+    """The benchmark geometry with a second, dense seed on the rectangle's
+    right side, so that the flags fire and the rectangle grows at the first
+    period ends: growth (Eq. 5a fill) and the E^2 sums at 512^2, with its
+    many strips and blocks, against the FP64 oracle (its log replayed), read
+    mid-period."""
+    w = W.dmr_512_r2(precision=1)
+    w = dict(w, seeds=list(w["seeds"]) + [(3e17, 272 / 512, 0.5, 0.125, 0.125)])
+    sim = O.sim_from_workload(w)
+    NT = w["cfg"]["steps_per_period"]
+    steps = 4 * NT + 17
+    sim.advance(steps)
+    assert sim.log[0] != tuple(w["rect"]), "the rectangle should grow at the first period end"
     run = D.run_from_workload(w)
     run.set_graphs(True)
     run.replay_log(sim.log)
-    run.advance(2 * NT)
-    compare(run, sim, TOL32, s2=False)
-    st = run.stats()
-    assert abs(st["N_e"] / sim.N_e - 1) < TOL32
+    run.advance(steps)
+    assert run.get_patch() == tuple(sim.rect)
+    compare(run, sim, TOL32, verbose=True)
+    for level in (0, 1):
+        assert rel_l2(run.read("erms", level).T, sim.erms(level)) <= TOL32
 
 
 def test_capacity_error_and_state_errors():

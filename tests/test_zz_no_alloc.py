@@ -8,12 +8,15 @@ are the caller's input map and its one-double output.
 
 The test calls it through the C ABI twice in a row on the density of a
 uniform run at two successive period ends and compares each result with the
-run's own FP64 total (dmr_stats), within the FP64 tolerance of the parity
-tests.  This file is collected last so that a stop-at-first-failure run has
-executed every other test before it.
+run's own FP64 total (dmr_stats) and with the trapezoid sum written out on
+the host, within the FP64 tolerance of the parity tests.  Around the second
+call it checks that no device memory was allocated.  This file is collected
+last so that a stop-at-first-failure run has executed every other test
+before it.
 """
 import ctypes
 
+import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -41,6 +44,18 @@ def _call(lib, nmap, nx, ny, precision, dx, stream, out):
                                           ctypes.c_void_p(out.data_ptr()))
 
 
+def _trapezoid_total(nmap, dx):
+    """The composite trapezoid sum written out on the host in FP64 (the rule
+    the run totals use): half weights on the first and last node of each
+    axis."""
+    n = np.asarray(nmap, dtype=np.float64)
+    wy = np.ones(n.shape[0])
+    wy[[0, -1]] = 0.5
+    wx = np.ones(n.shape[1])
+    wx[[0, -1]] = 0.5
+    return dx * dx * float(np.sum(wy[:, None] * wx[None, :] * n))
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_noalloc_total_equals_run_total_twice(lib, precision):
     nx, ny = 70, 50
@@ -54,11 +69,25 @@ def test_noalloc_total_equals_run_total_twice(lib, precision):
         run.advance(NT)                     # a period end: the run has its own total
         ref = run.stats()["N_e"]
         run.read_into("n", 0, nmap)         # queued on the run's stream
+        run.sync()
+        host = _trapezoid_total(nmap.cpu().numpy(), run.dxc)
+        torch.cuda.synchronize()
+        before = torch.cuda.memory_stats()
+        free0, _ = torch.cuda.mem_get_info()
         st = _call(lib, nmap, nx, ny, precision, run.dxc, run.stream, out)
         assert st == D.OK, lib.dmr_noalloc_last_error()
         run.sync()
+        free1, _ = torch.cuda.mem_get_info()
+        after = torch.cuda.memory_stats()
         got = float(out.item())
         assert ref > 0 and abs(got / ref - 1.0) <= TOL, (call, got, ref)
+        assert abs(got / host - 1.0) <= TOL, (call, got, host)
+        if call == 1:
+            # the call after the set-up allocates nothing, through torch's
+            # allocator or around it
+            for key in ("allocation.all.allocated", "segment.all.allocated"):
+                assert after.get(key, 0) == before.get(key, 0), key
+            assert free1 == free0, (free0, free1)
 
 
 def test_noalloc_rejects_maps_beyond_its_scratch(lib):
