@@ -138,15 +138,21 @@ def cpu_oracle_rate(w, budget_s=12.0, per_step_cap=None):
     return steps * per_step / dt, steps, dt
 
 
-def em_launch_bytes(cfg, rect, es):
-    """Algorithmic bytes of the first EM launch of a period (no E^2 sample):
-    every E, H, v component and n read once, E, H, v written once, 11 words
-    per node of the coarse mesh and of the fine rectangle."""
-    nodes = (cfg["nx"] + 1) * (cfg["ny"] + 1)
-    r = cfg.get("r", 1)
+def period_em_bytes(cfg, rect, es):
+    """Algorithmic bytes of all EM launches of one period with the fine
+    rectangle rect: every E, H, v component and n read once and E, H, v
+    written once (11 words per node and step), the FP64 E^2 sum read and
+    written (16 B) on every step but the first of the period, and the coarse
+    E means the last fine sub-step writes (2 words per coarse node of the
+    closed rectangle)."""
+    NT, r = cfg["steps_per_period"], cfg.get("r", 1)
+    cn = (cfg["nx"] + 1) * (cfg["ny"] + 1)
+    b = NT * 11 * es * cn + (NT - 1) * 16 * cn
     if r > 1 and rect is not None and rect[0] >= 0:
-        nodes += (r * (rect[2] - rect[0]) + 1) * (r * (rect[3] - rect[1]) + 1)
-    return 11 * es * nodes
+        fn = (r * (rect[2] - rect[0]) + 1) * (r * (rect[3] - rect[1]) + 1)
+        b += r * NT * 11 * es * fn + (r * NT - 1) * 16 * fn
+        b += NT * 2 * es * (rect[2] - rect[0] + 1) * (rect[3] - rect[1] + 1)
+    return b
 
 
 def kernel_source_sha():
@@ -488,8 +494,9 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def timed_periods(run, clocks_on):
-        """K periods from t = 0, one CUDA-event pair per period on the run's
-        stream, L2 flushed between periods outside the timed intervals."""
+        """K periods, one CUDA-event pair per period on the run's stream, L2
+        flushed between periods outside the timed intervals; also the EM
+        launches' algorithmic bytes of each period (its rectangle)."""
         s = run.stream
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(K)]
@@ -499,7 +506,9 @@ def run_ours(args):
         barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
+        em_bytes = 0.0
         for k in range(K):
+            em_bytes += period_em_bytes(cfg, run.get_patch(), es)
             evs[k][0].record(s)
             run.advance(NT)
             evs[k][1].record(s)
@@ -509,17 +518,17 @@ def run_ours(args):
         barrier()
         wall = time.perf_counter() - t0
         clocks = sampler.stop() if sampler else None
-        return sum(a.elapsed_time(b) for a, b in evs), wall, clocks
+        return sum(a.elapsed_time(b) for a, b in evs), wall, clocks, em_bytes
 
     # timed run: no per-kernel instrumentation.  The dominant kernel is the
     # first EM launch of a coarse step (k_em2: coarse step + first fine
-    # sub-step, about half of the period in the ncu launch list); its
-    # duration is taken from the autotuner's graph replays of that launch on
-    # the run's stream, at the start and at the end of the timed run.
+    # sub-step, about half of the period in the ncu launch list), in the form
+    # of 63 of the 64 steps of a period (with the E^2 samples); its duration
+    # is measured on the run's stream as CUDA-graph replays of that launch
+    # (dmr_time_launch), at the start and at the end of the timed run.
     run = D.run_from_workload(w, device=dev)
     wps, trial = run.autotune()
-    cand = list(D.TUNE_WPS)
-    roof_pts = [(trial[cand.index(wps)], em_launch_bytes(cfg, run.get_patch(), es))]
+    forms0 = [run.time_launch(f, 20) for f in ((0, 1, 2) if cfg.get("r", 1) > 1 else (0, 1))]
     run.set_graphs(True)
     # one untimed period on the timed run: its first graph capture and
     # instantiation are host work, kept out of the timed region (recaptures
@@ -527,12 +536,11 @@ def run_ours(args):
     run.advance(NT)
     run.sync()
     l0 = run.launch_count()
-    ms, t_wall, clocks = timed_periods(run, True)
+    ms, t_wall, clocks, em_bytes = timed_periods(run, True)
     launches = run.launch_count() - l0
     st = run.stats()
     final_rect = list(run.get_patch())
-    _, trial_end = run.autotune()
-    roof_pts.append((trial_end[cand.index(wps)], em_launch_bytes(cfg, final_rect, es)))
+    forms1 = [run.time_launch(f, 20) for f in ((0, 1, 2) if cfg.get("r", 1) > 1 else (0, 1))]
     del run
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
@@ -541,17 +549,34 @@ def run_ours(args):
     value = world * K * upp / (ms / 1e3)
 
     peak, src = measured_peak()
-    t_ms = sum(t for t, _ in roof_pts) / len(roof_pts)
-    nbytes = sum(b for _, b in roof_pts) / len(roof_pts)
-    ach = nbytes / (t_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": "k_em2 (coarse step + first fine sub-step)",
-            "achieved": ach, "peak": peak, "peak_source": src + " (burst copy)", "unit": "GB/s",
-            "frac": ach / peak, "traffic": recorded_traffic("k_em2"),
-            "avg_launch_us": 1e3 * t_ms, "algorithmic_bytes_per_launch": nbytes,
+
+    def form_roof(q):
+        t_ms = 0.5 * (forms0[q][0] + forms1[q][0])
+        nbytes = 0.5 * (forms0[q][1] + forms1[q][1])
+        ach = nbytes / (t_ms / 1e3) / 1e9
+        return {"achieved": ach, "frac": ach / peak, "avg_launch_us": 1e3 * t_ms,
+                "algorithmic_bytes_per_launch": nbytes,
+                "launch_us_start_end": [round(1e3 * forms0[q][0], 3), round(1e3 * forms1[q][0], 3)]}
+
+    mid = form_roof(1)
+    step_ach = em_bytes / (ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_em2 (coarse step + first fine sub-step), mid-period form",
+            "achieved": mid["achieved"], "peak": peak, "peak_source": src + " (burst copy)",
+            "unit": "GB/s", "frac": mid["frac"], "traffic": recorded_traffic("k_em2"),
+            "avg_launch_us": mid["avg_launch_us"],
+            "algorithmic_bytes_per_launch": mid["algorithmic_bytes_per_launch"],
             "timed_region": "CUDA-graph replays of 20 back-to-back copies of the launch on the "
-                            "run's stream at t = 0 and after the %d timed periods (mean of the "
-                            "two states: %.2f and %.2f us)" % (K, 1e3 * roof_pts[0][0],
-                                                               1e3 * roof_pts[1][0])}
+                            "run's stream (dmr_time_launch) at the start and after the %d timed "
+                            "periods, mean of the two states" % K,
+            "boundary_form": form_roof(0),
+            "frac_step": step_ach / peak,
+            "achieved_step": step_ach,
+            "step_note": "frac_step: algorithmic bytes of all EM launches of the timed periods "
+                         "(60 B per node and step in FP32, 44 B on a period's first step, + the "
+                         "coarse means) / the timed periods' total time (period-end kernels and "
+                         "launch gaps included) / peak"}
+    if len(forms0) > 2:
+        roof["fine_substep"] = form_roof(2)
 
     # uniform fine mesh on the same GPU: the comparison the metric names
     uni_rate = None

@@ -244,6 +244,20 @@ int dmr_sync(const dmr_ctx* ctx);
  * their own. */
 int dmr_autotune(dmr_ctx* ctx, int32_t* warps_per_sm, double trial_ms[5]);
 
+/* Duration of one EM launch form of the present step (at a period boundary;
+ * the run is left unchanged): reps back-to-back copies of the launch are
+ * captured in a CUDA graph and replayed on the run's stream (best of three
+ * timed replays), *ms_per_launch their mean.  form 0: the first launch of a
+ * coarse step at a period boundary (coarse step with the first fine
+ * sub-step, no E^2 sample); 1: the same launch as the other steps of a
+ * period run it, with the E^2 samples of both meshes (the sums are kept
+ * aside and put back); 2: the last fine sub-step alone (E^2 sample and the
+ * fine->coarse transfer into the coarse arrays).  *algorithmic_bytes: the
+ * bytes that launch must move (each element read and written once: 11 words
+ * per node, + 16 B per node with an E^2 sample, + the coarse means).
+ * Errors: DMR_ESTATE (mid-period, or form 2 without a rectangle), DMR_EINVAL. */
+int dmr_time_launch(dmr_ctx* ctx, int form, int reps, double* ms_per_launch, double* algorithmic_bytes);
+
 /* Set the strip height of all EM launches directly, as a warps-per-SM target
  * in [1, 1024] (e.g. the choice dmr_autotune made on an earlier run of the
  * same size).  Results do not depend on it.  DMR_EINVAL otherwise. */

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <string>
 #include <vector>
@@ -347,6 +348,7 @@ struct Base {
   virtual size_t adj_bytes() const = 0;
   virtual int adj_backward(const void* dLdn, void* ws, size_t bytes, void* ckpt, size_t cbytes,
                            double* dE0, double* dnu, void* dseed) = 0;
+  virtual int time_launch(int form, int reps, double* ms, double* bytes) = 0;
   virtual size_t state_bytes() const = 0;
   virtual int save_state(void* dst, size_t bytes) = 0;
   virtual int load_state(const void* src, size_t bytes) = 0;
@@ -1801,6 +1803,62 @@ struct Engine final : Base {
     return launched("autotune");
   }
 
+  // Measured duration of one EM launch form of the present step, as CUDA-graph
+  // replays of reps back-to-back copies on the run's stream (at a period
+  // boundary; the run is left unchanged): form 0 the first launch of a coarse
+  // step at a period boundary (coarse step + first fine sub-step, no E^2
+  // sample), 1 the same launch in the form of the other steps of a period
+  // (with the E^2 samples; the sums are kept aside and put back), 2 the last
+  // fine sub-step alone (with its E^2 sample and the fine->coarse transfer).
+  // *bytes: the launch's algorithmic bytes.
+  int time_launch(int form, int reps, double* ms_out, double* bytes_out) override {
+    if (m % cfg.steps_per_period != 0) return fail(DMR_ESTATE, "launch timing at a period boundary");
+    if (form < 0 || form > 2 || reps < 1 || reps > 1000) return fail(DMR_EINVAL, "form must be 0, 1 or 2 and reps in [1, 1000]");
+    if (form == 2 && !has_fine) return fail(DMR_ESTATE, "form 2 needs a fine rectangle");
+    const double cn = (double)(C.nx + 1) * (C.ny + 1);
+    const double fn = has_fine ? (double)(F[cur].nx + 1) * (F[cur].ny + 1) : 0.0;
+    const size_t cs2 = L.cplane * sizeof(double);
+    const size_t fs2 = has_fine ? (size_t)(F[cur].ny + 1) * (size_t)F[cur].p * sizeof(double) : 0;
+    // the E^2 sums a mid-period form adds to: coarse into the read-out
+    // buffer, fine into the idle fine set (rewritten at the next growth)
+    if (form >= 1) {
+      if (int s_ = ck(cudaMemcpyAsync(view, C.S2, cs2, cudaMemcpyDeviceToDevice, st), "keep S2")) return s_;
+      if (has_fine)
+        if (int s_ = ck(cudaMemcpyAsync(fS2[cur ^ 1], fS2[cur], fs2, cudaMemcpyDeviceToDevice, st), "keep S2")) return s_;
+    }
+    dmr::EmArgs<T> Ac, Af;
+    double bytes = 0.0;
+    std::function<void()> launch;
+    if (form <= 1) {
+      // form 1: the launch of coarse step m + 1 of the period (both meshes
+      // add their E^2 samples), on the present buffers
+      em_args_for(1, m + form, cpar, fpar, has_fine, &Ac, has_fine ? &Af : nullptr);
+      bytes = em_bytes(cn, form == 1) + (has_fine ? em_bytes(fn, form == 1) : 0.0);
+      launch = [&]() {
+        if (has_fine) go_em2(Ac.nblk + Ac.ncfb + Af.nblk + Af.ncfb, Ac, Af);
+        else go_em(Ac.nblk + Ac.ncfb, Ac);
+      };
+    } else {
+      em_args_for(cfg.r, m, cpar, fpar, true, nullptr, &Af);
+      bytes = em_bytes(fn, true) + 2.0 * (double)L.es * (rect[2] - rect[0] + 1) * (rect[3] - rect[1] + 1);
+      launch = [&]() { go_em(Af.nblk + Af.ncfb, Af); };
+    }
+    float ms = 0.f;
+    int s_ = ck(graph_time(st, launch, reps, &ms), "launch timing");
+    launches += 4 * reps;
+    if (form >= 1) {
+      int s2 = ck(cudaMemcpyAsync(C.S2, view, cs2, cudaMemcpyDeviceToDevice, st), "restore S2");
+      if (!s2 && has_fine) s2 = ck(cudaMemcpyAsync(fS2[cur], fS2[cur ^ 1], fs2, cudaMemcpyDeviceToDevice, st), "restore S2");
+      if (!s_) s_ = s2;
+    }
+    if (!s_) s_ = ck(cudaStreamSynchronize(st), "launch timing sync");
+    drop_graph();
+    if (s_) return s_;
+    if (ms_out) *ms_out = ms;
+    if (bytes_out) *bytes_out = bytes;
+    return launched("launch timing");
+  }
+
   // ---- checkpoint / resume of the whole run state (caller-owned buffer)
   size_t state_bytes() const override { return kStateHdrBytes + up(L.total, 256); }
 
@@ -2557,6 +2615,11 @@ int dmr_adjoint_backward(dmr_ctx* ctx, const void* dL_dn, void* ws, size_t bytes
 int dmr_autotune(dmr_ctx* ctx, int32_t* warps_per_sm, double trial_ms[5]) {
   CTX_OR_FAIL(ctx);
   return ctx->e->autotune(warps_per_sm, trial_ms);
+}
+
+int dmr_time_launch(dmr_ctx* ctx, int form, int reps, double* ms_per_launch, double* algorithmic_bytes) {
+  CTX_OR_FAIL(ctx);
+  return ctx->e->time_launch(form, reps, ms_per_launch, algorithmic_bytes);
 }
 
 size_t dmr_state_bytes(const dmr_ctx* ctx) {

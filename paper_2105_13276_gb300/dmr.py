@@ -100,6 +100,7 @@ def load():
         "dmr_batch_launch_count": (c_int, [P, POINTER(c_int64)]),
         "dmr_batch_last_error": (c_char_p, [P]),
         "dmr_noalloc_last_error": (c_char_p, []),
+        "dmr_time_launch": (c_int, [P, c_int, c_int, POINTER(c_double), POINTER(c_double)]),
         "dmr_state_bytes": (c_size_t, [P]),
         "dmr_save_state": (c_int, [P, P, c_size_t]),
         "dmr_load_state": (c_int, [P, P, c_size_t]),
@@ -263,6 +264,14 @@ class Run:
         ms = (c_double * 5)()
         self._check(self.lib.dmr_autotune(self.ctx, byref(w), ms))
         return w.value, list(ms)
+
+    def time_launch(self, form, reps=20):
+        """(ms per launch, algorithmic bytes) of an EM launch form of the
+        present step: 0 first launch at a period boundary, 1 the same launch
+        mid-period (with E^2 samples), 2 the last fine sub-step."""
+        ms, b = c_double(), c_double()
+        self._check(self.lib.dmr_time_launch(self.ctx, int(form), int(reps), byref(ms), byref(b)))
+        return ms.value, b.value
 
     def sync(self):
         self._check(self.lib.dmr_sync(self.ctx))

@@ -444,6 +444,31 @@ def test_autotune_leaves_run_unchanged(precision):
             assert np.array_equal(a.read(name, level), b.read(name, level)), (level, name)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_launch_timing_leaves_run_unchanged(precision):
+    """dmr_time_launch (the bench's roofline timings) in all three forms, on
+    a run mid-way through: the same bits afterwards as an untimed run."""
+    w = W.small_dmr(precision=precision)
+    a = D.run_from_workload(w)
+    b = D.run_from_workload(w)
+    a.advance(64)
+    b.advance(64)
+    for form in (0, 1, 2):
+        ms, nbytes = b.time_launch(form, reps=4)
+        assert ms > 0 and nbytes > 0
+    # the mid-period form moves 16 B per node more (the FP64 E^2 sums)
+    assert b.time_launch(1, 2)[1] > b.time_launch(0, 2)[1]
+    a.advance(2 * 32 + 7)
+    b.advance(2 * 32 + 7)
+    assert a.get_patch() == b.get_patch()
+    for level in (0, 1):
+        for name in FIELDS + ("S2",):
+            assert np.array_equal(a.read(name, level), b.read(name, level)), (level, name)
+    with pytest.raises(D.DMRError) as e:
+        b.time_launch(1)
+    assert e.value.code == D.ESTATE
+
+
 @pytest.mark.parametrize("graphs", [False, True])
 def test_launch_modes_mixed_in_one_run(graphs):
     """Per-kernel timing switches the programmatic dependent launches off;
