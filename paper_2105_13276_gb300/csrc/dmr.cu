@@ -831,75 +831,65 @@ struct Engine final : Base {
     return launched("EM step");
   }
 
-  // continuity step, totals and flags at the end of a period (coarse level mlev)
+  // continuity step, totals and flags at the end of a period (coarse level
+  // mlev): three launches over the coarse mesh's and the fine rectangle's
+  // node tiles (rates, new density, commit with flags and FP64 totals)
   int launch_period_end(int64_t mlev) {
     const int r = cfg.r;
-    const dim3 blk(BX, BY);
     last_em = false;
     int h = tbeg(3, 0.0);
-    dmr::Wts wc{cfg.nx, cfg.ny, has_fine ? 1 : 0, rect[0], rect[1], rect[2], rect[3]};
-    dmr::Dens dc = make_dens(1);
-    dmr::Step<T> sc = make_step(1, mlev, true);
+    dmr::PeArgs<T> A{};
     const dim3 gc = nodes_grid(C.nx, C.ny);
-    dmr::k_rates<T><<<gc, blk, 0, st>>>(C, sc, dc, wc, c_D, c_nu, part[0], ctl, cErms);
-    dmr::Mesh<T> f{};
-    dmr::Dens df{};
-    dmr::Wts wf{};
-    dim3 gf(1, 1);
-    int nbf = 0;
-    int n_launch = 1;
+    A.C.m = C;
+    A.C.c = make_step(1, mlev, true);
+    A.C.d = make_dens(1);
+    A.C.w = dmr::Wts{cfg.nx, cfg.ny, has_fine ? 1 : 0, rect[0], rect[1], rect[2], rect[3]};
+    A.C.D = c_D; A.C.nu = c_nu; A.C.ntmp = c_ntmp; A.C.erms = cErms;
+    A.C.partP = part[0]; A.C.partN = part[2];
+    A.C.gx = (int)gc.x; A.C.nb = (int)(gc.x * gc.y);
+    A.F.nb = 0;
+    A.F.partP = part[1]; A.F.partN = part[3];
+    A.r = r;
+    A.rect = make_int4(rect[0], rect[1], rect[2], rect[3]);
+    A.ctl = ctl;
+    A.mask = mask;
+    A.dxc2 = d.dxc * d.dxc;
+    A.dxf2 = d.dxf * d.dxf;
+    A.period = d.T;
     if (has_fine) {
-      f = F[cur];
-      df = make_dens(r);
-      wf = dmr::Wts{f.nx, f.ny, 0, 0, 0, 0, 0};
-      gf = nodes_grid(f.nx, f.ny);
-      nbf = (int)(gf.x * gf.y);
-      dmr::Step<T> sf = make_step(r, (int64_t)r * mlev, true);
-      dmr::k_rates<T><<<gf, blk, 0, st>>>(f, sf, df, wf, f_D, f_nu, part[1], nullptr, fErms[cur]);
-      ++n_launch;
-    }
-    dmr::Dir<T> none{};
-    dmr::k_density<T><<<gc, blk, 0, st>>>(C, c_D, c_nu, c_ntmp, dc, none);
-    ++n_launch;
-    if (has_fine) {
-      dmr::Dir<T> dir{};
+      const dmr::Mesh<T>& f = F[cur];
+      const dim3 gf = nodes_grid(f.nx, f.ny);
+      A.F.m = f;
+      A.F.c = make_step(r, (int64_t)r * mlev, true);
+      A.F.d = make_dens(r);
+      A.F.w = dmr::Wts{f.nx, f.ny, 0, 0, 0, 0, 0};
+      A.F.D = f_D; A.F.nu = f_nu; A.F.ntmp = f_ntmp; A.F.erms = fErms[cur];
+      A.F.gx = (int)gf.x; A.F.nb = (int)(gf.x * gf.y);
+      dmr::Dir<T>& dir = A.dir;
       dir.r = r;
       for (int q = 0; q < 4; ++q) {
         if (side_on_edge(q)) continue;
         dir.on[q] = 1;
         if (q == dmr::SIDE_BOTTOM || q == dmr::SIDE_TOP) {
-          const int jl = q == dmr::SIDE_BOTTOM ? rect[1] : rect[3];
-          dir.line[q] = c_ntmp + (size_t)jl * C.p;
-          dir.stride[q] = 1;
+          dir.at[q] = q == dmr::SIDE_BOTTOM ? rect[1] : rect[3];
           dir.len[q] = cfg.nx + 1;
           dir.start[q] = rect[0];
         } else {
-          const int il = q == dmr::SIDE_LEFT ? rect[0] : rect[2];
-          dir.line[q] = c_ntmp + il;
-          dir.stride[q] = C.p;
+          dir.at[q] = q == dmr::SIDE_LEFT ? rect[0] : rect[2];
           dir.len[q] = cfg.ny + 1;
           dir.start[q] = rect[1];
         }
       }
-      dmr::k_density<T><<<gf, blk, 0, st>>>(f, f_D, f_nu, f_ntmp, df, dir);
-      ++n_launch;
+      A.n_th = (T)d.n_th;
+      A.gs = (T)(1.0 / (2.0 * d.dxc * d.g_th));
     }
-    dmr::k_commit<T><<<gc, blk, 0, st>>>(C, c_ntmp, wc, has_fine ? f_ntmp : nullptr,
-                                          has_fine ? f.p : 0, r, part[2]);
-    ++n_launch;
-    if (has_fine) {
-      dmr::k_commit<T><<<gf, blk, 0, st>>>(f, f_ntmp, wf, nullptr, 0, r, part[3]);
-      const double gs = 1.0 / (2.0 * d.dxc * d.g_th);
-      dmr::k_flags<T><<<gc, blk, 0, st>>>(C, (T)d.n_th, (T)gs, mask, ctl,
-                                          make_int4(rect[0], rect[1], rect[2], rect[3]));
-      n_launch += 2;
-    }
-    dmr::k_finalize<<<1, 1024, 0, st>>>(part[0], (int)(gc.x * gc.y), part[1], nbf, part[2],
-                                         (int)(gc.x * gc.y), part[3], nbf, d.dxc * d.dxc,
-                                         d.dxf * d.dxf, d.T, ctl);
-    ++n_launch;
+    const int nb = A.C.nb + A.F.nb;
+    const dim3 blk(BX, BY);
+    dmr::k_pe_rates<T><<<nb, blk, 0, st>>>(A);
+    dmr::k_pe_density<T><<<nb, blk, 0, st>>>(A);
+    dmr::k_pe_commit<T><<<nb, blk, 0, st>>>(A);
     tend(h);
-    counted(n_launch);
+    counted(3);
     return launched("period end");
   }
 

@@ -757,79 +757,88 @@ struct Ctl {           // device control block
   int nflag;
   int err;
   int side;            // threshold-line hits: bit 0 left, 1 bottom, 2 right, 3 top
+  unsigned done;       // blocks of the period's last launch that have written their partials
 };
 
-// a9 first pass: finish the period's S2 with the last level, E_eff, nu_net,
-// D_eff; period-mean absorbed power partial; E_rms of the period kept in erms
-// (E_rms^2 = S2 / N, the output E_rms(x, y, t)); reset S2.
+// One mesh's part of the period-end launches: its blocks are 2-D tiles of
+// TX x TY nodes, gx tiles across, nb in all.
 template <class T>
-__global__ void k_rates(Mesh<T> m, Step<T> c, Dens d, Wts w, T* D, T* nu, double* partP,
-                        Ctl* ctl, T* erms) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (ctl && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
-    ctl->bbox[0] = 0x7fffffff; ctl->bbox[1] = 0x7fffffff;
-    ctl->bbox[2] = -1; ctl->bbox[3] = -1;
-    ctl->nflag = 0; ctl->st[4] = 0.0; ctl->side = 0;
-  }
-  double contrib = 0.0;
-  if (i <= m.nx && j <= m.ny) {
-    const int id = j * m.p + i;
-    const double s2 = m.S2[id] + (double)node_e2(m, c, i, j);
-    const double e2 = eeff2_of(s2, d);
-    const T nui = nu_ion<T>(e2, d);
-    T n = m.n[id];
-    T wp2 = n * (T)d.wp2c;
-    T num = nui * (T)d.nu_m * (T)d.De + wp2 * (T)d.Da;
-    T den = nui * (T)d.nu_m + wp2;
-    D[id] = (den == T(0)) ? (T)d.De : num / den;
-    nu[id] = nui - (T)d.nu_a;
-    contrib = trap_w(w, i, j) * (double)n * d.heat * e2;
-    erms[id] = sqrt((T)(s2 * d.invN));
-    m.S2[id] = 0.0;
-  }
-  double s = block_sum(contrib);
-  if (threadIdx.x == 0 && threadIdx.y == 0) partP[blockIdx.y * gridDim.x + blockIdx.x] = s;
-}
+struct PeMesh {
+  Mesh<T> m;
+  Step<T> c;           // level of the period's last E^2 sample
+  Dens d;
+  Wts w;
+  T *D, *nu, *ntmp, *erms;
+  double *partP, *partN;
+  int gx, nb;
+};
 
 // Dirichlet (coarse-fine) sides of the fine density step: new coarse density
 // interpolated along the side (Eq. 5b, frac = 1).
 template <class T>
 struct Dir {
   int on[4];            // side is a coarse-fine boundary
-  const T* line[4];     // new coarse density along the side (strided)
+  const T* line[4];     // new coarse density along the side (strided; adjoint)
   int stride[4];
   int len[4];
   int start[4];
+  int at[4];            // coarse row (bottom/top) or column (left/right) of the side
   int r;
 };
 
+// The arguments of the three period-end launches.
 template <class T>
-__device__ __forceinline__ T dir_value(const Dir<T>& d, int sd, int q) {
-  double pos = (double)d.start[sd] + (double)q / (double)d.r;
-  int i0 = (int)floor(pos);
-  double w = pos - (double)i0;
-  if (i0 < 0) { i0 = 0; w = 0.0; }
-  if (i0 > d.len[sd] - 2) { i0 = d.len[sd] - 2; w = 1.0; }
-  const T xp = (T)w;
-  const T* l = d.line[sd];
-  const int s = d.stride[sd];
-  return l[i0 * s] * (T(1) - xp) + l[(i0 + 1) * s] * xp;
+struct PeArgs {
+  PeMesh<T> C, F;       // coarse mesh; fine rectangle (F.nb = 0 when there is none)
+  Dir<T> dir;           // the fine density's coarse-fine sides
+  int r;
+  int4 rect;            // the rectangle's corner nodes (coarse)
+  T n_th, gs;           // flags: threshold density, 1/(2 dx g_th)
+  uint8_t* mask;
+  Ctl* ctl;
+  double dxc2, dxf2, period;   // cell areas, EM period
+};
+
+// node (i, j) of mesh-block b of a PeMesh (false past the mesh)
+template <class T>
+__device__ __forceinline__ bool pe_node(const PeMesh<T>& M, int b, int* i, int* j) {
+  const int by = b / M.gx, bx = b - by * M.gx;
+  *i = bx * TX + (int)threadIdx.x;
+  *j = by * TY + (int)threadIdx.y;
+  return *i <= M.m.nx && *j <= M.m.ny;
 }
 
-// a9 second pass (+ a10 on the fine mesh): forward-Euler continuity step over
-// one period with face-mean D_eff, zero flux through the domain edges.
+// a9 first pass at node (i, j): finish the period's S2 with the last level,
+// E_eff, nu_net, D_eff; E_rms of the period kept in erms (E_rms^2 = S2 / N,
+// the output E_rms(x, y, t)); reset S2.  Returns the node's period-mean
+// absorbed-power term.
 template <class T>
-__global__ void k_density(Mesh<T> m, const T* D, const T* nu, T* nout, Dens d, Dir<T> dir) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i > m.nx || j > m.ny) return;
+__device__ __forceinline__ double rates_node(const PeMesh<T>& M, int i, int j) {
+  const Mesh<T>& m = M.m;
+  const Dens& d = M.d;
+  const int id = j * m.p + i;
+  const double s2 = m.S2[id] + (double)node_e2(m, M.c, i, j);
+  const double e2 = eeff2_of(s2, d);
+  const T nui = nu_ion<T>(e2, d);
+  T n = m.n[id];
+  T wp2 = n * (T)d.wp2c;
+  T num = nui * (T)d.nu_m * (T)d.De + wp2 * (T)d.Da;
+  T den = nui * (T)d.nu_m + wp2;
+  M.D[id] = (den == T(0)) ? (T)d.De : num / den;
+  M.nu[id] = nui - (T)d.nu_a;
+  M.erms[id] = sqrt((T)(s2 * d.invN));
+  m.S2[id] = 0.0;
+  return trap_w(M.w, i, j) * (double)n * d.heat * e2;
+}
+
+// a9 second pass at node (i, j): forward-Euler continuity step over one
+// period with face-mean D_eff, zero flux through the domain edges.
+template <class T>
+__device__ __forceinline__ T density_new(const PeMesh<T>& M, int i, int j) {
+  const Mesh<T>& m = M.m;
   const int p = m.p;
   const int id = j * p + i;
-  if (dir.on[SIDE_BOTTOM] && j == 0) { nout[id] = dir_value(dir, SIDE_BOTTOM, i); return; }
-  if (dir.on[SIDE_TOP] && j == m.ny) { nout[id] = dir_value(dir, SIDE_TOP, i); return; }
-  if (dir.on[SIDE_LEFT] && i == 0) { nout[id] = dir_value(dir, SIDE_LEFT, j); return; }
-  if (dir.on[SIDE_RIGHT] && i == m.nx) { nout[id] = dir_value(dir, SIDE_RIGHT, j); return; }
+  const T* D = M.D;
   const T n = m.n[id];
   const T Di = D[id];
   T lap = T(0);
@@ -837,49 +846,93 @@ __global__ void k_density(Mesh<T> m, const T* D, const T* nu, T* nout, Dens d, D
   if (i > 0) lap = lap + T(0.5) * (Di + D[id - 1]) * (m.n[id - 1] - n);
   if (j < m.ny) lap = lap + T(0.5) * (Di + D[id + p]) * (m.n[id + p] - n);
   if (j > 0) lap = lap + T(0.5) * (Di + D[id - p]) * (m.n[id - p] - n);
-  const T rate = lap / (T)d.dx2 + nu[id] * n - (T)d.r_ei * n * n;
-  nout[id] = n + (T)d.T * rate;
+  const T rate = lap / (T)M.d.dx2 + M.nu[id] * n - (T)M.d.r_ei * n * n;
+  return n + (T)M.d.T * rate;
 }
 
-// commit the new density: coarse nodes of the closed rectangle take the fine
-// value (direct copy, Sec. III.C); electron-total partial.
+// a10: fine node q of side sd from the new coarse density at the two coarse
+// nodes of the side's line around it (Eq. 5b, frac = 1), the coarse values
+// evaluated here with the coarse step's own operations
 template <class T>
-__global__ void k_commit(Mesh<T> m, const T* nnew, Wts w, const T* fine_n, int fine_p, int r,
-                         double* partN) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  double contrib = 0.0;
-  if (i <= m.nx && j <= m.ny) {
-    const int id = j * m.p + i;
-    T v = nnew[id];
-    if (fine_n && i >= w.I0 && i <= w.I1 && j >= w.J0 && j <= w.J1)
-      v = fine_n[(size_t)(r * (j - w.J0)) * fine_p + r * (i - w.I0)];
-    m.n[id] = v;
-    contrib = trap_w(w, i, j) * (double)v;
+__device__ __forceinline__ T dir_value(const Dir<T>& d, const PeMesh<T>& C, int sd, int q) {
+  double pos = (double)d.start[sd] + (double)q / (double)d.r;
+  int i0 = (int)floor(pos);
+  double w = pos - (double)i0;
+  if (i0 < 0) { i0 = 0; w = 0.0; }
+  if (i0 > d.len[sd] - 2) { i0 = d.len[sd] - 2; w = 1.0; }
+  const T xp = (T)w;
+  const bool hor = sd == SIDE_BOTTOM || sd == SIDE_TOP;
+  const T a = hor ? density_new(C, i0, d.at[sd]) : density_new(C, d.at[sd], i0);
+  const T b = hor ? density_new(C, i0 + 1, d.at[sd]) : density_new(C, d.at[sd], i0 + 1);
+  return a * (T(1) - xp) + b * xp;
+}
+
+// Period end, launch 1 (a9 first pass, a13 power): the coarse mesh's blocks,
+// then the fine rectangle's; resets the control block.
+template <class T>
+__global__ void __launch_bounds__(TX * TY) k_pe_rates(PeArgs<T> A) {
+  const int b = (int)blockIdx.x;
+  if (b == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+    Ctl* ctl = A.ctl;
+    ctl->bbox[0] = 0x7fffffff; ctl->bbox[1] = 0x7fffffff;
+    ctl->bbox[2] = -1; ctl->bbox[3] = -1;
+    ctl->nflag = 0; ctl->st[4] = 0.0; ctl->side = 0; ctl->done = 0u;
   }
-  double s = block_sum(contrib);
-  if (threadIdx.x == 0 && threadIdx.y == 0) partN[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  const bool fine = b >= A.C.nb;
+  const PeMesh<T>& M = fine ? A.F : A.C;
+  const int mb = fine ? b - A.C.nb : b;
+  int i, j;
+  double contrib = 0.0;
+  if (pe_node(M, mb, &i, &j)) contrib = rates_node(M, i, j);
+  const double s = block_sum(contrib);
+  if (threadIdx.x == 0 && threadIdx.y == 0) M.partP[mb] = s;
 }
 
-// a11: flags on the coarse nodes (threshold OR central gradient, the latter
-// as (dn_x s)^2 + (dn_y s)^2 > 1 with s = 1/(2 dx g_th)); uint8 mask, flag
-// bounding box and count, largest density.
+// Period end, launch 2 (a9 second pass, a10): the new density of both meshes;
+// the fine nodes of coarse-fine sides take the interpolated new coarse density.
 template <class T>
-// rect: the fine rectangle's corner nodes (I0, J0, I1, J1): nodes on its
-// sides with n > n_th set the threshold-line bits (Sec. III.D)
-__global__ void k_flags(Mesh<T> m, T n_th, T gs, uint8_t* mask, Ctl* ctl, int4 rect) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i > m.nx || j > m.ny) return;
-  const int p = m.p;
-  const T n = m.n[j * p + i];
-  bool f = n > n_th;
+__global__ void __launch_bounds__(TX * TY) k_pe_density(PeArgs<T> A) {
+  const int b = (int)blockIdx.x;
+  const bool fine = b >= A.C.nb;
+  const PeMesh<T>& M = fine ? A.F : A.C;
+  int i, j;
+  if (!pe_node(M, fine ? b - A.C.nb : b, &i, &j)) return;
+  const int id = j * M.m.p + i;
+  if (fine) {
+    const Dir<T>& d = A.dir;
+    if (d.on[SIDE_BOTTOM] && j == 0) { M.ntmp[id] = dir_value(d, A.C, SIDE_BOTTOM, i); return; }
+    if (d.on[SIDE_TOP] && j == M.m.ny) { M.ntmp[id] = dir_value(d, A.C, SIDE_TOP, i); return; }
+    if (d.on[SIDE_LEFT] && i == 0) { M.ntmp[id] = dir_value(d, A.C, SIDE_LEFT, j); return; }
+    if (d.on[SIDE_RIGHT] && i == M.m.nx) { M.ntmp[id] = dir_value(d, A.C, SIDE_RIGHT, j); return; }
+  }
+  M.ntmp[id] = density_new(M, i, j);
+}
+
+// the new coarse density at node (i, j) as the commit writes it: the fine
+// value at nodes of the closed rectangle (direct copy, Sec. III.C)
+template <class T>
+__device__ __forceinline__ T committed_coarse(const PeArgs<T>& A, int i, int j) {
+  const int4 rc = A.rect;
+  if (A.F.nb > 0 && i >= rc.x && i <= rc.z && j >= rc.y && j <= rc.w)
+    return A.F.ntmp[(size_t)(A.r * (j - rc.y)) * A.F.m.p + A.r * (i - rc.x)];
+  return A.C.ntmp[j * A.C.m.p + i];
+}
+
+// a11 at coarse node (i, j) of the committed density: flag (threshold OR
+// central gradient, the latter as (dn_x s)^2 + (dn_y s)^2 > 1 with
+// s = 1/(2 dx g_th)), mask, bounding box, count, largest density,
+// threshold-line hits of the rectangle's sides (Sec. III.D)
+template <class T>
+__device__ __forceinline__ void flag_node(const PeArgs<T>& A, int i, int j, T n) {
+  const Mesh<T>& m = A.C.m;
+  Ctl* ctl = A.ctl;
+  bool f = n > A.n_th;
   if (i > 0 && i < m.nx && j > 0 && j < m.ny) {
-    T gx = (m.n[j * p + i + 1] - m.n[j * p + i - 1]) * gs;
-    T gy = (m.n[(j + 1) * p + i] - m.n[(j - 1) * p + i]) * gs;
+    T gx = (committed_coarse(A, i + 1, j) - committed_coarse(A, i - 1, j)) * A.gs;
+    T gy = (committed_coarse(A, i, j + 1) - committed_coarse(A, i, j - 1)) * A.gs;
     f = f || (gx * gx + gy * gy > T(1));
   }
-  mask[(size_t)j * (m.nx + 1) + i] = f ? 1 : 0;
+  A.mask[(size_t)j * (m.nx + 1) + i] = f ? 1 : 0;
   // largest density (non-negative doubles order like their bit patterns)
   const double dn = (double)n;
   if (dn != dn) {
@@ -887,10 +940,11 @@ __global__ void k_flags(Mesh<T> m, T n_th, T gs, uint8_t* mask, Ctl* ctl, int4 r
   } else if (dn > 0.0) {
     atomicMax((unsigned long long*)&ctl->st[4], (unsigned long long)__double_as_longlong(dn));
   }
-  if (n > n_th) {
-    const bool in_y = j >= rect.y && j <= rect.w, in_x = i >= rect.x && i <= rect.z;
-    const int bits = (i == rect.x && in_y ? 1 : 0) | (j == rect.y && in_x ? 2 : 0) |
-                     (i == rect.z && in_y ? 4 : 0) | (j == rect.w && in_x ? 8 : 0);
+  const int4 rc = A.rect;
+  if (n > A.n_th) {
+    const bool in_y = j >= rc.y && j <= rc.w, in_x = i >= rc.x && i <= rc.z;
+    const int bits = (i == rc.x && in_y ? 1 : 0) | (j == rc.y && in_x ? 2 : 0) |
+                     (i == rc.z && in_y ? 4 : 0) | (j == rc.w && in_x ? 8 : 0);
     if (bits) atomicOr(&ctl->side, bits);
   }
   if (f) {
@@ -902,38 +956,56 @@ __global__ void k_flags(Mesh<T> m, T n_th, T gs, uint8_t* mask, Ctl* ctl, int4 r
   }
 }
 
-// sum the partials in a fixed order (deterministic), update the totals.
-__global__ void k_finalize(const double* pPc, int nPc, const double* pPf, int nPf,
-                           const double* pNc, int nNc, const double* pNf, int nNf,
-                           double dxc2, double dxf2, double T, Ctl* ctl) {
-  __shared__ double sh[4][32];
-  const int t = threadIdx.x;  // 1024 threads
-  double a[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int q = t; q < nPc; q += blockDim.x) a[0] += pPc[q];
-  for (int q = t; q < nPf; q += blockDim.x) a[1] += pPf[q];
-  for (int q = t; q < nNc; q += blockDim.x) a[2] += pNc[q];
-  for (int q = t; q < nNf; q += blockDim.x) a[3] += pNf[q];
-  for (int k = 0; k < 4; ++k) {
-    double v = a[k];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((t & 31) == 0) sh[k][t >> 5] = v;
+// deterministic sum of v[0..n) by one block (thread 0 gets the result)
+__device__ __forceinline__ double block_sum_array(const double* v, int n) {
+  double a = 0.0;
+  const int t = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  for (int q = t; q < n; q += nt) a += v[q];
+  return block_sum(a);
+}
+
+// Period end, launch 3 (commit, a11, a13 totals): both meshes take their new
+// density, the coarse nodes of the closed rectangle the fine one; electron
+// partials; flags on the coarse mesh (a fine rectangle only); the last block
+// to finish sums all partials in a fixed order into the FP64 totals.
+template <class T>
+__global__ void __launch_bounds__(TX * TY) k_pe_commit(PeArgs<T> A) {
+  __shared__ bool last;
+  const int b = (int)blockIdx.x;
+  const bool fine = b >= A.C.nb;
+  const PeMesh<T>& M = fine ? A.F : A.C;
+  const int mb = fine ? b - A.C.nb : b;
+  int i, j;
+  double contrib = 0.0;
+  if (pe_node(M, mb, &i, &j)) {
+    const T v = fine ? M.ntmp[j * M.m.p + i] : committed_coarse(A, i, j);
+    M.m.n[j * M.m.p + i] = v;
+    contrib = trap_w(M.w, i, j) * (double)v;
+    if (!fine && A.F.nb > 0) flag_node(A, i, j, v);
+  }
+  const double s = block_sum(contrib);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    M.partN[mb] = s;
+    __threadfence();
+    last = atomicAdd(&A.ctl->done, 1u) == (unsigned)(A.C.nb + A.F.nb) - 1u;
   }
   __syncthreads();
-  if (t < 32) {
-    for (int k = 0; k < 4; ++k) {
-      double v = sh[k][t];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (t == 0) a[k] = v;
-    }
-    if (t == 0) {
-      double P = dxc2 * a[0] + dxf2 * a[1];
-      double N = dxc2 * a[2] + dxf2 * a[3];
-      ctl->st[0] = N;
-      ctl->st[1] = P;
-      ctl->st[2] = ctl->st[2] + P * T;
-      ctl->st[3] = ctl->st[3] + 1.0;
-      if (!(N == N) || !(P == P)) ctl->err |= 1;
-    }
+  if (!last) return;
+  __threadfence();
+  const double sPc = block_sum_array(A.C.partP, A.C.nb);
+  const double sPf = block_sum_array(A.F.partP, A.F.nb);
+  const double sNc = block_sum_array(A.C.partN, A.C.nb);
+  const double sNf = block_sum_array(A.F.partN, A.F.nb);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    Ctl* ctl = A.ctl;
+    const double P = A.dxc2 * sPc + A.dxf2 * sPf;
+    const double N = A.dxc2 * sNc + A.dxf2 * sNf;
+    ctl->st[0] = N;
+    ctl->st[1] = P;
+    ctl->st[2] = ctl->st[2] + P * A.period;
+    ctl->st[3] = ctl->st[3] + 1.0;
+    if (!(N == N) || !(P == P)) ctl->err |= 1;
+    ctl->done = 0u;
   }
 }
 
