@@ -251,7 +251,7 @@ def run_batch(args):
     from paper_2105_13276_gb300 import dmr as D
     from paper_2105_13276_gb300 import workloads as W
     dev = torch.device("cuda", 0)
-    ws = W.batch_runs(64)
+    ws = W.batch_runs(args.batch_runs)
     for w in ws:
         c = w["cfg"]
         w["cfg"] = dict(c, patch_cap_cells=(c["r"] * c["nx"]) * (c["r"] * c["ny"]) // 4)
@@ -282,8 +282,8 @@ def run_batch(args):
     line = {"metric": METRIC, "value": K * upp / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": K, "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batched: 64 DMR r=2 runs, coarse {128,256,512,1024}^2, E0 3-8 MV/m, "
-                                   "p 100-760 Torr (seed 13276)",
+            "config": {"workload": "batched: %d DMR r=2 runs, coarse {128,256,512,1024}^2, E0 3-8 MV/m, "
+                                   "p 100-760 Torr (seed 13276)" % len(ws),
                        "runs": len(ws), "coarse_cells_total": sum(w["cfg"]["nx"] * w["cfg"]["ny"] for w in ws),
                        "autotuned_warps_per_sm": wps, "autotune_trial_ms": trial,
                        "fine_cells_end_total": sum(fine),
@@ -678,6 +678,7 @@ def main():
     ap.add_argument("--no-uniform", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch-runs", type=int, default=64, help="runs of the batch64 workload")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("--steps >= 1 and --warmup >= 0")
