@@ -1,0 +1,57 @@
+"""Front-velocity experiment of Sec. IV.C on the GPU: a 1.5 x 1.5 wavelength
+domain in air at 760 Torr, E0 = 5.5 MV/m at 110 GHz, a Gaussian seed of
+1e16 m^-3 at (0.85 Lx, 0.5 Ly).  The paper reports the plasma front moving
+towards the source with the uniform fine mesh and DMR at r = 2 within 1-2 %
+of each other.  Here the DMR run (coarse lambda/64, r = 2, flag-box growth)
+is checked against the uniform lambda/128 mesh it refines to: the front (the
+n = 1e19 m^-3 crossing on the central x line) is tracked every 50 periods
+and its velocity fitted where it lies 1.0 to 0.3 wavelengths from the left
+edge; the two velocities agree within 2 %.  (The absolute velocity follows
+the ionization and diffusion readings, which the paper leaves to cited
+works; r = 4 runs into the coupling instability recorded in the design notes
+and is not asserted.)"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from bench import front_x  # noqa: E402
+from paper_2105_13276_gb300 import dmr as D  # noqa: E402
+from paper_2105_13276_gb300 import workloads as W  # noqa: E402
+
+LAM = 299792458.0 / 110e9
+PERIOD = 1.0 / 110e9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2105_13276_gb300 import build as B
+    B.build()
+    D.load()
+
+
+def front_velocity(w, periods=5000, chunk=50):
+    cfg = w["cfg"]
+    run = D.run_from_workload(w)
+    run.set_graphs(True)
+    track = []
+    for p in range(0, periods, chunk):
+        run.advance(chunk * cfg["steps_per_period"])
+        track.append(((p + chunk) * PERIOD, front_x(run, cfg, LAM)))
+    pts = [(t, x) for t, x in track if x is not None and 0.3 * LAM <= x <= 1.0 * LAM]
+    assert len(pts) >= 10, "the front should cross the fitting window"
+    t, x = np.array(pts).T
+    return -float(np.polyfit(t, x, 1)[0])
+
+
+def test_dmr_r2_front_velocity_within_two_percent_of_uniform():
+    v_uni = front_velocity(W.front_1p5(128, 1))
+    v_dmr = front_velocity(W.front_1p5(64, 2, growth=1))
+    print("front velocity: uniform lambda/128 %.1f km/s, DMR r=2 %.1f km/s (%+.2f %%)"
+          % (v_uni / 1e3, v_dmr / 1e3, 100.0 * (v_dmr / v_uni - 1.0)))
+    assert v_uni > 0 and v_dmr > 0
+    assert abs(v_dmr / v_uni - 1.0) <= 0.02
