@@ -1277,7 +1277,11 @@ struct Engine final : Base {
     if (cfg.r > 1) b += 2 * 10 * up(L.fplane * L.es, 256);        // fine adjoints, two layouts
     b += 6 * up(mx * L.es, 256);                                  // continuity-step scratch
     b += 256;                                                     // FP64 sums
+    b += 4 * side_line_bytes();                                   // Eq. 5b^T E^n shares
     return b;
+  }
+  size_t side_line_bytes() const {
+    return up((size_t)(std::max(cfg.nx, cfg.ny) + 2) * L.es, 256);
   }
 
   size_t adj_bytes() const override {
@@ -1355,36 +1359,40 @@ struct Engine final : Base {
     return s_;
   }
 
-  // one coarse step with its tape records (same kernels as launch_coarse_step,
-  // the first fine sub-step launched on its own)
+  // one coarse step with its tape records: the launches of launch_coarse_step
+  // (the coarse step with the first fine sub-step, then sub-steps 2..r) with
+  // the tape copies queued after each and flushed before any launch that
+  // overwrites their sources (double buffering keeps the inputs of a launch
+  // until the launch after it)
   int record_step(StepRec* R) {
-    const int NT = cfg.steps_per_period, r = cfg.r;
+    const int r = cfg.r;
     R->m = m;
     for (int k = 0; k < 4; ++k) R->rect[k] = rect[k];
     R->fine = has_fine;
     R->rvalid = rvalid;
-    R->cEx = tape_copy(C.Ex, cplane_b());
-    R->cEy = tape_copy(C.Ey, cplane_b());
     const int cp0 = cpar;
     dmr::EmArgs<T> Ac, Af;
-    em_args_for(1, m, cpar, fpar, rvalid, &Ac, nullptr);
-    go_em(Ac.nblk + Ac.ncfb, Ac);
+    em_args_for(1, m, cpar, fpar, rvalid, &Ac, has_fine ? &Af : nullptr);
+    if (has_fine) go_em2(Ac.nblk + Ac.ncfb + Af.nblk + Af.ncfb, Ac, Af);
+    else go_em(Ac.nblk + Ac.ncfb, Ac);
     counted(1);
+    R->cEx = tape_copy(C.Ex, cplane_b());        // E^n (this step's input parity)
+    R->cEy = tape_copy(C.Ey, cplane_b());
     flip_coarse();
-    R->cvx = tape_copy(C.vx, cplane_b());
+    R->cvx = tape_copy(C.vx, cplane_b());        // v^{n+1/2}
     R->cvy = tape_copy(C.vy, cplane_b());
-    // queued copies: coarse E^n and v^{n+1/2} stay in place until the next
-    // coarse step; the fine input of sub-step k until sub-step k+1
     if (has_fine) {
       const size_t fb = fplane_b(rect);
       for (int k = 1; k <= r; ++k) {
-        R->fEx.push_back(tape_copy(F[cur].Ex, fb));
+        if (k > 1) {
+          em_args_for(k, m, cp0, fpar, rvalid, nullptr, &Af);
+          go_em(Af.nblk + Af.ncfb, Af);
+          counted(1);
+        }
+        R->fEx.push_back(tape_copy(F[cur].Ex, fb));   // the sub-step's input
         R->fEy.push_back(tape_copy(F[cur].Ey, fb));
-        em_args_for(k, m, cp0, fpar, rvalid, nullptr, &Af);
-        go_em(Af.nblk + Af.ncfb, Af);
-        counted(1);
         flip_fine();
-        R->fvx.push_back(tape_copy(F[cur].vx, fb));
+        R->fvx.push_back(tape_copy(F[cur].vx, fb));   // its v output
         R->fvy.push_back(tape_copy(F[cur].vy, fb));
         flush_tape();
       }
@@ -1393,7 +1401,6 @@ struct Engine final : Base {
       flush_tape();
     }
     ++m;
-    (void)NT;
     return launched("recorded EM step");
   }
 
@@ -1506,6 +1513,9 @@ struct Engine final : Base {
     T* sc[6];
     for (int k = 0; k < 6; ++k) sc[k] = (T*)take(mx * L.es);
     double* sums = (double*)take(256);
+    T* side_lines[4];
+    for (int k = 0; k < 4; ++k) side_lines[k] = (T*)take(side_line_bytes());
+    adj_side = side_lines;
     tape = w + o;
     tape_cap = bytes - o;
     if (int s_ = ck(cudaMemsetAsync(w, 0, o, st), "zero adjoints")) return s_;
@@ -1673,12 +1683,19 @@ struct Engine final : Base {
 
   // reverse of coarse step R.m: fine sub-steps r..1, then the coarse step,
   // then the transfer^T of the restricted coarse edges to the fine mesh
+  // the four Eq. 5b^T line buffers of the present backward sweep
+  T** adj_side = nullptr;
+
+  // Reverse of coarse step R.m in 2r + 2 launches: per fine sub-step (r..1)
+  // ka_hc (H^T with the Eq. 5b^T scatter) and ka_e; then the coarse ka_h and
+  // ka_e, which adds the Eq. 5b^T shares of the coarse E^n and transposes the
+  // fine->coarse transfer (a8) of the step before.  Every adjoint E edge is
+  // stored by one ka_e, so no buffer is cleared between steps.
   int adj_step(const StepRec& R, const PerRec& P, AdjArr& ca, AdjArr* fa, int& cin, int& fin,
                int fset, double* sums) {
     const int NT = cfg.steps_per_period, r = cfg.r;
     const dim3 blk(BX, BY);
-    cudaMemsetAsync(ca.E[cin ^ 1][0], 0, cplane_b(), st);
-    cudaMemsetAsync(ca.E[cin ^ 1][1], 0, cplane_b(), st);
+    dmr::CoarseT<T> ct{};
     if (R.fine) {
       int fnx, fny, fp;
       fdims(R.rect, &fnx, &fny, &fp);
@@ -1695,24 +1712,39 @@ struct Engine final : Base {
       }
       cb.r = r;
       cb.cp = C.p;
-      cb.old_x = ca.E[cin ^ 1][0]; cb.old_y = ca.E[cin ^ 1][1];
       cb.new_x = ca.E[cin][0]; cb.new_y = ca.E[cin][1];
-      const int ncfb = 2 * fnx + 2 * fny;
+      for (int q = 0; q < 4; ++q) {
+        cb.old_line[q] = adj_side[q];
+        ct.side_on[q] = md.m[q] == dmr::BC_CFB;
+        ct.side_at[q] = cb.at[q];
+        ct.side[q] = adj_side[q];
+      }
+      int ncfb = 0;
+      for (int q = 0; q < 4; ++q)
+        if (md.m[q] == dmr::BC_CFB) ncfb += (q == dmr::SIDE_BOTTOM || q == dmr::SIDE_TOP) ? fnx : fny;
       const dim3 gf = nodes_grid(fnx, fny);
-      const size_t fb = fplane_b(R.rect);
+      const int nbh = (int)(gf.x * gf.y), nbc = (ncfb + BX * BY - 1) / (BX * BY);
+      const dmr::CoarseT<T> none{};
       for (int k = r; k >= 1; --k) {
-        cudaMemsetAsync(A.E[fin ^ 1][0], 0, fb, st);
-        cudaMemsetAsync(A.E[fin ^ 1][1], 0, fb, st);
         const int64_t mf = (int64_t)r * R.m + (k - 1);
         const dmr::Step<T> sf = make_step_at(r, mf, (mf % ((int64_t)r * NT)) != 0, R.rect[0]);
         const dmr::AdjM<T> am = adjm(A, fin, fnx, fny, fp);
-        dmr::ka_h<T><<<gf, blk, 0, st>>>(am, sf, md);
         cb.frac = (T)((double)k / (double)r);
-        dmr::ka_cfb<T><<<(ncfb + 127) / 128, 128, 0, st>>>(am, cb);
+        dmr::ka_hc<T><<<nbh + nbc, blk, 0, st>>>(am, sf, md, cb, nbh, (int)gf.x);
         dmr::FwdM<T> fw;
         fw.Ex = R.fEx[k - 1]; fw.Ey = R.fEy[k - 1]; fw.vx = R.fvx[k - 1]; fw.vy = R.fvy[k - 1]; fw.n = P.nf;
-        dmr::ka_e<T><<<gf, blk, 0, st>>>(am, fw, sf, md, sums);
+        dmr::ka_e<T><<<gf, blk, 0, st>>>(am, fw, sf, md, sums, none);
         fin ^= 1;
+      }
+      if (R.rvalid) {
+        // a8^T of the previous step's transfer, into the fine E^n adjoint
+        ct.restr = 1;
+        ct.I0 = R.rect[0]; ct.J0 = R.rect[1]; ct.I1 = R.rect[2]; ct.J1 = R.rect[3]; ct.r = r;
+        ct.jlo = side_at(R.rect, dmr::SIDE_BOTTOM) ? R.rect[1] : R.rect[1] + 1;
+        ct.jhi = side_at(R.rect, dmr::SIDE_TOP) ? R.rect[3] : R.rect[3] - 1;
+        ct.ilo = side_at(R.rect, dmr::SIDE_LEFT) ? R.rect[0] : R.rect[0] + 1;
+        ct.ihi = side_at(R.rect, dmr::SIDE_RIGHT) ? R.rect[2] : R.rect[2] - 1;
+        ct.fEx = A.E[fin][0]; ct.fEy = A.E[fin][1]; ct.fp = fp;
       }
     }
     const dmr::Step<T> sc = make_step(1, R.m, (R.m % NT) != 0);
@@ -1723,9 +1755,8 @@ struct Engine final : Base {
     dmr::ka_h<T><<<gc, blk, 0, st>>>(am, sc, mc);
     dmr::FwdM<T> fw;
     fw.Ex = R.cEx; fw.Ey = R.cEy; fw.vx = R.cvx; fw.vy = R.cvy; fw.n = P.nc;
-    dmr::ka_e<T><<<gc, blk, 0, st>>>(am, fw, sc, mc, sums);
+    dmr::ka_e<T><<<gc, blk, 0, st>>>(am, fw, sc, mc, sums, ct);
     cin ^= 1;
-    if (R.fine && R.rvalid) restrict_t(ca, cin, fa[fset], fin, R.rect);
     return launched("adjoint step");
   }
 

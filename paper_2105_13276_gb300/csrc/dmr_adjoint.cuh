@@ -77,11 +77,10 @@ __device__ __forceinline__ T adj_y(const AdjM<T>& a, const Modes& md, T mur, int
   return v;
 }
 
-// aH += ce curlH^T(aE'), interior edges (after the Mur rows' share).
+// aH += ce curlH^T(aE'), interior edges (after the Mur rows' share), at cell
+// (i, j).
 template <class T>
-__global__ void ka_h(AdjM<T> a, Step<T> c, Modes md) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void ka_h_cell(const AdjM<T>& a, const Step<T>& c, const Modes& md, int i, int j) {
   if (i >= a.nx || j >= a.ny) return;
   T acc = T(0);
   if (j > 0) acc = acc + adj_x(a, md, c.mur, i, j);
@@ -93,9 +92,29 @@ __global__ void ka_h(AdjM<T> a, Step<T> c, Modes md) {
 
 __device__ __forceinline__ double block_sum_d(double v) { return block_sum(v); }
 
-// Node-wise gather of aE^l (edges (i,j)), av, an; E0 share summed in FP64.
+// Coarse side of a reversed coarse step (nullptrs / off on a fine mesh or
+// without a rectangle):
+//  * the Eq. 5b^T shares of the coarse tangential E^n along the rectangle's
+//    coarse-fine sides, gathered by ka_cfb into line buffers (indexed along
+//    the line) instead of the edge adjoints: the coarse ka_e adds them to
+//    the edges it writes and clears them;
+//  * a8^T: the adjoint of a restricted coarse E^n edge goes to its r fine
+//    edges (1/r each; the fine E^n adjoint) and the coarse edge keeps 0.
 template <class T>
-__global__ void ka_e(AdjM<T> a, FwdM<T> f, Step<T> c, Modes md, double* e0acc) {
+struct CoarseT {
+  int side_on[4], side_at[4];   // lines of the coarse-fine sides (row bottom/top, column left/right)
+  T* side[4];
+  int restr;                     // a8 is transposed at this step
+  int I0, J0, I1, J1, r, jlo, jhi, ilo, ihi;
+  T *fEx, *fEy;                  // the fine E^n adjoint
+  int fp;
+};
+
+// Node-wise gather of aE^l (edges (i,j)), av, an; E0 share summed in FP64.
+// The edge adjoints of E^l are stored (the output buffer is not cleared
+// before); with a CoarseT the side shares are added and a8 transposed.
+template <class T>
+__global__ void ka_e(AdjM<T> a, FwdM<T> f, Step<T> c, Modes md, double* e0acc, CoarseT<T> ct) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int nx = a.nx, ny = a.ny, p = a.p;
@@ -129,7 +148,21 @@ __global__ void ka_e(AdjM<T> a, FwdM<T> f, Step<T> c, Modes md, double* e0acc) {
         out = out + T(2) * f.Ex[id] * (a.aS2[id] * wl + a.aS2[id + 1] * wr);
       }
       a.avx[id] = c.va * avt;
-      a.aEx_out[id] += out;
+      if (ct.side_on[SIDE_BOTTOM] && j == ct.side_at[SIDE_BOTTOM]) {
+        out = ct.side[SIDE_BOTTOM][i] + out;
+        ct.side[SIDE_BOTTOM][i] = T(0);
+      }
+      if (ct.side_on[SIDE_TOP] && j == ct.side_at[SIDE_TOP]) {
+        out = ct.side[SIDE_TOP][i] + out;
+        ct.side[SIDE_TOP][i] = T(0);
+      }
+      if (ct.restr && i >= ct.I0 && i < ct.I1 && j >= ct.jlo && j <= ct.jhi) {
+        const T t = out / (T)ct.r;
+        T* d = ct.fEx + (size_t)(ct.r * (j - ct.J0)) * ct.fp + ct.r * (i - ct.I0);
+        for (int q = 0; q < ct.r; ++q) d[q] += t;
+        out = T(0);
+      }
+      a.aEx_out[id] = out;
     }
     if (i > 0 && i - 1 < nx && j > 0 && j < ny) an_acc = an_acc + f.vx[id - 1] * adj_x(a, md, c.mur, i - 1, j);
     // ---- y edge (i, j)
@@ -163,7 +196,21 @@ __global__ void ka_e(AdjM<T> a, FwdM<T> f, Step<T> c, Modes md, double* e0acc) {
         e0 += (double)g * (double)phi;
       }
       a.avy[id] = c.va * avt;
-      a.aEy_out[id] += out;
+      if (ct.side_on[SIDE_LEFT] && i == ct.side_at[SIDE_LEFT]) {
+        out = ct.side[SIDE_LEFT][j] + out;
+        ct.side[SIDE_LEFT][j] = T(0);
+      }
+      if (ct.side_on[SIDE_RIGHT] && i == ct.side_at[SIDE_RIGHT]) {
+        out = ct.side[SIDE_RIGHT][j] + out;
+        ct.side[SIDE_RIGHT][j] = T(0);
+      }
+      if (ct.restr && j >= ct.J0 && j < ct.J1 && i >= ct.ilo && i <= ct.ihi) {
+        const T t = out / (T)ct.r;
+        T* d = ct.fEy + (size_t)(ct.r * (j - ct.J0)) * ct.fp + ct.r * (i - ct.I0);
+        for (int q = 0; q < ct.r; ++q) d[(size_t)q * ct.fp] += t;
+        out = T(0);
+      }
+      a.aEy_out[id] = out;
     }
     if (j > 0 && i > 0 && i < nx) an_acc = an_acc + f.vy[id - p] * adj_y(a, md, c.mur, i, j - 1);
     a.an[id] += c.cj * an_acc;
@@ -179,13 +226,14 @@ struct CfbT {
   int mode[4], start[4], len[4], at[4];
   int r;
   T frac;
-  T *old_x, *new_x, *old_y, *new_y;   // coarse adjoint arrays of E^n and E^{n+1}
+  T *new_x, *new_y;                   // coarse adjoint arrays of E^{n+1}
+  T* old_line[4];                     // E^n shares, per side along its line (CoarseT::side)
   int cp;                             // coarse pitch
 };
 
+// Eq. 5b^T of side sample q (the sides in the order bottom, top, left, right)
 template <class T>
-__global__ void ka_cfb(AdjM<T> a, CfbT<T> b) {
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void ka_cfb_sample(const AdjM<T>& a, const CfbT<T>& b, int q) {
   const int nfx = a.nx, nfy = a.ny, p = a.p;
   const int order[4] = {SIDE_BOTTOM, SIDE_TOP, SIDE_LEFT, SIDE_RIGHT};
   for (int k = 0; k < 4; ++k) {
@@ -209,20 +257,41 @@ __global__ void ka_cfb(AdjM<T> a, CfbT<T> b) {
       const T wo0 = (one - b.frac) * (one - xp), wo1 = (one - b.frac) * xp;
       const T wn0 = b.frac * (one - xp), wn1 = b.frac * xp;
       size_t s0, s1;
-      T *o, *n;
+      T* n;
       if (xs) {
-        s0 = (size_t)b.at[sd] * b.cp + i0; s1 = s0 + 1; o = b.old_x; n = b.new_x;
+        s0 = (size_t)b.at[sd] * b.cp + i0; s1 = s0 + 1; n = b.new_x;
       } else {
-        s0 = (size_t)i0 * b.cp + b.at[sd]; s1 = s0 + b.cp; o = b.old_y; n = b.new_y;
+        s0 = (size_t)i0 * b.cp + b.at[sd]; s1 = s0 + b.cp; n = b.new_y;
       }
-      atomicAdd(o + s0, wo0 * t);
-      atomicAdd(o + s1, wo1 * t);
+      atomicAdd(b.old_line[sd] + i0, wo0 * t);
+      atomicAdd(b.old_line[sd] + i0 + 1, wo1 * t);
       atomicAdd(n + s0, wn0 * t);
       atomicAdd(n + s1, wn1 * t);
       return;
     }
     q -= len;
   }
+}
+
+// One launch per reversed fine sub-step before ka_e: ka_h over the mesh's
+// cells (the first nbh blocks, TX x TY cells each, gx across), then Eq. 5b^T
+// over the coarse-fine side samples (TX * TY per block).  The two are
+// independent: ka_h writes aH, the samples read aE' and write coarse adjoints.
+template <class T>
+__global__ void __launch_bounds__(TX * TY) ka_hc(AdjM<T> a, Step<T> c, Modes md, CfbT<T> b, int nbh, int gx) {
+  const int blk = (int)blockIdx.x;
+  if (blk < nbh) {
+    const int by = blk / gx, bx = blk - by * gx;
+    ka_h_cell(a, c, md, bx * TX + (int)threadIdx.x, by * TY + (int)threadIdx.y);
+  } else {
+    ka_cfb_sample(a, b, (blk - nbh) * TX * TY + (int)(threadIdx.y * TX + threadIdx.x));
+  }
+}
+
+// The coarse mesh's ka_h (no side samples).
+template <class T>
+__global__ void __launch_bounds__(TX * TY) ka_h(AdjM<T> a, Step<T> c, Modes md) {
+  ka_h_cell(a, c, md, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
 
 // a8^T for E: the adjoint of a restricted coarse edge goes to its r fine edges
