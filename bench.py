@@ -194,6 +194,10 @@ def workload(name):
         return W.large_dmr(r=2)
     if name == "large_r4":
         return W.large_dmr(r=4)
+    if name == "large_r2_wide":
+        return W.large_dmr(r=2, lo=0.17)
+    if name == "large_r4_wide":
+        return W.large_dmr(r=4, lo=0.17)
     raise SystemExit("unknown workload " + name)
 
 
@@ -607,12 +611,15 @@ def run_ours(args):
         er = D.run_from_workload(w, device=dev)
         er.set_graphs(True)
         (rc, cc), eb = er.shape("n", 0)
-        (rf, cf), _ = er.shape("n", 1)
+        has_fine = w["cfg"].get("r", 1) > 1 and w.get("rect") is not None
         dt_ = torch.float32 if es == 4 else torch.float64
         h_nc = torch.empty((rc, cc), dtype=dt_, pin_memory=True)
-        h_nf = torch.empty((rf, cf), dtype=dt_, pin_memory=True)
         er.read_to_host("n", 0, h_nc)
-        er.read_to_host("n", 1, h_nf)
+        h_nf = None
+        if has_fine:
+            (rf, cf), _ = er.shape("n", 1)
+            h_nf = torch.empty((rf, cf), dtype=dt_, pin_memory=True)
+            er.read_to_host("n", 1, h_nf)
         h_out = torch.empty((rc, cc), dtype=dt_, pin_memory=True)
         er2 = D.run_from_workload(dict(w, seeds=[(0.0, 0.5, 0.5, 0.1, 0.1)]), device=dev)
         er2.autotune()
@@ -620,14 +627,15 @@ def run_ours(args):
         del er
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        er2.write_from_host("n", 1, h_nf)     # fine seed map (also sets coinciding coarse nodes)
+        if has_fine:
+            er2.write_from_host("n", 1, h_nf)  # fine seed map (also sets coinciding coarse nodes)
         er2.write_from_host("n", 0, h_nc)     # coarse seed map
         for k in range(K):
             er2.advance(NT)
             er2.read_to_host("n", 0, h_out)   # the step's result: coarse density map
         torch.cuda.synchronize(dev)
         t_e = time.perf_counter() - t0
-        h2d = (h_nc.numel() + h_nf.numel()) * h_nc.element_size()
+        h2d = (h_nc.numel() + (h_nf.numel() if has_fine else 0)) * h_nc.element_size()
         d2h = h_out.numel() * h_out.element_size() + 96
         e2e = {"value": world * K * upp / t_e, "unit": UNIT,
                "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h,
@@ -672,7 +680,9 @@ def main():
     ap.add_argument("--steps", type=int, default=2200, help="timed EM periods")
     ap.add_argument("--warmup", type=int, default=3, help="warm-up periods (separate run)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dmr512")
+    ap.add_argument("--workload", default="dmr512",
+                    help="dmr512 | dmr512_fp64 | uniform256 | uniform256_fp32 | large_r2 | large_r4 | "
+                         "large_r2_wide | large_r4_wide | batch64 | adjoint512 | front")
     ap.add_argument("--uniform-periods", type=int, default=40)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-uniform", action="store_true")

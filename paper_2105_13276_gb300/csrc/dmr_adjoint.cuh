@@ -110,31 +110,49 @@ struct CoarseT {
   int fp;
 };
 
-// Node-wise gather of aE^l (edges (i,j)), av, an; E0 share summed in FP64.
-// The edge adjoints of E^l are stored (the output buffer is not cleared
-// before); with a CoarseT the side shares are added and a8 transposed.
+// Node-wise gather of aE^l (edges (i,j)), av, an; E0 share summed in FP64
+// per block.  The edge adjoints of E^l are stored (the output buffer is not
+// cleared before); with a CoarseT the side shares are added and a8
+// transposed.  Every load of a thread comes before its first store, so the
+// loads of the in-place arrays (av, an, side lines) and of the read-only
+// inputs are all in flight at once.
 template <class T>
-__global__ void ka_e(AdjM<T> a, FwdM<T> f, Step<T> c, Modes md, double* e0acc, CoarseT<T> ct) {
+__global__ void __launch_bounds__(TX * TY) ka_e(AdjM<T> a, FwdM<T> f, Step<T> c, Modes md, double* e0acc,
+                                                CoarseT<T> ct) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int nx = a.nx, ny = a.ny, p = a.p;
-  double e0 = 0.0;
+  T e0 = T(0);
   if (i <= nx && j <= ny) {
     const int id = j * p + i;
+    const bool xe = i < nx, ye = j < ny;
+    // ---- loads: in-place values and side lines
+    const T avx0 = xe ? a.avx[id] : T(0);
+    const T avy0 = ye ? a.avy[id] : T(0);
+    const T an0 = a.an[id];
+    const bool s_b = xe && ct.side_on[SIDE_BOTTOM] && j == ct.side_at[SIDE_BOTTOM];
+    const bool s_t = xe && ct.side_on[SIDE_TOP] && j == ct.side_at[SIDE_TOP];
+    const bool s_l = ye && ct.side_on[SIDE_LEFT] && i == ct.side_at[SIDE_LEFT];
+    const bool s_r = ye && ct.side_on[SIDE_RIGHT] && i == ct.side_at[SIDE_RIGHT];
+    const T v_b = s_b ? ct.side[SIDE_BOTTOM][i] : T(0);
+    const T v_t = s_t ? ct.side[SIDE_TOP][i] : T(0);
+    const T v_l = s_l ? ct.side[SIDE_LEFT][j] : T(0);
+    const T v_r = s_r ? ct.side[SIDE_RIGHT][j] : T(0);
     T an_acc = T(0);
     // ---- x edge (i, j)
-    if (i < nx) {
+    T outx = T(0), avx1 = T(0);
+    if (xe) {
       T out, avt;
       if (j > 0 && j < ny) {
         const T aEa = adj_x(a, md, c.mur, i, j);
-        avt = a.avx[id] + c.cj * (f.n[id] + f.n[id + 1]) * aEa;
+        avt = avx0 + c.cj * (f.n[id] + f.n[id + 1]) * aEa;
         out = aEa;
         if (j == 1 && md.m[SIDE_BOTTOM] == BC_MUR) out = out + a.aEx_in[i];
         if (j == ny - 1 && md.m[SIDE_TOP] == BC_MUR) out = out + a.aEx_in[ny * p + i];
         an_acc = an_acc + f.vx[id] * aEa;
       } else {
         const int sd = j == 0 ? SIDE_BOTTOM : SIDE_TOP;
-        avt = a.avx[id];
+        avt = avx0;
         out = md.m[sd] == BC_MUR ? -c.mur * a.aEx_in[id] : T(0);
       }
       out = out - c.vb * avt;
@@ -147,42 +165,31 @@ __global__ void ka_e(AdjM<T> a, FwdM<T> f, Step<T> c, Modes md, double* e0acc, C
         const T wr = (i + 1 < nx) ? T(0.5) : T(1);            // node i+1: its left edge
         out = out + T(2) * f.Ex[id] * (a.aS2[id] * wl + a.aS2[id + 1] * wr);
       }
-      a.avx[id] = c.va * avt;
-      if (ct.side_on[SIDE_BOTTOM] && j == ct.side_at[SIDE_BOTTOM]) {
-        out = ct.side[SIDE_BOTTOM][i] + out;
-        ct.side[SIDE_BOTTOM][i] = T(0);
-      }
-      if (ct.side_on[SIDE_TOP] && j == ct.side_at[SIDE_TOP]) {
-        out = ct.side[SIDE_TOP][i] + out;
-        ct.side[SIDE_TOP][i] = T(0);
-      }
-      if (ct.restr && i >= ct.I0 && i < ct.I1 && j >= ct.jlo && j <= ct.jhi) {
-        const T t = out / (T)ct.r;
-        T* d = ct.fEx + (size_t)(ct.r * (j - ct.J0)) * ct.fp + ct.r * (i - ct.I0);
-        for (int q = 0; q < ct.r; ++q) d[q] += t;
-        out = T(0);
-      }
-      a.aEx_out[id] = out;
+      avx1 = c.va * avt;
+      if (s_b) out = v_b + out;
+      if (s_t) out = v_t + out;
+      outx = out;
     }
     if (i > 0 && i - 1 < nx && j > 0 && j < ny) an_acc = an_acc + f.vx[id - 1] * adj_x(a, md, c.mur, i - 1, j);
     // ---- y edge (i, j)
-    if (j < ny) {
+    T outy = T(0), avy1 = T(0);
+    if (ye) {
       const T phi = c.sphi * c.ckx[i] - c.cphi * c.skx[i];
       T out, avt;
       if (i > 0 && i < nx) {
         const T aEa = adj_y(a, md, c.mur, i, j);
-        avt = a.avy[id] + c.cj * (f.n[id] + f.n[id + p]) * aEa;
+        avt = avy0 + c.cj * (f.n[id] + f.n[id + p]) * aEa;
         out = aEa;
         if (i == 1 && md.m[SIDE_LEFT] == BC_MUR) out = out + a.aEy_in[j * p];
         if (i == nx - 1 && md.m[SIDE_RIGHT] == BC_MUR) out = out + a.aEy_in[j * p + nx];
         an_acc = an_acc + f.vy[id] * aEa;
       } else {
         const int sd = i == 0 ? SIDE_LEFT : SIDE_RIGHT;
-        avt = a.avy[id];
+        avt = avy0;
         out = md.m[sd] == BC_MUR ? -c.mur * a.aEy_in[id] : T(0);
       }
       out = out - c.vb * avt;
-      e0 -= (double)c.vb * (double)avt * (double)phi;
+      e0 -= c.vb * avt * phi;
       T hs = T(0);
       if (i < nx) hs = hs - a.aHz[id];
       if (i > 0) hs = hs + a.aHz[id - 1];
@@ -193,29 +200,42 @@ __global__ void ka_e(AdjM<T> a, FwdM<T> f, Step<T> c, Modes md, double* e0acc, C
         const T wt = (j + 1 < ny) ? T(0.5) : T(1);
         const T g = T(2) * ey * (a.aS2[id] * wb + a.aS2[id + p] * wt);
         out = out + g;
-        e0 += (double)g * (double)phi;
+        e0 += g * phi;
       }
-      a.avy[id] = c.va * avt;
-      if (ct.side_on[SIDE_LEFT] && i == ct.side_at[SIDE_LEFT]) {
-        out = ct.side[SIDE_LEFT][j] + out;
-        ct.side[SIDE_LEFT][j] = T(0);
-      }
-      if (ct.side_on[SIDE_RIGHT] && i == ct.side_at[SIDE_RIGHT]) {
-        out = ct.side[SIDE_RIGHT][j] + out;
-        ct.side[SIDE_RIGHT][j] = T(0);
-      }
-      if (ct.restr && j >= ct.J0 && j < ct.J1 && i >= ct.ilo && i <= ct.ihi) {
-        const T t = out / (T)ct.r;
-        T* d = ct.fEy + (size_t)(ct.r * (j - ct.J0)) * ct.fp + ct.r * (i - ct.I0);
-        for (int q = 0; q < ct.r; ++q) d[(size_t)q * ct.fp] += t;
-        out = T(0);
-      }
-      a.aEy_out[id] = out;
+      avy1 = c.va * avt;
+      if (s_l) out = v_l + out;
+      if (s_r) out = v_r + out;
+      outy = out;
     }
     if (j > 0 && i > 0 && i < nx) an_acc = an_acc + f.vy[id - p] * adj_y(a, md, c.mur, i, j - 1);
-    a.an[id] += c.cj * an_acc;
+    // ---- stores
+    a.an[id] = an0 + c.cj * an_acc;
+    if (xe) {
+      a.avx[id] = avx1;
+      if (s_b) ct.side[SIDE_BOTTOM][i] = T(0);
+      if (s_t) ct.side[SIDE_TOP][i] = T(0);
+      if (ct.restr && i >= ct.I0 && i < ct.I1 && j >= ct.jlo && j <= ct.jhi) {
+        const T t = outx / (T)ct.r;
+        T* d = ct.fEx + (size_t)(ct.r * (j - ct.J0)) * ct.fp + ct.r * (i - ct.I0);
+        for (int q = 0; q < ct.r; ++q) d[q] += t;
+        outx = T(0);
+      }
+      a.aEx_out[id] = outx;
+    }
+    if (ye) {
+      a.avy[id] = avy1;
+      if (s_l) ct.side[SIDE_LEFT][j] = T(0);
+      if (s_r) ct.side[SIDE_RIGHT][j] = T(0);
+      if (ct.restr && j >= ct.J0 && j < ct.J1 && i >= ct.ilo && i <= ct.ihi) {
+        const T t = outy / (T)ct.r;
+        T* d = ct.fEy + (size_t)(ct.r * (j - ct.J0)) * ct.fp + ct.r * (i - ct.I0);
+        for (int q = 0; q < ct.r; ++q) d[(size_t)q * ct.fp] += t;
+        outy = T(0);
+      }
+      a.aEy_out[id] = outy;
+    }
   }
-  const double s = block_sum_d(e0);
+  const double s = block_sum_d((double)e0);
   if (threadIdx.x == 0 && threadIdx.y == 0 && s != 0.0) atomicAdd(e0acc, s);
 }
 
@@ -231,46 +251,50 @@ struct CfbT {
   int cp;                             // coarse pitch
 };
 
+// Eq. 5b^T of sample q of side SD, if q lies on it; else q is reduced by the
+// side's length and false returned.
+template <int SD, class T>
+__device__ __forceinline__ bool ka_cfb_side(const AdjM<T>& a, const CfbT<T>& b, int& q) {
+  if (b.mode[SD] != BC_CFB) return false;
+  constexpr bool xs = SD == SIDE_BOTTOM || SD == SIDE_TOP;
+  const int nfx = a.nx, nfy = a.ny, p = a.p;
+  const int len = xs ? nfx : nfy;
+  if (q >= len) { q -= len; return false; }
+  T t;
+  if (SD == SIDE_BOTTOM) t = a.aEx_in[q];
+  else if (SD == SIDE_TOP) t = a.aEx_in[nfy * p + q];
+  else if (SD == SIDE_LEFT) t = a.aEy_in[q * p];
+  else t = a.aEy_in[q * p + nfx];
+  const int num = 2 * q + 1 - b.r, den = 2 * b.r;
+  const int fl = (num >= 0) ? num / den : -((-num + den - 1) / den);
+  int i0 = b.start[SD] + fl;
+  T xp = (T)(num - fl * den) / (T)den;
+  if (i0 < 0) { i0 = 0; xp = T(0); }
+  if (i0 > b.len[SD] - 2) { i0 = b.len[SD] - 2; xp = T(1); }
+  const T one = T(1);
+  const T wo0 = (one - b.frac) * (one - xp), wo1 = (one - b.frac) * xp;
+  const T wn0 = b.frac * (one - xp), wn1 = b.frac * xp;
+  size_t s0, s1;
+  T* n;
+  if (xs) {
+    s0 = (size_t)b.at[SD] * b.cp + i0; s1 = s0 + 1; n = b.new_x;
+  } else {
+    s0 = (size_t)i0 * b.cp + b.at[SD]; s1 = s0 + b.cp; n = b.new_y;
+  }
+  atomicAdd(b.old_line[SD] + i0, wo0 * t);
+  atomicAdd(b.old_line[SD] + i0 + 1, wo1 * t);
+  atomicAdd(n + s0, wn0 * t);
+  atomicAdd(n + s1, wn1 * t);
+  return true;
+}
+
 // Eq. 5b^T of side sample q (the sides in the order bottom, top, left, right)
 template <class T>
 __device__ __forceinline__ void ka_cfb_sample(const AdjM<T>& a, const CfbT<T>& b, int q) {
-  const int nfx = a.nx, nfy = a.ny, p = a.p;
-  const int order[4] = {SIDE_BOTTOM, SIDE_TOP, SIDE_LEFT, SIDE_RIGHT};
-  for (int k = 0; k < 4; ++k) {
-    const int sd = order[k];
-    if (b.mode[sd] != BC_CFB) continue;
-    const bool xs = sd == SIDE_BOTTOM || sd == SIDE_TOP;
-    const int len = xs ? nfx : nfy;
-    if (q < len) {
-      T t;
-      if (sd == SIDE_BOTTOM) t = a.aEx_in[q];
-      else if (sd == SIDE_TOP) t = a.aEx_in[nfy * p + q];
-      else if (sd == SIDE_LEFT) t = a.aEy_in[q * p];
-      else t = a.aEy_in[q * p + nfx];
-      const int num = 2 * q + 1 - b.r, den = 2 * b.r;
-      const int fl = (num >= 0) ? num / den : -((-num + den - 1) / den);
-      int i0 = b.start[sd] + fl;
-      T xp = (T)(num - fl * den) / (T)den;
-      if (i0 < 0) { i0 = 0; xp = T(0); }
-      if (i0 > b.len[sd] - 2) { i0 = b.len[sd] - 2; xp = T(1); }
-      const T one = T(1);
-      const T wo0 = (one - b.frac) * (one - xp), wo1 = (one - b.frac) * xp;
-      const T wn0 = b.frac * (one - xp), wn1 = b.frac * xp;
-      size_t s0, s1;
-      T* n;
-      if (xs) {
-        s0 = (size_t)b.at[sd] * b.cp + i0; s1 = s0 + 1; n = b.new_x;
-      } else {
-        s0 = (size_t)i0 * b.cp + b.at[sd]; s1 = s0 + b.cp; n = b.new_y;
-      }
-      atomicAdd(b.old_line[sd] + i0, wo0 * t);
-      atomicAdd(b.old_line[sd] + i0 + 1, wo1 * t);
-      atomicAdd(n + s0, wn0 * t);
-      atomicAdd(n + s1, wn1 * t);
-      return;
-    }
-    q -= len;
-  }
+  if (ka_cfb_side<SIDE_BOTTOM>(a, b, q)) return;
+  if (ka_cfb_side<SIDE_TOP>(a, b, q)) return;
+  if (ka_cfb_side<SIDE_LEFT>(a, b, q)) return;
+  ka_cfb_side<SIDE_RIGHT>(a, b, q);
 }
 
 // One launch per reversed fine sub-step before ka_e: ka_h over the mesh's

@@ -69,20 +69,25 @@ def uniform_fine_equivalent(w):
                 rect=None, steps=w["steps"])
 
 
-def large_dmr(r=2, precision=1, seed=2105):
+def large_dmr(r=2, precision=1, seed=2105, lo=0.25):
     """Large DMR: coarse 2048x1024 (64 x 32 wavelengths) at lambda/32, eight
     Gaussian seeds with n0 log-uniform in [1e14, 1e16] m^-3, centres uniform in
-    the central half, sigma = lambda/8."""
+    [lo, 1 - lo] along each axis (the central half by default), sigma =
+    lambda/8.  The rectangle starts at the seeds' bounding box plus 16 coarse
+    cells: 15 % of the domain for the central half, 25 % for lo = 0.17."""
     rng = np.random.default_rng(seed)
     n0 = 10.0 ** rng.uniform(14.0, 16.0, size=8)
-    xc = rng.uniform(0.25, 0.75, size=8)
-    yc = rng.uniform(0.25, 0.75, size=8)
+    xc = rng.uniform(lo, 1.0 - lo, size=8)
+    yc = rng.uniform(lo, 1.0 - lo, size=8)
     seeds = [(float(n0[q]), float(xc[q]), float(yc[q]), 0.125, 0.125) for q in range(8)]
     cfg = base_cfg(nx=2048, ny=1024, r=r, n_lambda=32, steps_per_period=64, precision=precision)
     i = [int(round(s[1] * 2048)) for s in seeds]
     j = [int(round(s[2] * 1024)) for s in seeds]
     rect = (max(min(i) - 16, 0), max(min(j) - 16, 0), min(max(i) + 16, 2048), min(max(j) + 16, 1024))
-    return dict(name="large DMR coarse 2048x1024 r=%d" % r, cfg=cfg, seeds=seeds,
+    name = "large DMR coarse 2048x1024 r=%d" % r
+    if lo != 0.25:
+        name += ", seed centres in [%.2f, %.2f]^2" % (lo, 1.0 - lo)
+    return dict(name=name, cfg=cfg, seeds=seeds,
                 rect=rect, steps=None)
 
 
