@@ -212,8 +212,9 @@ int dmr_set_graphs(dmr_ctx* ctx, int enable);
  * Classes: 0 EM step (the coarse step together with the first fine
  * sub-step), 1 later fine sub-steps (the last also writes the fine->coarse E
  * transfer into the coarse arrays), 2 kept for compatibility (no launches),
- * 3 period-end kernels, 4 growth.  While timing is on, EM launches do not
- * overlap (no programmatic dependent launch).
+ * 3 period-end kernels, 4 growth, 5 persistent period (all EM steps of a
+ * period in one launch, dmr_set_persistent).  While timing is on, EM
+ * launches do not overlap (no programmatic dependent launch).
  * dmr_kernel_time returns, for a class, the summed device time in ms, the
  * number of timed launches and the algorithmic bytes those launches had to
  * move (each array element read and written once; 0 for classes 3 and 4);
@@ -262,6 +263,31 @@ int dmr_time_launch(dmr_ctx* ctx, int form, int reps, double* ms_per_launch, dou
  * in [1, 1024] (e.g. the choice dmr_autotune made on an earlier run of the
  * same size).  Results do not depend on it.  DMR_EINVAL otherwise. */
 int dmr_set_launch_shape(dmr_ctx* ctx, int32_t warps_per_sm);
+
+/* Persistent period (enable = 1; default 0): every full period that starts
+ * at a period boundary runs its N_T coarse steps with their r fine sub-steps
+ * (Sec. III.C sub-cycling; r <= 8) as one cooperative launch instead of two
+ * launches per coarse step.  Each block of the per-step launches becomes a
+ * unit of work that waits only for the units whose output it reads (its
+ * neighbouring strips of the previous step; near the fine rectangle, the
+ * fine sub-steps and the coarse step it is coupled with through Eq. 5b and
+ * the fine->coarse transfer), so the results are the same bit for bit.
+ * rows_coarse / rows_fine: node rows per warp of its coarse / fine units in
+ * [1, 64], 0 to let the library choose (one unit of a step per resident
+ * block where that fits).  Graph capture of a period (dmr_set_graphs)
+ * captures the persistent launch.  Every wait inside the launch is bounded;
+ * if one gives up, the period end returns DMR_ETIMEOUT and the run refuses
+ * to advance (DMR_ESTATE) until dmr_load_state.  Errors: DMR_EINVAL (rows
+ * outside [0, 64]), DMR_ESTATE (a run of a batch). */
+int dmr_set_persistent(dmr_ctx* ctx, int enable, int32_t rows_coarse, int32_t rows_fine);
+
+/* Test of those bounded waits: with stall = 1, in every later persistent
+ * period one unit (the first coarse unit, at the period's second step)
+ * waits for a count that nothing reaches; polls (>= 1) bounds every wait of
+ * the launch.  The wait gives up after `polls` polls, the launch returns,
+ * and the period end reports DMR_ETIMEOUT.  stall = 0 with polls = 4194304
+ * restores the default.  Errors: DMR_EINVAL (polls < 1). */
+int dmr_test_stall(dmr_ctx* ctx, int stall, int64_t polls);
 
 /* ---- Checkpoint / resume of a run ----
  * The state of a run is everything its later steps depend on: the whole

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libdmr.so")
 
 SOURCES = ["dmr.cu", "dmr_noalloc.cu"]
-HEADERS = ["dmr_kernels.cuh", "dmr_adjoint.cuh"]
+HEADERS = ["dmr_kernels.cuh", "dmr_adjoint.cuh", "dmr_period.cuh"]
 
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 FLAGS = ["-O3", "-lineinfo", "-fmad=false", "-std=c++17", "-Xcompiler", "-fPIC,-O2",

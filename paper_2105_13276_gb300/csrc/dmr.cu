@@ -16,6 +16,7 @@
 #include "dmr.h"
 #include "dmr_kernels.cuh"
 #include "dmr_adjoint.cuh"
+#include "dmr_period.cuh"
 
 namespace {
 
@@ -164,8 +165,14 @@ struct Layout {
   size_t off_mask = 0, off_part[4] = {}, off_ctl = 0, off_view = 0;
   size_t off_psi[8] = {};                 // CPML psi, parity 0 then 1: Hz (x, y), Ex (y), Ey (x)
   size_t off_pmlc[8] = {};                // CPML b, c: x cells, y cells, x nodes, y nodes
+  size_t off_sched = 0, off_ptab = 0;     // persistent period: counters + unit flags, argument tables
+  int nsched = 0;                         // words at off_sched (cleared by every period end)
   size_t total = 0;
 };
+
+// persistent period words: the fine sub-step counts (one 128-byte line each),
+// then one near-rectangle count per step of a period, then the coarse unit flags
+constexpr int kSchedCnt = dmr::kCntStride * (dmr::kMaxR + 1);
 
 int64_t fine_pitch(int64_t nfx) { return (int64_t)up((size_t)nfx + 1, 64); }
 
@@ -220,6 +227,16 @@ int make_layout(const dmr_config* c, const Derived& d, Layout* L, std::string* e
                            (size_t)nx + 1, (size_t)nx + 1, (size_t)ny + 1, (size_t)ny + 1};
     for (int q = 0; q < 8; ++q) L->off_pmlc[q] = take(len[q] * L->es);
   }
+  {
+    // persistent period: kSchedCnt count words, one count per step, then one
+    // flag per coarse unit (at most one unit per EM_WARPS node rows of a strip)
+    const int64_t gx = (nx + 1 + dmr::STRIP_W - 1) / dmr::STRIP_W;
+    const int64_t uy = (ny + 1 + dmr::EM_WARPS - 1) / dmr::EM_WARPS;
+    L->nsched = (int)(kSchedCnt + c->steps_per_period + gx * uy);
+    L->off_sched = take((size_t)L->nsched * 4);
+    const size_t ea = L->es == 4 ? sizeof(dmr::EmArgs<float>) : sizeof(dmr::EmArgs<double>);
+    L->off_ptab = take(2 * (dmr::kMaxR + 1) * ea);
+  }
   L->total = o;
   return DMR_OK;
 }
@@ -238,6 +255,13 @@ struct Base {
   bool capturing = false;
   int64_t graph_nodes = 0;
   bool graphs = false;
+  // the EM steps of a whole period in one persistent launch (k_period)
+  bool persist = false;
+  int prow_c = 0, prow_f = 0;          // node rows per warp of its coarse / fine units (0: chosen)
+  long long sched_limit = 1ll << 22;   // polls of one of its waits before it gives up
+  int sched_stall = 0;                 // test: one unit waits for a count nothing reaches
+  bool dead = false;                   // such a wait gave up: the run's fields are lost
+  bool in_batch = false;               // a run of a batch (its launches go through segment tables)
   cudaGraphExec_t gexec = nullptr;
   int g_cpar = 0, g_fpar = 0, g_rvalid = 0;   // state the graph was captured in
   std::vector<int32_t> replay;
@@ -417,6 +441,184 @@ struct Engine final : Base {
   template <class P>
   P* at(size_t off) { return reinterpret_cast<P*>(ws + off); }
 
+  // ---- persistent period -------------------------------------------------
+  std::vector<dmr::EmArgs<T>> ptab_h;   // launch arguments [parity][phase] of the prepared period
+  dmr::PerSched psched{};
+  int pgrid = 0;
+  size_t psmem = 0;
+
+  bool persist_on() const { return persist && cfg.r <= dmr::kMaxR; }
+
+  // node rows per warp as em_rows constrains them: a multiple of rr (the
+  // strips of the last fine sub-step align with the coarse cells), or one
+  // row when rr divides the warps of a block
+  static int rows_for(int rows, int rr) {
+    rows = std::max(1, std::min(rows, 64));
+    if (rr > 1) {
+      if (rows == 1 && dmr::EM_WARPS % rr == 0) return 1;
+      rows = (rows + rr - 1) / rr * rr;
+      return std::min(rows, 64 - 64 % rr);
+    }
+    return rows;
+  }
+  static void set_rows(dmr::EmArgs<T>* A, int rows, int rr) {
+    A->rows = rows_for(rows, rr);
+    const int sy = (A->m.ny + 1 + A->rows - 1) / A->rows;
+    A->nblk = A->gx * ((sy + dmr::EM_WARPS - 1) / dmr::EM_WARPS);
+  }
+
+  // Arguments, unit counts and grid of the persistent period starting at
+  // coarse level m0 (a period boundary); the tables go to the workspace on
+  // the stream.  Rows per warp: as set, else one row for the fine units and
+  // the fewest coarse rows that leave one unit of a step per resident block.
+  int prep_period(int64_t m0) {
+    const int NT = cfg.steps_per_period, r = cfg.r;
+    const bool fine = has_fine;
+    const int nph = fine ? r + 1 : 1;
+    const bool pml = d.boundary == 1;
+    psmem = 2 * (size_t)nph * sizeof(dmr::EmArgs<T>);
+    int bpsm = 0;
+    cudaError_t e = pml ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, dmr::k_period<T, true>,
+                                                                       32 * dmr::EM_WARPS, psmem)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, dmr::k_period<T, false>,
+                                                                       32 * dmr::EM_WARPS, psmem);
+    if (e != cudaSuccess) return ck(e, "persistent period occupancy");
+    if (bpsm < 1) return fail(DMR_ECUDA, "the persistent period kernel does not fit on an SM");
+    const long long G = (long long)bpsm * num_sms;
+    ptab_h.assign(2 * (size_t)nph, dmr::EmArgs<T>{});
+    for (int par = 0; par < 2; ++par) {
+      const int cp = cpar ^ par;
+      const int f0 = (fpar + par * r) & 1;   // fine parity at the start of coarse step m0 + par
+      dmr::EmArgs<T> Ac, Af;
+      em_args_for(1, m0 + par, cp, f0, rvalid, &Ac, fine ? &Af : nullptr);
+      ptab_h[par * nph] = Ac;
+      if (fine) {
+        ptab_h[par * nph + 1] = Af;
+        for (int k = 2; k <= r; ++k) {
+          em_args_for(k, m0 + par, cp, (f0 + k - 1) & 1, rvalid, nullptr, &Af);
+          ptab_h[par * nph + k] = Af;
+        }
+      }
+    }
+    auto units = [&](int rc, int rf) {
+      dmr::EmArgs<T> a = ptab_h[0];
+      set_rows(&a, rc, 1);
+      long long n = a.nblk;
+      for (int k = 1; k < nph; ++k) {
+        a = ptab_h[k];
+        set_rows(&a, rf, k == r ? r : 1);
+        n += a.nblk + a.ncfb;
+      }
+      return n;
+    };
+    static const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+    int rc = prow_c, rf = prow_f > 0 ? prow_f : 1;
+    if (rc <= 0) {
+      rc = 64;
+      for (int t : cand)
+        if (units(t, rf) <= G) { rc = t; break; }
+      if (units(rc, rf) > G && prow_f <= 0) {
+        rc = rf = 64;
+        for (int t : cand)
+          if (units(t, t) <= G) { rc = rf = t; break; }
+      }
+    }
+    for (int par = 0; par < 2; ++par) {
+      set_rows(&ptab_h[par * nph], rc, 1);
+      for (int k = 1; k < nph; ++k) set_rows(&ptab_h[par * nph + k], rf, k == r ? r : 1);
+    }
+    if (fine) {
+      // the coarse step leaves the edges the last fine sub-step restricts (a8)
+      for (int par = 0; par < 2; ++par) {
+        dmr::RestrW<T>& Wc = ptab_h[par * nph].W;
+        Wc = ptab_h[par * nph + r].W;
+        Wc.on = 0;
+        Wc.skip = 1;
+      }
+    }
+    dmr::PerSched S{};
+    unsigned* sw = at<unsigned>(L.off_sched);
+    S.cnt = sw;
+    S.rnq = sw + kSchedCnt;
+    S.flag = sw + kSchedCnt + NT;
+    S.ctl = ctl;
+    S.m0 = m0;
+    S.limit = sched_limit;
+    S.NT = NT;
+    S.r = fine ? r : 1;
+    const dmr::EmArgs<T>& Ac = ptab_h[0];
+    S.nC = Ac.nblk;
+    S.gxC = Ac.gx;
+    S.nyC = Ac.nblk / Ac.gx;
+    S.rowsC = Ac.rows;
+    S.swC = Ac.sw;
+    if (S.nC + kSchedCnt + NT > L.nsched) return fail(DMR_ECAPACITY, "persistent period: too many coarse units");
+    long long nU = S.nC, nFt = 0;
+    for (int k = 1; k < nph; ++k) {
+      S.nF[k] = ptab_h[k].nblk + ptab_h[k].ncfb;
+      nFt += S.nF[k];
+    }
+    nU += nFt;
+    S.nFt = (int)nFt;
+    if (nU > (1ll << 30)) return fail(DMR_ECAPACITY, "persistent period: too many units");
+    S.nU = (int)nU;
+    constexpr int kMargin = 3;   // coarse cells around the rectangle read or written by the fine steps
+    S.rn[0] = rect[0] - kMargin; S.rn[1] = rect[1] - kMargin;
+    S.rn[2] = rect[2] + kMargin; S.rn[3] = rect[3] + kMargin;
+    S.nRN = 0;
+    if (fine)
+      for (int u = 0; u < S.nC; ++u) {
+        const int bx = u % S.gxC, by = u / S.gxC;
+        const int i0 = bx * S.swC - 1, i1 = bx * S.swC + S.swC;
+        const int j0 = by * dmr::EM_WARPS * S.rowsC - 1, j1 = (by + 1) * dmr::EM_WARPS * S.rowsC;
+        if (i1 >= S.rn[0] && i0 <= S.rn[2] && j1 >= S.rn[1] && j0 <= S.rn[3]) ++S.nRN;
+      }
+    S.stall = sched_stall;
+    psched = S;
+    pgrid = (int)std::min<long long>(nU, G);
+    return ck(cudaMemcpyAsync(at<char>(L.off_ptab), ptab_h.data(), psmem, cudaMemcpyHostToDevice, st),
+              "upload persistent period arguments");
+  }
+
+  // the prepared persistent period: one cooperative launch (every block resident)
+  int go_period() {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)pgrid);
+    lc.blockDim = dim3(32 * dmr::EM_WARPS);
+    lc.dynamicSmemBytes = psmem;
+    lc.stream = st;
+    cudaLaunchAttribute la[1];
+    la[0].id = cudaLaunchAttributeCooperative;
+    la[0].val.cooperative = 1;
+    lc.attrs = la;
+    lc.numAttrs = 1;
+    const dmr::EmArgs<T>* tab = at<dmr::EmArgs<T>>(L.off_ptab);
+    // algorithmic bytes of the period's EM steps, as the per-step launches count them
+    const int NT = cfg.steps_per_period, r = cfg.r;
+    const double cn = (double)(C.nx + 1) * (C.ny + 1);
+    double units = em_bytes(cn, true) * (NT - 1) + em_bytes(cn, false);
+    if (has_fine) {
+      const double fn = (double)(F[cur].nx + 1) * (F[cur].ny + 1);
+      units += em_bytes(fn, true) * ((double)r * NT - 1) + em_bytes(fn, false) +
+               (double)NT * 2.0 * (double)L.es * (rect[2] - rect[0] + 1) * (rect[3] - rect[1] + 1);
+    }
+    int h = tbeg(5, units);
+    cudaError_t e = d.boundary == 1 ? cudaLaunchKernelEx(&lc, dmr::k_period<T, true>, tab, psched)
+                                    : cudaLaunchKernelEx(&lc, dmr::k_period<T, false>, tab, psched);
+    tend(h);
+    counted(1);
+    return ck(e, "persistent period launch");
+  }
+
+  // host state after a persistent period (the parities N_T coarse steps and
+  // r N_T fine sub-steps leave)
+  void after_period() {
+    const int NT = cfg.steps_per_period;
+    if (NT & 1) flip_coarse();
+    if (has_fine && (((int64_t)cfg.r * NT) & 1)) flip_fine();
+    if (has_fine) rvalid = true;
+  }
+
   int init() override {
     for (int q = 0; q < 5; ++q) { cE[0][q] = at<T>(L.off_c[q]); cE[1][q] = at<T>(L.off_c[9 + q]); }
     C.Ex = cE[0][0]; C.Ey = cE[0][1]; C.Hz = cE[0][2]; C.vx = cE[0][3]; C.vy = cE[0][4];
@@ -521,7 +723,6 @@ struct Engine final : Base {
   // about one memory latency, large ones up to 64 (the warm-up row is 1/rows)
   int warps_per_sm = 48;     // strip-height policy (the batch autotuner may change it)
   int warps_per_sm_fine = 48;   // the same for the fine sub-steps after the first (own launches)
-  bool in_batch = false;        // a run of a batch (its launches go through segment tables)
   // rows per warp of an EM launch over an nx x ny mesh with sw-column strips;
   // a multiple of rr, or 1 (the last fine sub-step sums Ey over the r rows of
   // a coarse row)
@@ -856,6 +1057,8 @@ struct Engine final : Base {
     A.dxc2 = d.dxc * d.dxc;
     A.dxf2 = d.dxf * d.dxf;
     A.period = d.T;
+    A.sched = at<unsigned>(L.off_sched);
+    A.nsched = L.nsched;
     if (has_fine) {
       const dmr::Mesh<T>& f = F[cur];
       const dim3 gf = nodes_grid(f.nx, f.ny);
@@ -905,6 +1108,11 @@ struct Engine final : Base {
 
   // stability guard and growth decision from a period's control block
   int period_decide(const dmr::Ctl& hc) {
+    if (hc.err & dmr::kSchedErr) {
+      dead = true;
+      return fail(DMR_ETIMEOUT, "a bounded wait of the persistent period launch gave up; the period's "
+                                "fields are lost (dmr_load_state restores a saved state)");
+    }
     if (hc.err) return fail(DMR_EUNSTABLE, "NaN in the density or totals at a period end");
     const double wp_lim = (2.0 / (has_fine ? d.dtf : d.dtc));
     const double n_lim = wp_lim * wp_lim * ME * EPS0 / (QE * QE);
@@ -1007,6 +1215,7 @@ struct Engine final : Base {
 
   int advance(int64_t n) override {
     if (n < 0) return fail(DMR_EINVAL, "negative step count");
+    if (dead) return fail(DMR_ESTATE, "the run's fields were lost when a bounded wait gave up; load a saved state");
     const int NT = cfg.steps_per_period;
     last_em = false;   // other work may have been queued on the stream since
     while (n > 0) {
@@ -1027,6 +1236,19 @@ struct Engine final : Base {
         if (int s = period_end_host(true)) return s;
         continue;
       }
+      if (persist_on() && m % NT == 0 && n >= NT) {
+        // one persistent launch for the period's EM steps, then the period end
+        drop_graph();   // the argument tables of a captured period would change
+        if (int s = prep_period(m)) return s;
+        if (int s = go_period()) return s;
+        last_em = false;
+        m += NT;
+        n -= NT;
+        after_period();
+        if (int s = launch_period_end(m)) return s;
+        if (int s = period_end_host()) return s;
+        continue;
+      }
       if (int s = launch_coarse_step(m)) return s;
       ++m;
       --n;
@@ -1042,6 +1264,12 @@ struct Engine final : Base {
     drop_graph();
     const int NT = cfg.steps_per_period;
     cudaGraph_t g = nullptr;
+    const bool per = persist_on();
+    if (per) {
+      // the argument tables go to the workspace before the capture; the graph
+      // launches read them on every replay
+      if (int s = prep_period(m)) return s;
+    }
     if (int s = ck(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture")) return s;
     capturing = true;
     graph_nodes = 0;
@@ -1050,7 +1278,12 @@ struct Engine final : Base {
     const bool rv0 = rvalid;
     int s = DMR_OK;
     last_em = false;   // the graph's first launch follows the previous replay's copy
-    for (int q = 0; q < NT && !s; ++q) s = launch_coarse_step(m + q);
+    if (per) {
+      s = go_period();
+      if (!s) after_period();
+    } else {
+      for (int q = 0; q < NT && !s; ++q) s = launch_coarse_step(m + q);
+    }
     if (!s) s = launch_period_end(m + NT);
     capturing = false;
     if (cpar != c0) flip_coarse();
@@ -1928,6 +2161,7 @@ struct Engine final : Base {
       return s_;
     drop_graph();
     last_em = false;
+    dead = false;
     rec = Rec();
     m = h.m;
     cpar = h.cpar;
@@ -2491,6 +2725,27 @@ int dmr_set_graphs(dmr_ctx* ctx, int enable) {
   return DMR_OK;
 }
 
+int dmr_set_persistent(dmr_ctx* ctx, int enable, int32_t rows_coarse, int32_t rows_fine) {
+  CTX_OR_FAIL(ctx);
+  if (rows_coarse < 0 || rows_coarse > 64 || rows_fine < 0 || rows_fine > 64)
+    return ctx->e->fail(DMR_EINVAL, "rows per warp outside [0, 64]");
+  if (ctx->e->in_batch) return ctx->e->fail(DMR_ESTATE, "runs of a batch step in the batch's launches");
+  ctx->e->persist = enable != 0;
+  ctx->e->prow_c = rows_coarse;
+  ctx->e->prow_f = rows_fine;
+  ctx->e->drop_graph();
+  return DMR_OK;
+}
+
+int dmr_test_stall(dmr_ctx* ctx, int stall, int64_t polls) {
+  CTX_OR_FAIL(ctx);
+  if (polls < 1) return ctx->e->fail(DMR_EINVAL, "polls must be >= 1");
+  ctx->e->sched_stall = stall != 0;
+  ctx->e->sched_limit = polls;
+  ctx->e->drop_graph();
+  return DMR_OK;
+}
+
 int dmr_set_launch_shape(dmr_ctx* ctx, int32_t warps_per_sm) {
   CTX_OR_FAIL(ctx);
   if (warps_per_sm < 1 || warps_per_sm > 1024) return ctx->e->fail(DMR_EINVAL, "warps_per_sm outside [1, 1024]");
@@ -2519,8 +2774,8 @@ int dmr_kernel_time(const dmr_ctx* ctx, int kclass, double* ms, int64_t* n, doub
 }
 
 const char* dmr_kernel_class_name(int kclass) {
-  static const char* names[] = {"em_step", "fine_em", "restrict", "period_end", "expand"};
-  if (kclass < 0 || kclass >= 5) return nullptr;
+  static const char* names[] = {"em_step", "fine_em", "restrict", "period_end", "expand", "em_period"};
+  if (kclass < 0 || kclass >= 6) return nullptr;
   return names[kclass];
 }
 

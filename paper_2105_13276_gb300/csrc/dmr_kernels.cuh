@@ -53,6 +53,9 @@ struct RestrW {
   int I0, J0, I1, J1, r;
   int jlo, jhi, ilo, ihi;   // coarse Ex rows [jlo, jhi], Ey columns [ilo, ihi]
   T rinv;
+  // coarse step of the persistent period: leave the edges that the last
+  // fine sub-step writes (the box above) to it
+  int skip;
 };
 
 // Coarse-fine boundary (Eq. 5b) for the fine mesh: per side, Mur or the
@@ -116,53 +119,63 @@ __device__ __forceinline__ T node_e2(const Mesh<T>& m, const Step<T>& c, int i, 
 
 constexpr int TX = 32, TY = 8;   // 2-D thread block of the node-wise kernels
 
-// E at an edge, 0 off the mesh
-template <class T>
-__device__ __forceinline__ T load_ex(const Mesh<T>& m, int i, int j) {
-  if (i < 0 || i >= m.nx || j < 0 || j > m.ny) return T(0);
-  return m.Ex[j * m.p + i];
+// Field loads of the EM step.  CG: through L2 only (ld.global.cg), for the
+// persistent period kernel, whose blocks read what other blocks of the same
+// launch wrote after a flag told them it is there; no L1 line or read-only
+// cache path can then hold an older value.  Otherwise a plain load.
+template <bool CG, class T>
+__device__ __forceinline__ T ldv(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
 }
 
-template <class T>
+// E at an edge, 0 off the mesh
+template <class T, bool CG = false>
+__device__ __forceinline__ T load_ex(const Mesh<T>& m, int i, int j) {
+  if (i < 0 || i >= m.nx || j < 0 || j > m.ny) return T(0);
+  return ldv<CG>(m.Ex + j * m.p + i);
+}
+
+template <class T, bool CG = false>
 __device__ __forceinline__ T load_ey(const Mesh<T>& m, int i, int j) {
   if (i < 0 || i > m.nx || j < 0 || j >= m.ny) return T(0);
-  return m.Ey[j * m.p + i];
+  return ldv<CG>(m.Ey + j * m.p + i);
 }
 
 // Coarse E^{n+1} of interior coarse edge Ex(i, J) / Ey(I, j) evaluated from
 // the level-n state with exactly the coarse step's operations (same values).
-template <class T>
+template <class T, bool CG = false>
 __device__ __forceinline__ T coarse_new_ex(const Bnd<T>& b, int i, int J) {
   const Mesh<T>& m = b.cm;
   const Step<T>& c = b.cc;
   const int p = m.p;
-  const T exm = load_ex(m, i, J - 1), exc = load_ex(m, i, J), exn = load_ex(m, i, J + 1);
-  const T eym = load_ey(m, i, J - 1), eyc = load_ey(m, i, J);
-  const T eymr = load_ey(m, i + 1, J - 1), eyr = load_ey(m, i + 1, J);
-  const T hzp = m.Hz[(J - 1) * p + i] - c.ch * ((eymr - eym) - (exc - exm));
-  const T hz = m.Hz[J * p + i] - c.ch * ((eyr - eyc) - (exn - exc));
-  const T v = c.va * m.vx[J * p + i] - c.vb * exc;
+  const T exm = load_ex<T, CG>(m, i, J - 1), exc = load_ex<T, CG>(m, i, J), exn = load_ex<T, CG>(m, i, J + 1);
+  const T eym = load_ey<T, CG>(m, i, J - 1), eyc = load_ey<T, CG>(m, i, J);
+  const T eymr = load_ey<T, CG>(m, i + 1, J - 1), eyr = load_ey<T, CG>(m, i + 1, J);
+  const T hzp = ldv<CG>(m.Hz + (J - 1) * p + i) - c.ch * ((eymr - eym) - (exc - exm));
+  const T hz = ldv<CG>(m.Hz + J * p + i) - c.ch * ((eyr - eyc) - (exn - exc));
+  const T v = c.va * ldv<CG>(m.vx + J * p + i) - c.vb * exc;
   return exc + c.ce * (hz - hzp) + c.cj * (m.n[J * p + i] + m.n[J * p + i + 1]) * v;
 }
 
-template <class T>
+template <class T, bool CG = false>
 __device__ __forceinline__ T coarse_new_ey(const Bnd<T>& b, int I, int j) {
   const Mesh<T>& m = b.cm;
   const Step<T>& c = b.cc;
   const int p = m.p;
-  const T eyl = load_ey(m, I - 1, j), eyc = load_ey(m, I, j), eyr = load_ey(m, I + 1, j);
-  const T exl = load_ex(m, I - 1, j), exln = load_ex(m, I - 1, j + 1);
-  const T exc = load_ex(m, I, j), exn = load_ex(m, I, j + 1);
-  const T hzl = m.Hz[j * p + I - 1] - c.ch * ((eyc - eyl) - (exln - exl));
-  const T hz = m.Hz[j * p + I] - c.ch * ((eyr - eyc) - (exn - exc));
-  const T v = c.va * m.vy[j * p + I] - c.vb * (eyc + incident(c, I));
+  const T eyl = load_ey<T, CG>(m, I - 1, j), eyc = load_ey<T, CG>(m, I, j), eyr = load_ey<T, CG>(m, I + 1, j);
+  const T exl = load_ex<T, CG>(m, I - 1, j), exln = load_ex<T, CG>(m, I - 1, j + 1);
+  const T exc = load_ex<T, CG>(m, I, j), exn = load_ex<T, CG>(m, I, j + 1);
+  const T hzl = ldv<CG>(m.Hz + j * p + I - 1) - c.ch * ((eyc - eyl) - (exln - exl));
+  const T hz = ldv<CG>(m.Hz + j * p + I) - c.ch * ((eyr - eyc) - (exn - exc));
+  const T v = c.va * ldv<CG>(m.vy + j * p + I) - c.vb * (eyc + incident(c, I));
   return eyc - c.ce * (hz - hzl) + c.cj * (m.n[j * p + I] + m.n[(j + 1) * p + I]) * v;
 }
 
-template <class T>
+template <class T, bool CG = false>
 __device__ __forceinline__ T coarse_new(const Bnd<T>& b, int sd, int k) {
-  if (sd == SIDE_BOTTOM || sd == SIDE_TOP) return coarse_new_ex(b, k, b.at[sd]);
-  return coarse_new_ey(b, b.at[sd], k);
+  if (sd == SIDE_BOTTOM || sd == SIDE_TOP) return coarse_new_ex<T, CG>(b, k, b.at[sd]);
+  return coarse_new_ey<T, CG>(b, b.at[sd], k);
 }
 
 // Eq. 5b for tangential sample q of side sd of the fine rectangle.  The
@@ -184,12 +197,12 @@ __device__ __forceinline__ int cfb_pos(const Bnd<T>& b, int sd, int q, T* xp_out
 // Eq. 5b: the coarse tangential E at level n (old line) interpolated in
 // space at the sample, lo, blended in time with the level-n+1 one from n0, n1
 // at coarse positions i0, i0 + 1.
-template <class T>
+template <class T, bool CG = false>
 __device__ __forceinline__ T cfb_old(const Bnd<T>& b, int sd, int i0, T xp) {
   const T one = T(1);
   const T* o = b.old_line[sd];
   const int s = b.stride[sd];
-  return o[i0 * s] * (one - xp) + o[(i0 + 1) * s] * xp;
+  return ldv<CG>(o + i0 * s) * (one - xp) + ldv<CG>(o + (i0 + 1) * s) * xp;
 }
 
 template <class T>
@@ -292,7 +305,7 @@ __device__ __forceinline__ void em_set_level(EmArgs<T>& A, long long m, int k) {
 // coarse step (recompute) the coarse E^{n+1} at the positions the block's
 // samples use is evaluated once per position into shared memory, then
 // blended; later sub-steps read the stored level-n+1 line.
-template <class T>
+template <class T, bool CG = false>
 __device__ __forceinline__ void em_cfb(const EmArgs<T>& A, int blk) {
   constexpr int NTH = 32 * EM_WARPS;
   __shared__ T cn[NTH + 2];
@@ -311,18 +324,18 @@ __device__ __forceinline__ void em_cfb(const EmArgs<T>& A, int blk) {
   const int q = qa + (int)threadIdx.x;
   T xp = T(0);
   const int i0 = cfb_pos(A.b, sd, min(q, qb), &xp);
-  const T lo = cfb_old(A.b, sd, i0, xp);        // in flight during the recompute
+  const T lo = cfb_old<T, CG>(A.b, sd, i0, xp);        // in flight during the recompute
   T v;
   if (A.b.recompute) {
     T xa;
     const int c0 = cfb_pos(A.b, sd, qa, &xa), c1 = cfb_pos(A.b, sd, qb, &xa) + 1;
-    for (int t = threadIdx.x; t <= c1 - c0; t += NTH) cn[t] = coarse_new(A.b, sd, c0 + t);
+    for (int t = threadIdx.x; t <= c1 - c0; t += NTH) cn[t] = coarse_new<T, CG>(A.b, sd, c0 + t);
     __syncthreads();
     v = cfb_blend(A.b, lo, xp, cn[i0 - c0], cn[i0 + 1 - c0]);
   } else {
     const T* nl = A.b.new_line[sd];
     const int s = A.b.stride[sd];
-    v = cfb_blend(A.b, lo, xp, nl[i0 * s], nl[(i0 + 1) * s]);
+    v = cfb_blend(A.b, lo, xp, ldv<CG>(nl + i0 * s), ldv<CG>(nl + (i0 + 1) * s));
   }
   if (q > qb) return;
   if (sd == SIDE_BOTTOM) A.dEx[q] = v;
@@ -331,7 +344,7 @@ __device__ __forceinline__ void em_cfb(const EmArgs<T>& A, int blk) {
   else A.dEy[q * p + nfx] = v;
 }
 
-template <class T, bool PML, bool WR>
+template <class T, bool PML, bool WR, bool CG>
 __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk);
 
 // Blocks of one mesh's EM step: the coarse-fine side blocks first (the
@@ -340,13 +353,14 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk);
 // PML: compile the CPML terms in (coarse launches of CPML runs only)
 // WR: compile the producer-side fine->coarse transfer in (launches of the
 // last fine sub-step of a coarse step only)
-template <class T, bool PML = false, bool WR = false>
+// CG: loads through L2 only (the persistent period kernel)
+template <class T, bool PML = false, bool WR = false, bool CG = false>
 __device__ __forceinline__ void em_segment(const EmArgs<T>& A, int blk) {
-  if (blk < A.ncfb) em_cfb(A, blk);
-  else em_strips<T, PML, WR>(A, blk - A.ncfb);
+  if (blk < A.ncfb) em_cfb<T, CG>(A, blk);
+  else em_strips<T, PML, WR, CG>(A, blk - A.ncfb);
 }
 
-template <class T, bool PML, bool WR>
+template <class T, bool PML, bool WR, bool CG>
 __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
   const Mesh<T>& m = A.m;
   T* __restrict__ dEx = A.dEx;
@@ -367,6 +381,15 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
   if (j0 > ny) return;                       // whole warp leaves together
   const int j1 = min(j0 + rows, ny + 1);     // node rows [j0, j1)
   const bool own = lane >= 1 && lane <= sw && i <= nx;
+  // persistent period, coarse step: edges the last fine sub-step restricts
+  // are left to it (only CG code reads the box)
+  const RestrW<T>& Wk = A.W;
+  auto keep_ex = [&](int ii, int jj) {
+    return !(CG && Wk.skip && ii >= Wk.I0 && ii < Wk.I1 && jj >= Wk.jlo && jj <= Wk.jhi);
+  };
+  auto keep_ey = [&](int ii, int jj) {
+    return !(CG && Wk.skip && ii >= Wk.ilo && ii <= Wk.ihi && jj >= Wk.J0 && jj < Wk.J1);
+  };
   // CPML (warp-uniform): the strip's columns or rows reach into the layer
   const Pml<T>& P = A.pml;
   const int c0 = bx * sw;
@@ -379,22 +402,22 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
   const T inc0 = incident(c, 0), incn = incident(c, nx);
   // ---- carried state for row j: Ex^n(j), Ex^n(j-1), Ey^n(j-1), Hz^{n+1/2}(j-1), n(j)
   T exc = T(0), exp_ = T(0), eyp = T(0), hzp = T(0), nc = T(0);
-  if (xcol) exc = load_ex(m, i, j0);
+  if (xcol) exc = load_ex<T, CG>(m, i, j0);
   if (ycol) nc = m.n[j0 * p + i];
   if (j0 > 0) {
     // H of row j0-1, needed by the Ex update of row j0
     const int jm = j0 - 1;
-    const T exm = xcol ? load_ex(m, i, jm) : T(0);
-    const T eym = ycol ? load_ey(m, i, jm) : T(0);
-    const T hzo = xcol ? m.Hz[jm * p + i] : T(0);
+    const T exm = xcol ? load_ex<T, CG>(m, i, jm) : T(0);
+    const T eym = ycol ? load_ey<T, CG>(m, i, jm) : T(0);
+    const T hzo = xcol ? ldv<CG>(m.Hz + jm * p + i) : T(0);
     const T eyr = __shfl_down_sync(0xffffffffu, eym, 1);
     if (xcol) {
       if (pw) {
         // the CPML-corrected H of row j0-1 (its owner stores psi)
         const int q = jm * p + i;
         const T dey = eyr - eym, dex = exc - exm;
-        const T px = P.bxh[i] * P.hx[q] + P.cxh[i] * dey;
-        const T py = P.byh[jm] * P.hy[q] + P.cyh[jm] * dex;
+        const T px = P.bxh[i] * ldv<CG>(P.hx + q) + P.cxh[i] * dey;
+        const T py = P.byh[jm] * ldv<CG>(P.hy + q) + P.cyh[jm] * dex;
         hzp = hzo - c.ch * ((dey + px) - (dex + py));
       } else {
         hzp = hzo - c.ch * ((eyr - eym) - (exc - exm));
@@ -409,13 +432,13 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
     Row q;
     const int id = j * p + i;
     const bool in = j < ny;
-    q.exn = (xcol && in) ? load_ex(m, i, j + 1) : T(0);
-    q.eyc = (ycol && in) ? load_ey(m, i, j) : T(0);
-    q.hzo = (xcol && in) ? m.Hz[id] : T(0);
-    q.vxo = xcol ? m.vx[id] : T(0);
-    q.vyo = (ycol && in) ? m.vy[id] : T(0);
+    q.exn = (xcol && in) ? load_ex<T, CG>(m, i, j + 1) : T(0);
+    q.eyc = (ycol && in) ? load_ey<T, CG>(m, i, j) : T(0);
+    q.hzo = (xcol && in) ? ldv<CG>(m.Hz + id) : T(0);
+    q.vxo = xcol ? ldv<CG>(m.vx + id) : T(0);
+    q.vyo = (ycol && in) ? ldv<CG>(m.vy + id) : T(0);
     q.nn = (ycol && in) ? m.n[id + p] : T(0);
-    q.s2 = (c.accum && own) ? m.S2[id] : 0.0;
+    q.s2 = (c.accum && own) ? ldv<CG>(m.S2 + id) : 0.0;
     return q;
   };
   Row nxt = load_row(j0);
@@ -444,8 +467,8 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
     if (xcol && j < ny) {
       if (pw) {
         const T dey = eyr - eyc, dex = exn - exc;
-        const T px = P.bxh[i] * P.hx[id] + P.cxh[i] * dey;
-        const T py = P.byh[j] * P.hy[id] + P.cyh[j] * dex;
+        const T px = P.bxh[i] * ldv<CG>(P.hx + id) + P.cxh[i] * dey;
+        const T py = P.byh[j] * ldv<CG>(P.hy + id) + P.cyh[j] * dex;
         if (own) {
           P.dhx[id] = px;
           P.dhy[id] = py;
@@ -484,24 +507,24 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
           T en;
           if (pw) {
             const T dh = hz - hzp;
-            const T pe = P.byn[j] * P.exy[id] + P.cyn[j] * dh;
+            const T pe = P.byn[j] * ldv<CG>(P.exy + id) + P.cyn[j] * dh;
             P.dexy[id] = pe;
             en = exc + c.ce * (dh + pe) + c.cj * (nc + ncr) * v;
           } else {
             en = exc + c.ce * (hz - hzp) + c.cj * (nc + ncr) * v;
           }
-          dEx[id] = en;
+          if (keep_ex(i, j)) dEx[id] = en;
           exw = en;
           if (j == 1 && b.mode[SIDE_BOTTOM] == BC_MUR) {
-            dvx[i] = c.va * m.vx[i] - c.vb * exp_;
+            dvx[i] = c.va * ldv<CG>(m.vx + i) - c.vb * exp_;
             exw0 = exc + c.mur * (en - exp_);
-            dEx[i] = exw0;
+            if (keep_ex(i, 0)) dEx[i] = exw0;
           }
           if (j == ny - 1 && b.mode[SIDE_TOP] == BC_MUR) {
             const int ib = ny * p + i;
-            dvx[ib] = c.va * m.vx[ib] - c.vb * exn;
+            dvx[ib] = c.va * ldv<CG>(m.vx + ib) - c.vb * exn;
             exwN = exc + c.mur * (en - exn);
-            dEx[ib] = exwN;
+            if (keep_ex(i, ny)) dEx[ib] = exwN;
           }
         } else {
           const int sd = (j == 0) ? SIDE_BOTTOM : SIDE_TOP;
@@ -520,25 +543,25 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
           T en;
           if (pw) {
             const T dh = hz - hzl;
-            const T pe = P.bxn[i] * P.eyx[id] + P.cxn[i] * dh;
+            const T pe = P.bxn[i] * ldv<CG>(P.eyx + id) + P.cxn[i] * dh;
             P.deyx[id] = pe;
             en = eyc - c.ce * (dh + pe) + c.cj * (nc + nn) * v;
           } else {
             en = eyc - c.ce * (hz - hzl) + c.cj * (nc + nn) * v;
           }
-          dEy[id] = en;
+          if (keep_ey(i, j)) dEy[id] = en;
           eyw = en;
           if (i == 1 && b.mode[SIDE_LEFT] == BC_MUR) {
             const int ib = j * p;
             dvy[ib] = c.va * vyl - c.vb * (eyl + inc0);
             eywL = eyc + c.mur * (en - eyl);
-            dEy[ib] = eywL;
+            if (keep_ey(0, j)) dEy[ib] = eywL;
           }
           if (i == nx - 1 && b.mode[SIDE_RIGHT] == BC_MUR) {
             const int ib = j * p + nx;
             dvy[ib] = c.va * vyr - c.vb * (eyr + incn);
             eywR = eyc + c.mur * (en - eyr);
-            dEy[ib] = eywR;
+            if (keep_ey(nx, j)) dEy[ib] = eywR;
           }
         } else {
           const int sd = (i == 0) ? SIDE_LEFT : SIDE_RIGHT;
@@ -577,7 +600,12 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
         sey[wq][lane] = eyw;
         if (own && i == 1) slr[wq][0] = eywL;
         if (own && i == nx - 1) slr[wq][1] = eywR;
-        asm volatile("bar.sync %0, %1;" :: "r"(1 + w0 / rw), "r"(32 * rw) : "memory");
+        // immediate barrier ids: the block then reserves barriers 0..2 only,
+        // not all sixteen, which would cap the blocks resident on an SM
+        static_assert(EM_WARPS == 4, "r = 2: two groups of two warps; r = 4: one group of four");
+        if (rw == 4) asm volatile("bar.sync 1, 128;" ::: "memory");
+        else if (w0 == 0) asm volatile("bar.sync 1, 64;" ::: "memory");
+        else asm volatile("bar.sync 2, 64;" ::: "memory");
         if (jq == rw - 1) {
           eacc = sey[w0][lane];
           for (int q = 1; q < rw; ++q) eacc = eacc + sey[w0 + q][lane];
@@ -797,6 +825,8 @@ struct PeArgs {
   uint8_t* mask;
   Ctl* ctl;
   double dxc2, dxf2, period;   // cell areas, EM period
+  unsigned* sched;             // the persistent period's counters and flags, cleared here
+  int nsched;
 };
 
 // node (i, j) of mesh-block b of a PeMesh (false past the mesh)
@@ -878,6 +908,9 @@ __global__ void __launch_bounds__(TX * TY) k_pe_rates(PeArgs<T> A) {
     ctl->bbox[2] = -1; ctl->bbox[3] = -1;
     ctl->nflag = 0; ctl->st[4] = 0.0; ctl->side = 0; ctl->done = 0u;
   }
+  // the persistent period launch that may follow starts from zero counts
+  for (int k = b * (TX * TY) + threadIdx.y * TX + threadIdx.x; k < A.nsched; k += gridDim.x * TX * TY)
+    A.sched[k] = 0u;
   const bool fine = b >= A.C.nb;
   const PeMesh<T>& M = fine ? A.F : A.C;
   const int mb = fine ? b - A.C.nb : b;

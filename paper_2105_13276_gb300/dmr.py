@@ -77,6 +77,8 @@ def load():
         "dmr_stats": (c_int, [P, POINTER(c_double)]),
         "dmr_set_graphs": (c_int, [P, c_int]),
         "dmr_set_launch_shape": (c_int, [P, c_int32]),
+        "dmr_set_persistent": (c_int, [P, c_int, c_int32, c_int32]),
+        "dmr_test_stall": (c_int, [P, c_int, c_int64]),
         "dmr_set_timing": (c_int, [P, c_int]),
         "dmr_kernel_time": (c_int, [P, c_int, POINTER(c_double), POINTER(c_int64),
                                     POINTER(c_double)]),
@@ -223,6 +225,14 @@ class Run:
 
     def set_graphs(self, on=True):
         self._check(self.lib.dmr_set_graphs(self.ctx, int(bool(on))))
+
+    def set_persistent(self, on=True, rows_coarse=0, rows_fine=0):
+        """Each full period's EM steps in one persistent launch (same results)."""
+        self._check(self.lib.dmr_set_persistent(self.ctx, int(bool(on)), int(rows_coarse), int(rows_fine)))
+
+    def test_stall(self, on=True, polls=1 << 22):
+        """Test of the persistent launch's bounded waits (see dmr.h)."""
+        self._check(self.lib.dmr_test_stall(self.ctx, int(bool(on)), int(polls)))
 
     def set_launch_shape(self, warps_per_sm):
         """Strip height of the EM launches as a warps-per-SM target."""
