@@ -1506,8 +1506,8 @@ struct Engine final : Base {
 
   size_t adj_fixed_bytes() const {
     const size_t mx = std::max(L.cplane, L.fplane);
-    size_t b = 10 * up(cplane_b(), 256);                          // coarse adjoints
-    if (cfg.r > 1) b += 2 * 10 * up(L.fplane * L.es, 256);        // fine adjoints, two layouts
+    size_t b = 11 * up(cplane_b(), 256);                          // coarse adjoints
+    if (cfg.r > 1) b += 2 * 11 * up(L.fplane * L.es, 256);        // fine adjoints, two layouts
     b += 6 * up(mx * L.es, 256);                                  // continuity-step scratch
     b += 256;                                                     // FP64 sums
     b += 4 * side_line_bytes();                                   // Eq. 5b^T E^n shares
@@ -1596,7 +1596,10 @@ struct Engine final : Base {
   // (the coarse step with the first fine sub-step, then sub-steps 2..r) with
   // the tape copies queued after each and flushed before any launch that
   // overwrites their sources (double buffering keeps the inputs of a launch
-  // until the launch after it)
+  // until the launch after it).  At r = 2 one flush per coarse step, before
+  // its first launch, covers all of them: the step's own inputs are queued
+  // ahead of it, and what the step leaves (v outputs, sub-step 2's inputs)
+  // stays intact until the next step's first launch.
   int record_step(StepRec* R) {
     const int r = cfg.r;
     R->m = m;
@@ -1604,30 +1607,42 @@ struct Engine final : Base {
     R->fine = has_fine;
     R->rvalid = rvalid;
     const int cp0 = cpar;
+    const bool one_flush = has_fine && r == 2;
+    const size_t fb = has_fine ? fplane_b(rect) : 0;
+    if (one_flush) {
+      R->cEx = tape_copy(C.Ex, cplane_b());          // E^n
+      R->cEy = tape_copy(C.Ey, cplane_b());
+      R->fEx.push_back(tape_copy(F[cur].Ex, fb));    // sub-step 1's input
+      R->fEy.push_back(tape_copy(F[cur].Ey, fb));
+      flush_tape();
+    }
     dmr::EmArgs<T> Ac, Af;
     em_args_for(1, m, cpar, fpar, rvalid, &Ac, has_fine ? &Af : nullptr);
     if (has_fine) go_em2(Ac.nblk + Ac.ncfb + Af.nblk + Af.ncfb, Ac, Af);
     else go_em(Ac.nblk + Ac.ncfb, Ac);
     counted(1);
-    R->cEx = tape_copy(C.Ex, cplane_b());        // E^n (this step's input parity)
-    R->cEy = tape_copy(C.Ey, cplane_b());
+    if (!one_flush) {
+      R->cEx = tape_copy(C.Ex, cplane_b());        // E^n (this step's input parity)
+      R->cEy = tape_copy(C.Ey, cplane_b());
+    }
     flip_coarse();
     R->cvx = tape_copy(C.vx, cplane_b());        // v^{n+1/2}
     R->cvy = tape_copy(C.vy, cplane_b());
     if (has_fine) {
-      const size_t fb = fplane_b(rect);
       for (int k = 1; k <= r; ++k) {
         if (k > 1) {
           em_args_for(k, m, cp0, fpar, rvalid, nullptr, &Af);
           go_em(Af.nblk + Af.ncfb, Af);
           counted(1);
         }
-        R->fEx.push_back(tape_copy(F[cur].Ex, fb));   // the sub-step's input
-        R->fEy.push_back(tape_copy(F[cur].Ey, fb));
+        if (!(one_flush && k == 1)) {
+          R->fEx.push_back(tape_copy(F[cur].Ex, fb));   // the sub-step's input
+          R->fEy.push_back(tape_copy(F[cur].Ey, fb));
+        }
         flip_fine();
         R->fvx.push_back(tape_copy(F[cur].vx, fb));   // its v output
         R->fvy.push_back(tape_copy(F[cur].vy, fb));
-        flush_tape();
+        if (!one_flush) flush_tape();
       }
       rvalid = true;
     } else {
@@ -1674,7 +1689,8 @@ struct Engine final : Base {
   // adjoint arrays of one mesh
   struct AdjArr {
     T* E[2][2];      // [buffer][x, y]
-    T *H, *vx, *vy, *n, *ntmp, *S2;
+    T *H, *H2;       // adjoint of the present H level; the other buffer of the pair
+    T *vx, *vy, *n, *ntmp, *S2;
   };
 
   dmr::Modes modes_of(const int* rc) const {
@@ -1690,7 +1706,7 @@ struct Engine final : Base {
     dmr::AdjM<T> A;
     A.aEx_in = a.E[in][0]; A.aEy_in = a.E[in][1];
     A.aEx_out = a.E[in ^ 1][0]; A.aEy_out = a.E[in ^ 1][1];
-    A.aHz = a.H; A.avx = a.vx; A.avy = a.vy; A.an = a.n; A.aS2 = a.S2;
+    A.aHz = a.H; A.aHz_out = a.H2; A.avx = a.vx; A.avy = a.vy; A.an = a.n; A.aS2 = a.S2;
     A.nx = nx; A.ny = ny; A.p = p;
     return A;
   }
@@ -1730,17 +1746,18 @@ struct Engine final : Base {
     auto take = [&](size_t b) { char* q = w + o; o += up(b, 256); return q; };
     AdjArr ca, fa[2];
     {
-      T* pl[10];
-      for (int k = 0; k < 10; ++k) pl[k] = (T*)take(cplane_b());
+      T* pl[11];
+      for (int k = 0; k < 11; ++k) pl[k] = (T*)take(cplane_b());
       ca.E[0][0] = pl[0]; ca.E[0][1] = pl[1]; ca.E[1][0] = pl[2]; ca.E[1][1] = pl[3];
       ca.H = pl[4]; ca.vx = pl[5]; ca.vy = pl[6]; ca.n = pl[7]; ca.ntmp = pl[8]; ca.S2 = pl[9];
+      ca.H2 = pl[10];
     }
     for (int sset = 0; sset < 2 && dmr_; ++sset) {
-      T* pl[10];
-      for (int k = 0; k < 10; ++k) pl[k] = (T*)take(L.fplane * L.es);
+      T* pl[11];
+      for (int k = 0; k < 11; ++k) pl[k] = (T*)take(L.fplane * L.es);
       fa[sset].E[0][0] = pl[0]; fa[sset].E[0][1] = pl[1]; fa[sset].E[1][0] = pl[2]; fa[sset].E[1][1] = pl[3];
       fa[sset].H = pl[4]; fa[sset].vx = pl[5]; fa[sset].vy = pl[6]; fa[sset].n = pl[7];
-      fa[sset].ntmp = pl[8]; fa[sset].S2 = pl[9];
+      fa[sset].ntmp = pl[8]; fa[sset].S2 = pl[9]; fa[sset].H2 = pl[10];
     }
     const size_t mx = std::max(L.cplane, L.fplane);
     T* sc[6];
@@ -1919,11 +1936,12 @@ struct Engine final : Base {
   // the four Eq. 5b^T line buffers of the present backward sweep
   T** adj_side = nullptr;
 
-  // Reverse of coarse step R.m in 2r + 2 launches: per fine sub-step (r..1)
-  // ka_hc (H^T with the Eq. 5b^T scatter) and ka_e; then the coarse ka_h and
-  // ka_e, which adds the Eq. 5b^T shares of the coarse E^n and transposes the
-  // fine->coarse transfer (a8) of the step before.  Every adjoint E edge is
-  // stored by one ka_e, so no buffer is cleared between steps.
+  // Reverse of coarse step R.m in r + 1 launches of ka_eh: per fine sub-step
+  // (r..1) H^T and E^T with the Eq. 5b^T scatter; then the coarse step's,
+  // which adds the Eq. 5b^T shares of the coarse E^n and transposes the
+  // fine->coarse transfer (a8) of the step before.  Every adjoint E edge and
+  // H cell is stored by one launch (E and H adjoints are double-buffered), so
+  // no buffer is cleared between steps.
   int adj_step(const StepRec& R, const PerRec& P, AdjArr& ca, AdjArr* fa, int& cin, int& fin,
                int fset, double* sums) {
     const int NT = cfg.steps_per_period, r = cfg.r;
@@ -1956,17 +1974,17 @@ struct Engine final : Base {
       for (int q = 0; q < 4; ++q)
         if (md.m[q] == dmr::BC_CFB) ncfb += (q == dmr::SIDE_BOTTOM || q == dmr::SIDE_TOP) ? fnx : fny;
       const dim3 gf = nodes_grid(fnx, fny);
-      const int nbh = (int)(gf.x * gf.y), nbc = (ncfb + BX * BY - 1) / (BX * BY);
+      const int nbe = (int)(gf.x * gf.y), nbc = (ncfb + BX * BY - 1) / (BX * BY);
       const dmr::CoarseT<T> none{};
       for (int k = r; k >= 1; --k) {
         const int64_t mf = (int64_t)r * R.m + (k - 1);
         const dmr::Step<T> sf = make_step_at(r, mf, (mf % ((int64_t)r * NT)) != 0, R.rect[0]);
         const dmr::AdjM<T> am = adjm(A, fin, fnx, fny, fp);
         cb.frac = (T)((double)k / (double)r);
-        dmr::ka_hc<T><<<nbh + nbc, blk, 0, st>>>(am, sf, md, cb, nbh, (int)gf.x);
         dmr::FwdM<T> fw;
         fw.Ex = R.fEx[k - 1]; fw.Ey = R.fEy[k - 1]; fw.vx = R.fvx[k - 1]; fw.vy = R.fvy[k - 1]; fw.n = P.nf;
-        dmr::ka_e<T><<<gf, blk, 0, st>>>(am, fw, sf, md, sums, none);
+        dmr::ka_eh<T><<<nbe + nbc, blk, 0, st>>>(am, fw, sf, md, sums, none, cb, nbe, (int)gf.x);
+        std::swap(A.H, A.H2);
         fin ^= 1;
       }
       if (R.rvalid) {
@@ -1985,10 +2003,11 @@ struct Engine final : Base {
     for (int q = 0; q < 4; ++q) mc.m[q] = dmr::BC_MUR;
     const dmr::AdjM<T> am = adjm(ca, cin, C.nx, C.ny, C.p);
     const dim3 gc = nodes_grid(C.nx, C.ny);
-    dmr::ka_h<T><<<gc, blk, 0, st>>>(am, sc, mc);
     dmr::FwdM<T> fw;
     fw.Ex = R.cEx; fw.Ey = R.cEy; fw.vx = R.cvx; fw.vy = R.cvy; fw.n = P.nc;
-    dmr::ka_e<T><<<gc, blk, 0, st>>>(am, fw, sc, mc, sums, ct);
+    const dmr::CfbT<T> cnone{};
+    dmr::ka_eh<T><<<gc.x * gc.y, blk, 0, st>>>(am, fw, sc, mc, sums, ct, cnone, (int)(gc.x * gc.y), (int)gc.x);
+    std::swap(ca.H, ca.H2);
     cin ^= 1;
     return launched("adjoint step");
   }

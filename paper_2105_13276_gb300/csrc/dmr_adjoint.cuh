@@ -42,7 +42,8 @@ template <class T>
 struct AdjM {
   const T *aEx_in, *aEy_in;   // adjoint of E^{l+1}
   T *aEx_out, *aEy_out;       // adjoint of E^l (accumulated with +=)
-  T* aHz;                     // adjoint of H^{l+1/2} in, of H^{l-1/2} out (in place)
+  const T* aHz;               // adjoint of H^{l+1/2} (ka_eh: before the step's own curl share)
+  T* aHz_out;                 // ka_eh: adjoint of H^{l-1/2} (the other buffer of the pair)
   T *avx, *avy;               // adjoint of v^{l+1/2} in, of v^{l-1/2} out (in place)
   T* an;                      // adjoint of n (accumulated)
   const T* aS2;               // adjoint of the period's S2 sum (nodes)
@@ -77,17 +78,16 @@ __device__ __forceinline__ T adj_y(const AdjM<T>& a, const Modes& md, T mur, int
   return v;
 }
 
-// aH += ce curlH^T(aE'), interior edges (after the Mur rows' share), at cell
-// (i, j).
+// The adjoint of H^{l-1/2} at cell (i, j): that of H^{l+1/2} plus
+// ce curlH^T(aE') over the interior edges (after the Mur rows' share).
 template <class T>
-__device__ __forceinline__ void ka_h_cell(const AdjM<T>& a, const Step<T>& c, const Modes& md, int i, int j) {
-  if (i >= a.nx || j >= a.ny) return;
+__device__ __forceinline__ T ka_h_value(const AdjM<T>& a, const Step<T>& c, const Modes& md, int i, int j) {
   T acc = T(0);
   if (j > 0) acc = acc + adj_x(a, md, c.mur, i, j);
   if (j + 1 < a.ny) acc = acc - adj_x(a, md, c.mur, i, j + 1);
   if (i > 0) acc = acc - adj_y(a, md, c.mur, i, j);
   if (i + 1 < a.nx) acc = acc + adj_y(a, md, c.mur, i + 1, j);
-  a.aHz[j * a.p + i] += c.ce * acc;
+  return a.aHz[j * a.p + i] + c.ce * acc;
 }
 
 __device__ __forceinline__ double block_sum_d(double v) { return block_sum(v); }
@@ -110,22 +110,26 @@ struct CoarseT {
   int fp;
 };
 
-// Node-wise gather of aE^l (edges (i,j)), av, an; E0 share summed in FP64
-// per block.  The edge adjoints of E^l are stored (the output buffer is not
-// cleared before); with a CoarseT the side shares are added and a8
-// transposed.  Every load of a thread comes before its first store, so the
-// loads of the in-place arrays (av, an, side lines) and of the read-only
-// inputs are all in flight at once.
+// Node (i, j) of a reversed EM step: the adjoint of H^{l-1/2} at cell (i, j)
+// (from the other H buffer, re-evaluated at the two neighbouring cells the
+// edges of the node need), then the gather of aE^l (edges (i, j)), av, an;
+// returns the node's E0 share.  The edge adjoints of E^l are stored (the
+// output buffer is not cleared before); with a CoarseT the side shares are
+// added and a8 transposed.  Every load of a thread comes before its first
+// store, so the loads of the in-place arrays (av, an, side lines) and of the
+// read-only inputs are all in flight at once.
 template <class T>
-__global__ void __launch_bounds__(TX * TY) ka_e(AdjM<T> a, FwdM<T> f, Step<T> c, Modes md, double* e0acc,
-                                                CoarseT<T> ct) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ T ka_e_node(const AdjM<T>& a, const FwdM<T>& f, const Step<T>& c, const Modes& md,
+                                       const CoarseT<T>& ct, int i, int j) {
   const int nx = a.nx, ny = a.ny, p = a.p;
   T e0 = T(0);
   if (i <= nx && j <= ny) {
     const int id = j * p + i;
     const bool xe = i < nx, ye = j < ny;
+    // ---- H adjoints of the cells the node's edges border
+    const T h00 = (xe && ye) ? ka_h_value(a, c, md, i, j) : T(0);
+    const T h0m = (xe && j > 0) ? ka_h_value(a, c, md, i, j - 1) : T(0);
+    const T hm0 = (ye && i > 0) ? ka_h_value(a, c, md, i - 1, j) : T(0);
     // ---- loads: in-place values and side lines
     const T avx0 = xe ? a.avx[id] : T(0);
     const T avy0 = ye ? a.avy[id] : T(0);
@@ -157,8 +161,8 @@ __global__ void __launch_bounds__(TX * TY) ka_e(AdjM<T> a, FwdM<T> f, Step<T> c,
       }
       out = out - c.vb * avt;
       T hs = T(0);
-      if (j < ny) hs = hs + a.aHz[id];
-      if (j > 0) hs = hs - a.aHz[id - p];
+      if (j < ny) hs = hs + h00;
+      if (j > 0) hs = hs - h0m;
       out = out - c.ch * hs;
       if (c.accum) {
         const T wl = (i > 0) ? T(0.5) : T(1);                 // node i: this is its right edge
@@ -191,8 +195,8 @@ __global__ void __launch_bounds__(TX * TY) ka_e(AdjM<T> a, FwdM<T> f, Step<T> c,
       out = out - c.vb * avt;
       e0 -= c.vb * avt * phi;
       T hs = T(0);
-      if (i < nx) hs = hs - a.aHz[id];
-      if (i > 0) hs = hs + a.aHz[id - 1];
+      if (i < nx) hs = hs - h00;
+      if (i > 0) hs = hs + hm0;
       out = out - c.ch * hs;
       if (c.accum) {
         const T ey = f.Ey[id] + c.E0 * phi;
@@ -209,6 +213,7 @@ __global__ void __launch_bounds__(TX * TY) ka_e(AdjM<T> a, FwdM<T> f, Step<T> c,
     }
     if (j > 0 && i > 0 && i < nx) an_acc = an_acc + f.vy[id - p] * adj_y(a, md, c.mur, i, j - 1);
     // ---- stores
+    if (xe && ye) a.aHz_out[id] = h00;
     a.an[id] = an0 + c.cj * an_acc;
     if (xe) {
       a.avx[id] = avx1;
@@ -235,8 +240,7 @@ __global__ void __launch_bounds__(TX * TY) ka_e(AdjM<T> a, FwdM<T> f, Step<T> c,
       a.aEy_out[id] = outy;
     }
   }
-  const double s = block_sum_d((double)e0);
-  if (threadIdx.x == 0 && threadIdx.y == 0 && s != 0.0) atomicAdd(e0acc, s);
+  return e0;
 }
 
 // Eq. 5b^T: the adjoint of each coarse-fine boundary edge of the fine mesh goes
@@ -297,25 +301,22 @@ __device__ __forceinline__ void ka_cfb_sample(const AdjM<T>& a, const CfbT<T>& b
   ka_cfb_side<SIDE_RIGHT>(a, b, q);
 }
 
-// One launch per reversed fine sub-step before ka_e: ka_h over the mesh's
-// cells (the first nbh blocks, TX x TY cells each, gx across), then Eq. 5b^T
-// over the coarse-fine side samples (TX * TY per block).  The two are
-// independent: ka_h writes aH, the samples read aE' and write coarse adjoints.
+// One launch per reversed EM step of one mesh: the node blocks (the first
+// nbe blocks, TX x TY nodes each, gx across; ka_e_node, E0 share summed per
+// block in FP64), then on a fine mesh the Eq. 5b^T side samples (TX * TY per
+// block), which read aE' and add to the coarse adjoints only.
 template <class T>
-__global__ void __launch_bounds__(TX * TY) ka_hc(AdjM<T> a, Step<T> c, Modes md, CfbT<T> b, int nbh, int gx) {
+__global__ void __launch_bounds__(TX * TY) ka_eh(AdjM<T> a, FwdM<T> f, Step<T> c, Modes md, double* e0acc,
+                                                 CoarseT<T> ct, CfbT<T> cb, int nbe, int gx) {
   const int blk = (int)blockIdx.x;
-  if (blk < nbh) {
-    const int by = blk / gx, bx = blk - by * gx;
-    ka_h_cell(a, c, md, bx * TX + (int)threadIdx.x, by * TY + (int)threadIdx.y);
-  } else {
-    ka_cfb_sample(a, b, (blk - nbh) * TX * TY + (int)(threadIdx.y * TX + threadIdx.x));
+  if (blk >= nbe) {
+    ka_cfb_sample(a, cb, (blk - nbe) * TX * TY + (int)(threadIdx.y * TX + threadIdx.x));
+    return;
   }
-}
-
-// The coarse mesh's ka_h (no side samples).
-template <class T>
-__global__ void __launch_bounds__(TX * TY) ka_h(AdjM<T> a, Step<T> c, Modes md) {
-  ka_h_cell(a, c, md, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
+  const int by = blk / gx, bx = blk - by * gx;
+  const T e0 = ka_e_node(a, f, c, md, ct, bx * TX + (int)threadIdx.x, by * TY + (int)threadIdx.y);
+  const double s = block_sum_d((double)e0);
+  if (threadIdx.x == 0 && threadIdx.y == 0 && s != 0.0) atomicAdd(e0acc, s);
 }
 
 // a8^T for E: the adjoint of a restricted coarse edge goes to its r fine edges
