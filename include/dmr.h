@@ -323,7 +323,10 @@ int dmr_load_state(dmr_ctx* ctx, const void* dev_src, size_t bytes);
  *     of dmr_adjoint_workspace_bytes (valid after step 1).  For each segment,
  *     last first, it restores the checkpoint, recomputes the segment with the
  *     recorded rectangles while writing every step's E and v to a tape, and
- *     sweeps the tape backwards with the adjoint kernels.  It writes dL/dE0,
+ *     sweeps the tape backwards with the adjoint kernels; the recompute of
+ *     the next segment (on a stream the call creates and destroys) runs
+ *     while the sweep of the present one reads the other of two tapes.  The
+ *     call returns after all its work is done.  It writes dL/dE0,
  *     dL/ds_nu (host doubles) and dL/d(seed map) (device, dense rows x cols of
  *     the initial fine rectangle's nodes, the run's precision).  Afterwards
  *     the run holds the state at the end of its first recorded segment.

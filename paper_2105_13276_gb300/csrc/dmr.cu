@@ -1524,7 +1524,7 @@ struct Engine final : Base {
     size_t mx = 0;
     for (int64_t p0 = 0; p0 < periods; p0 += ppseg)
       mx = std::max(mx, seg_tape_bytes(p0, std::min(ppseg, periods - p0)));
-    return adj_fixed_bytes() + mx;
+    return adj_fixed_bytes() + 2 * mx;   // two segment tapes (recompute and sweep overlap)
   }
 
   struct StepRec {
@@ -1766,8 +1766,11 @@ struct Engine final : Base {
     T* side_lines[4];
     for (int k = 0; k < 4; ++k) side_lines[k] = (T*)take(side_line_bytes());
     adj_side = side_lines;
-    tape = w + o;
-    tape_cap = bytes - o;
+    // two segment tapes: the recompute of segment sg - 1 (on a stream of its
+    // own) runs while the reverse sweep of segment sg (on the run's stream)
+    // reads the other tape
+    const size_t tseg = ((bytes - o) / 2) & ~(size_t)255;
+    char* tapes[2] = {w + o, w + o + tseg};
     if (int s_ = ck(cudaMemsetAsync(w, 0, o, st), "zero adjoints")) return s_;
     // dL/dn at the end (dense coarse map) -> pitched adjoint of the coarse density
     if (int s_ = ck(cudaMemcpy2DAsync(ca.n, (size_t)C.p * L.es, dLdn, (size_t)(C.nx + 1) * L.es,
@@ -1784,36 +1787,62 @@ struct Engine final : Base {
     const int nseg = (int)rec.ck.size();
     const dmr::Dens dc = make_dens(1), df = make_dens(r);
     const double A1 = (d.nu_model == 1 ? d.town_A : 5.14e11) * cfg.p_torr;   // d nu_i / d s_nu, per unit
-    int st_ = DMR_OK;
-    for (int sg = nseg - 1; sg >= 0 && !st_; --sg) {
-      // ---- restore the segment's start and recompute it onto the tape
-      if ((st_ = ck(cudaMemcpyAsync(ws, rec.ckpt + (size_t)sg * wbytes(), L.total,
-                                    cudaMemcpyDeviceToDevice, st), "restore checkpoint"))) break;
-      load_host(rec.ck[sg]);
-      const int64_t p0 = (int64_t)sg * ppseg;
-      const int64_t periods = std::min<int64_t>(ppseg, rec.n / NT - p0);
-      replay.assign(rec.log.begin() + p0 * 4, rec.log.begin() + (p0 + periods) * 4);
-      replay_pos = 0;
+    const cudaStream_t sr = st;
+    cudaStream_t sq = nullptr;
+    cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr}, ev_go = nullptr;
+    int st_ = ck(cudaStreamCreateWithFlags(&sq, cudaStreamNonBlocking), "recompute stream");
+    for (int k = 0; k < 2 && !st_; ++k) {
+      st_ = ck(cudaEventCreateWithFlags(&ev_rec[k], cudaEventDisableTiming), "event");
+      if (!st_) st_ = ck(cudaEventCreateWithFlags(&ev_rev[k], cudaEventDisableTiming), "event");
+    }
+    if (!st_) st_ = ck(cudaEventCreateWithFlags(&ev_go, cudaEventDisableTiming), "event");
+    // the recompute stream starts after everything queued on the run's stream
+    if (!st_) st_ = ck(cudaEventRecord(ev_go, sr), "event record");
+    if (!st_) st_ = ck(cudaStreamWaitEvent(sq, ev_go, 0), "stream wait");
+    std::vector<StepRec> steps[2];
+    std::vector<PerRec> pers[2];
+    // restore segment sg's start and recompute it onto tape sg & 1, on sq
+    auto recompute = [&](int sg) -> int {
+      const int b = sg & 1;
+      st = sq;
+      tape = tapes[b];
+      tape_cap = tseg;
       tape_used = 0;
       tape_over = false;
-      std::vector<StepRec> steps;
-      std::vector<PerRec> pers;
-      for (int64_t pp = 0; pp < periods && !st_; ++pp) {
-        for (int q = 0; q < NT && !st_; ++q) {
-          steps.emplace_back();
-          st_ = record_step(&steps.back());
+      int s_ = ck(cudaMemcpyAsync(ws, rec.ckpt + (size_t)sg * wbytes(), L.total, cudaMemcpyDeviceToDevice, st),
+                  "restore checkpoint");
+      if (!s_) {
+        load_host(rec.ck[sg]);
+        const int64_t p0 = (int64_t)sg * ppseg;
+        const int64_t periods = std::min<int64_t>(ppseg, rec.n / NT - p0);
+        replay.assign(rec.log.begin() + p0 * 4, rec.log.begin() + (p0 + periods) * 4);
+        replay_pos = 0;
+        steps[b].clear();
+        pers[b].clear();
+        for (int64_t pp = 0; pp < periods && !s_; ++pp) {
+          for (int q = 0; q < NT && !s_; ++q) {
+            steps[b].emplace_back();
+            s_ = record_step(&steps[b].back());
+          }
+          if (s_) break;
+          pers[b].emplace_back();
+          s_ = record_period(&pers[b].back());
         }
-        if (st_) break;
-        pers.emplace_back();
-        st_ = record_period(&pers.back());
       }
-      if (st_) break;
-      if (tape_over) { st_ = fail(DMR_ECAPACITY, "adjoint tape overflow"); break; }
-      if (fset < 0) fset = cur;
+      if (!s_ && tape_over) s_ = fail(DMR_ECAPACITY, "adjoint tape overflow");
+      if (!s_) s_ = ck(cudaEventRecord(ev_rec[b], sq), "event record");
+      st = sr;
+      return s_;
+    };
+    if (!st_) st_ = recompute(nseg - 1);
+    if (!st_) fset = cur;
+    for (int sg = nseg - 1; sg >= 0 && !st_; --sg) {
+      const int b = sg & 1;
+      if ((st_ = ck(cudaStreamWaitEvent(sr, ev_rec[b], 0), "stream wait"))) break;
       // ---- reverse sweep over the segment
-      for (int64_t idx = (int64_t)steps.size() - 1; idx >= 0 && !st_; --idx) {
-        const StepRec& R = steps[idx];
-        const PerRec& P = pers[idx / NT];
+      for (int64_t idx = (int64_t)steps[b].size() - 1; idx >= 0 && !st_; --idx) {
+        const StepRec& R = steps[b][idx];
+        const PerRec& P = pers[b][idx / NT];
         if ((idx + 1) % NT == 0) {
           // period end at level P.L (forward order: restriction, S2 sample,
           // continuity steps, commit, growth)
@@ -1839,7 +1868,25 @@ struct Engine final : Base {
         // ---- coarse step R.m: fine sub-steps r..1, then the coarse step
         st_ = adj_step(R, P, ca, fa, cin, fin, fset, sums);
       }
+      if (st_) break;
+      if ((st_ = ck(cudaEventRecord(ev_rev[b], sr), "event record"))) break;
+      if (sg > 0) {
+        // the next segment's tape is free once the sweep that read it is done
+        // (no wait before the first use: an event never recorded has completed)
+        if ((st_ = ck(cudaStreamWaitEvent(sq, ev_rev[(sg - 1) & 1], 0), "stream wait"))) break;
+        st_ = recompute(sg - 1);
+      }
     }
+    st = sr;
+    if (sq) {
+      cudaStreamSynchronize(sq);
+      cudaStreamDestroy(sq);
+    }
+    for (int k = 0; k < 2; ++k) {
+      if (ev_rec[k]) cudaEventDestroy(ev_rec[k]);
+      if (ev_rev[k]) cudaEventDestroy(ev_rev[k]);
+    }
+    if (ev_go) cudaEventDestroy(ev_go);
     // seed map gradient: initial fine density (+ the coarse nodes it was copied to)
     if (!st_) {
       const HostState& h0 = rec.ck[0];
@@ -1936,6 +1983,15 @@ struct Engine final : Base {
   // the four Eq. 5b^T line buffers of the present backward sweep
   T** adj_side = nullptr;
 
+  // a reversed EM step (ka_eh).  Programmatic dependent launches were
+  // measured slower here: the early blocks hold SM slots that the segment
+  // recompute on the other stream needs.
+  void go_ka_eh(int nb, const dmr::AdjM<T>& am, const dmr::FwdM<T>& fw, const dmr::Step<T>& s_,
+                const dmr::Modes& md, double* sums, const dmr::CoarseT<T>& ct, const dmr::CfbT<T>& cb, int nbe,
+                int gx) const {
+    dmr::ka_eh<T><<<nb, dim3(BX, BY), 0, st>>>(am, fw, s_, md, sums, ct, cb, nbe, gx);
+  }
+
   // Reverse of coarse step R.m in r + 1 launches of ka_eh: per fine sub-step
   // (r..1) H^T and E^T with the Eq. 5b^T scatter; then the coarse step's,
   // which adds the Eq. 5b^T shares of the coarse E^n and transposes the
@@ -1983,7 +2039,7 @@ struct Engine final : Base {
         cb.frac = (T)((double)k / (double)r);
         dmr::FwdM<T> fw;
         fw.Ex = R.fEx[k - 1]; fw.Ey = R.fEy[k - 1]; fw.vx = R.fvx[k - 1]; fw.vy = R.fvy[k - 1]; fw.n = P.nf;
-        dmr::ka_eh<T><<<nbe + nbc, blk, 0, st>>>(am, fw, sf, md, sums, none, cb, nbe, (int)gf.x);
+        go_ka_eh(nbe + nbc, am, fw, sf, md, sums, none, cb, nbe, (int)gf.x);
         std::swap(A.H, A.H2);
         fin ^= 1;
       }
@@ -2006,7 +2062,7 @@ struct Engine final : Base {
     dmr::FwdM<T> fw;
     fw.Ex = R.cEx; fw.Ey = R.cEy; fw.vx = R.cvx; fw.vy = R.cvy; fw.n = P.nc;
     const dmr::CfbT<T> cnone{};
-    dmr::ka_eh<T><<<gc.x * gc.y, blk, 0, st>>>(am, fw, sc, mc, sums, ct, cnone, (int)(gc.x * gc.y), (int)gc.x);
+    go_ka_eh((int)(gc.x * gc.y), am, fw, sc, mc, sums, ct, cnone, (int)(gc.x * gc.y), (int)gc.x);
     std::swap(ca.H, ca.H2);
     cin ^= 1;
     return launched("adjoint step");
