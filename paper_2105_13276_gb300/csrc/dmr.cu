@@ -1983,86 +1983,119 @@ struct Engine final : Base {
   // the four Eq. 5b^T line buffers of the present backward sweep
   T** adj_side = nullptr;
 
-  // a reversed EM step (ka_eh).  Programmatic dependent launches were
-  // measured slower here: the early blocks hold SM slots that the segment
-  // recompute on the other stream needs.
-  void go_ka_eh(int nb, const dmr::AdjM<T>& am, const dmr::FwdM<T>& fw, const dmr::Step<T>& s_,
-                const dmr::Modes& md, double* sums, const dmr::CoarseT<T>& ct, const dmr::CfbT<T>& cb, int nbe,
-                int gx) const {
-    dmr::ka_eh<T><<<nb, dim3(BX, BY), 0, st>>>(am, fw, s_, md, sums, ct, cb, nbe, gx);
+  // one reversed-step launch: part P0 (and its mesh's side samples), then P1.
+  // Programmatic dependent launches were measured slower here: the early
+  // blocks hold SM slots that the segment recompute on the other stream needs.
+  void go_ka_eh(const dmr::NodePart<T>& P0, int nb0, const dmr::CfbT<T>& cb, int ncfb, const dmr::NodePart<T>& P1,
+                int nb1, double* sums) const {
+    dmr::ka_eh<T><<<nb0 + ncfb + nb1, dim3(BX, BY), 0, st>>>(P0, P1, cb, nb0, ncfb, sums);
   }
 
   // Reverse of coarse step R.m in r + 1 launches of ka_eh: per fine sub-step
-  // (r..1) H^T and E^T with the Eq. 5b^T scatter; then the coarse step's,
-  // which adds the Eq. 5b^T shares of the coarse E^n and transposes the
-  // fine->coarse transfer (a8) of the step before.  Every adjoint E edge and
-  // H cell is stored by one launch (E and H adjoints are double-buffered), so
-  // no buffer is cleared between steps.
+  // (r..1) H^T and E^T with the Eq. 5b^T scatter; then the coarse nodes
+  // within 2 nodes of the rectangle, which add the Eq. 5b^T shares of the
+  // coarse E^n and transpose the fine->coarse transfer (a8) of the step
+  // before.  The other coarse nodes neither read what the fine sub-steps of
+  // this step write nor write what they read, so they run inside the launches
+  // of fine sub-steps r and 1 (half of their block rows each).  Every adjoint
+  // E edge and H cell is stored by one launch (E and H adjoints are
+  // double-buffered), so no buffer is cleared between steps.
   int adj_step(const StepRec& R, const PerRec& P, AdjArr& ca, AdjArr* fa, int& cin, int& fin,
                int fset, double* sums) {
     const int NT = cfg.steps_per_period, r = cfg.r;
-    const dim3 blk(BX, BY);
+    const dim3 gc = nodes_grid(C.nx, C.ny);
+    dmr::NodePart<T> Pc{};   // the coarse step's node blocks, all of them
+    Pc.a = adjm(ca, cin, C.nx, C.ny, C.p);
+    Pc.f.Ex = R.cEx; Pc.f.Ey = R.cEy; Pc.f.vx = R.cvx; Pc.f.vy = R.cvy; Pc.f.n = P.nc;
+    Pc.c = make_step(1, R.m, (R.m % NT) != 0);
+    for (int q = 0; q < 4; ++q) Pc.md.m[q] = dmr::BC_MUR;
+    Pc.nbx = (int)gc.x;
+    Pc.nby = (int)gc.y;
+    Pc.sx0 = Pc.sy0 = 1;     // nothing skipped
+    Pc.sx1 = Pc.sy1 = 0;
+    const dmr::CfbT<T> cnone{};
+    const dmr::NodePart<T> empty{};
+    if (!R.fine) {
+      go_ka_eh(Pc, Pc.nbx * Pc.nby, cnone, 0, empty, 0, sums);
+      std::swap(ca.H, ca.H2);
+      cin ^= 1;
+      return launched("adjoint step");
+    }
+    int fnx, fny, fp;
+    fdims(R.rect, &fnx, &fny, &fp);
+    AdjArr& A = fa[fset];
+    const dmr::Modes md = modes_of(R.rect);
+    dmr::CfbT<T> cb{};
     dmr::CoarseT<T> ct{};
-    if (R.fine) {
-      int fnx, fny, fp;
-      fdims(R.rect, &fnx, &fny, &fp);
-      AdjArr& A = fa[fset];
-      const dmr::Modes md = modes_of(R.rect);
-      dmr::CfbT<T> cb{};
-      for (int q = 0; q < 4; ++q) {
-        cb.mode[q] = md.m[q];
-        if (q == dmr::SIDE_BOTTOM || q == dmr::SIDE_TOP) {
-          cb.start[q] = R.rect[0]; cb.len[q] = cfg.nx; cb.at[q] = q == dmr::SIDE_BOTTOM ? R.rect[1] : R.rect[3];
-        } else {
-          cb.start[q] = R.rect[1]; cb.len[q] = cfg.ny; cb.at[q] = q == dmr::SIDE_LEFT ? R.rect[0] : R.rect[2];
-        }
-      }
-      cb.r = r;
-      cb.cp = C.p;
-      cb.new_x = ca.E[cin][0]; cb.new_y = ca.E[cin][1];
-      for (int q = 0; q < 4; ++q) {
-        cb.old_line[q] = adj_side[q];
-        ct.side_on[q] = md.m[q] == dmr::BC_CFB;
-        ct.side_at[q] = cb.at[q];
-        ct.side[q] = adj_side[q];
-      }
-      int ncfb = 0;
-      for (int q = 0; q < 4; ++q)
-        if (md.m[q] == dmr::BC_CFB) ncfb += (q == dmr::SIDE_BOTTOM || q == dmr::SIDE_TOP) ? fnx : fny;
-      const dim3 gf = nodes_grid(fnx, fny);
-      const int nbe = (int)(gf.x * gf.y), nbc = (ncfb + BX * BY - 1) / (BX * BY);
-      const dmr::CoarseT<T> none{};
-      for (int k = r; k >= 1; --k) {
-        const int64_t mf = (int64_t)r * R.m + (k - 1);
-        const dmr::Step<T> sf = make_step_at(r, mf, (mf % ((int64_t)r * NT)) != 0, R.rect[0]);
-        const dmr::AdjM<T> am = adjm(A, fin, fnx, fny, fp);
-        cb.frac = (T)((double)k / (double)r);
-        dmr::FwdM<T> fw;
-        fw.Ex = R.fEx[k - 1]; fw.Ey = R.fEy[k - 1]; fw.vx = R.fvx[k - 1]; fw.vy = R.fvy[k - 1]; fw.n = P.nf;
-        go_ka_eh(nbe + nbc, am, fw, sf, md, sums, none, cb, nbe, (int)gf.x);
-        std::swap(A.H, A.H2);
-        fin ^= 1;
-      }
-      if (R.rvalid) {
-        // a8^T of the previous step's transfer, into the fine E^n adjoint
-        ct.restr = 1;
-        ct.I0 = R.rect[0]; ct.J0 = R.rect[1]; ct.I1 = R.rect[2]; ct.J1 = R.rect[3]; ct.r = r;
-        ct.jlo = side_at(R.rect, dmr::SIDE_BOTTOM) ? R.rect[1] : R.rect[1] + 1;
-        ct.jhi = side_at(R.rect, dmr::SIDE_TOP) ? R.rect[3] : R.rect[3] - 1;
-        ct.ilo = side_at(R.rect, dmr::SIDE_LEFT) ? R.rect[0] : R.rect[0] + 1;
-        ct.ihi = side_at(R.rect, dmr::SIDE_RIGHT) ? R.rect[2] : R.rect[2] - 1;
-        ct.fEx = A.E[fin][0]; ct.fEy = A.E[fin][1]; ct.fp = fp;
+    for (int q = 0; q < 4; ++q) {
+      cb.mode[q] = md.m[q];
+      if (q == dmr::SIDE_BOTTOM || q == dmr::SIDE_TOP) {
+        cb.start[q] = R.rect[0]; cb.len[q] = cfg.nx; cb.at[q] = q == dmr::SIDE_BOTTOM ? R.rect[1] : R.rect[3];
+      } else {
+        cb.start[q] = R.rect[1]; cb.len[q] = cfg.ny; cb.at[q] = q == dmr::SIDE_LEFT ? R.rect[0] : R.rect[2];
       }
     }
-    const dmr::Step<T> sc = make_step(1, R.m, (R.m % NT) != 0);
-    dmr::Modes mc;
-    for (int q = 0; q < 4; ++q) mc.m[q] = dmr::BC_MUR;
-    const dmr::AdjM<T> am = adjm(ca, cin, C.nx, C.ny, C.p);
-    const dim3 gc = nodes_grid(C.nx, C.ny);
-    dmr::FwdM<T> fw;
-    fw.Ex = R.cEx; fw.Ey = R.cEy; fw.vx = R.cvx; fw.vy = R.cvy; fw.n = P.nc;
-    const dmr::CfbT<T> cnone{};
-    go_ka_eh((int)(gc.x * gc.y), am, fw, sc, mc, sums, ct, cnone, (int)(gc.x * gc.y), (int)gc.x);
+    cb.r = r;
+    cb.cp = C.p;
+    cb.new_x = ca.E[cin][0]; cb.new_y = ca.E[cin][1];
+    for (int q = 0; q < 4; ++q) {
+      cb.old_line[q] = adj_side[q];
+      ct.side_on[q] = md.m[q] == dmr::BC_CFB;
+      ct.side_at[q] = cb.at[q];
+      ct.side[q] = adj_side[q];
+    }
+    int ncfb = 0;
+    for (int q = 0; q < 4; ++q)
+      if (md.m[q] == dmr::BC_CFB) ncfb += (q == dmr::SIDE_BOTTOM || q == dmr::SIDE_TOP) ? fnx : fny;
+    const int nbc = (ncfb + BX * BY - 1) / (BX * BY);
+    // coarse blocks within 2 nodes of the rectangle (after the fine
+    // sub-steps) and the two halves of the rest (beside sub-steps r and 1)
+    dmr::NodePart<T> Pn = Pc, Pfar[2] = {Pc, Pc};
+    const int sx0 = std::max(R.rect[0] - 2, 0) / BX, sx1 = std::min(R.rect[2] + 2, C.nx) / BX;
+    const int sy0 = std::max(R.rect[1] - 2, 0) / BY, sy1 = std::min(R.rect[3] + 2, C.ny) / BY;
+    Pn.bx0 = sx0; Pn.nbx = sx1 - sx0 + 1;
+    Pn.by0 = sy0; Pn.nby = sy1 - sy0 + 1;
+    const int half = (int)gc.y / 2;
+    Pfar[0].nby = half;
+    Pfar[1].by0 = half;
+    Pfar[1].nby = (int)gc.y - half;
+    for (int h = 0; h < 2; ++h) {
+      Pfar[h].sx0 = sx0; Pfar[h].sx1 = sx1;
+      Pfar[h].sy0 = sy0; Pfar[h].sy1 = sy1;
+    }
+    const dim3 gf = nodes_grid(fnx, fny);
+    for (int k = r; k >= 1; --k) {
+      const int64_t mf = (int64_t)r * R.m + (k - 1);
+      dmr::NodePart<T> Pf{};
+      Pf.a = adjm(A, fin, fnx, fny, fp);
+      Pf.f.Ex = R.fEx[k - 1]; Pf.f.Ey = R.fEy[k - 1]; Pf.f.vx = R.fvx[k - 1]; Pf.f.vy = R.fvy[k - 1];
+      Pf.f.n = P.nf;
+      Pf.c = make_step_at(r, mf, (mf % ((int64_t)r * NT)) != 0, R.rect[0]);
+      Pf.md = md;
+      Pf.nbx = (int)gf.x;
+      Pf.nby = (int)gf.y;
+      Pf.sx0 = Pf.sy0 = 1;
+      Pf.sx1 = Pf.sy1 = 0;
+      cb.frac = (T)((double)k / (double)r);
+      const int side = k == r ? 0 : (k == 1 ? 1 : -1);
+      const dmr::NodePart<T>& P1 = side >= 0 ? Pfar[side] : empty;
+      const int nb1 = side >= 0 ? P1.nbx * P1.nby : 0;
+      go_ka_eh(Pf, Pf.nbx * Pf.nby, cb, nbc, P1, nb1, sums);
+      std::swap(A.H, A.H2);
+      fin ^= 1;
+    }
+    if (R.rvalid) {
+      // a8^T of the previous step's transfer, into the fine E^n adjoint
+      ct.restr = 1;
+      ct.I0 = R.rect[0]; ct.J0 = R.rect[1]; ct.I1 = R.rect[2]; ct.J1 = R.rect[3]; ct.r = r;
+      ct.jlo = side_at(R.rect, dmr::SIDE_BOTTOM) ? R.rect[1] : R.rect[1] + 1;
+      ct.jhi = side_at(R.rect, dmr::SIDE_TOP) ? R.rect[3] : R.rect[3] - 1;
+      ct.ilo = side_at(R.rect, dmr::SIDE_LEFT) ? R.rect[0] : R.rect[0] + 1;
+      ct.ihi = side_at(R.rect, dmr::SIDE_RIGHT) ? R.rect[2] : R.rect[2] - 1;
+      ct.fEx = A.E[fin][0]; ct.fEy = A.E[fin][1]; ct.fp = fp;
+    }
+    Pn.ct = ct;
+    go_ka_eh(Pn, Pn.nbx * Pn.nby, cnone, 0, empty, 0, sums);
     std::swap(ca.H, ca.H2);
     cin ^= 1;
     return launched("adjoint step");

@@ -301,22 +301,47 @@ __device__ __forceinline__ void ka_cfb_sample(const AdjM<T>& a, const CfbT<T>& b
   ka_cfb_side<SIDE_RIGHT>(a, b, q);
 }
 
-// One launch per reversed EM step of one mesh: the node blocks (the first
-// nbe blocks, TX x TY nodes each, gx across; ka_e_node, E0 share summed per
-// block in FP64), then on a fine mesh the Eq. 5b^T side samples (TX * TY per
-// block), which read aE' and add to the coarse adjoints only.
+// A rectangle of node blocks of one mesh in a reversed EM step: blocks
+// (bx0 + k % nbx, by0 + k / nbx), each TX x TY nodes, except those inside the
+// skip box [sx0, sx1] x [sy0, sy1] (sx0 > sx1: none skipped).
 template <class T>
-__global__ void __launch_bounds__(TX * TY) ka_eh(AdjM<T> a, FwdM<T> f, Step<T> c, Modes md, double* e0acc,
-                                                 CoarseT<T> ct, CfbT<T> cb, int nbe, int gx) {
-  const int blk = (int)blockIdx.x;
-  if (blk >= nbe) {
-    ka_cfb_sample(a, cb, (blk - nbe) * TX * TY + (int)(threadIdx.y * TX + threadIdx.x));
-    return;
-  }
-  const int by = blk / gx, bx = blk - by * gx;
-  const T e0 = ka_e_node(a, f, c, md, ct, bx * TX + (int)threadIdx.x, by * TY + (int)threadIdx.y);
+struct NodePart {
+  AdjM<T> a;
+  FwdM<T> f;
+  Step<T> c;
+  Modes md;
+  CoarseT<T> ct;
+  int bx0, by0, nbx, nby;
+  int sx0, sx1, sy0, sy1;
+};
+
+// Node block k of a part: ka_e_node over its nodes, E0 share summed in FP64.
+template <class T>
+__device__ __forceinline__ void ka_part_block(const NodePart<T>& P, int k, double* e0acc) {
+  const int by = P.by0 + k / P.nbx, bx = P.bx0 + k % P.nbx;
+  if (bx >= P.sx0 && bx <= P.sx1 && by >= P.sy0 && by <= P.sy1) return;   // whole block
+  const T e0 = ka_e_node(P.a, P.f, P.c, P.md, P.ct, bx * TX + (int)threadIdx.x, by * TY + (int)threadIdx.y);
   const double s = block_sum_d((double)e0);
   if (threadIdx.x == 0 && threadIdx.y == 0 && s != 0.0) atomicAdd(e0acc, s);
+}
+
+// One launch of a reversed EM step: the node blocks of part P0 (nb0 blocks),
+// then the Eq. 5b^T side samples of P0's fine mesh (ncfb blocks of TX * TY
+// samples; they read aE' and add to coarse adjoints only), then the node
+// blocks of part P1 (nb1 blocks): coarse nodes away from the rectangle run
+// beside the fine sub-steps of the same coarse step, which neither read nor
+// write them.
+template <class T>
+__global__ void __launch_bounds__(TX * TY) ka_eh(NodePart<T> P0, NodePart<T> P1, CfbT<T> cb, int nb0, int ncfb,
+                                                 double* e0acc) {
+  const int blk = (int)blockIdx.x;
+  if (blk < nb0) {
+    ka_part_block(P0, blk, e0acc);
+  } else if (blk < nb0 + ncfb) {
+    ka_cfb_sample(P0.a, cb, (blk - nb0) * TX * TY + (int)(threadIdx.y * TX + threadIdx.x));
+  } else {
+    ka_part_block(P1, blk - nb0 - ncfb, e0acc);
+  }
 }
 
 // a8^T for E: the adjoint of a restricted coarse edge goes to its r fine edges
