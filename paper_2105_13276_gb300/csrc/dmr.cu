@@ -858,6 +858,8 @@ struct Engine final : Base {
   // coarse EM launches compile the CPML terms in only for CPML runs
   void go_em(int nb, const dmr::EmArgs<T>& A, bool pdl = false) const {
     if (A.pml.on) launch_em_kernel(dmr::k_em<T, true>, nb, pdl, A);
+    else if (A.W.on && A.W.r == 2) launch_em_kernel(dmr::k_em<T, false, true, 2>, nb, pdl, A);
+    else if (A.W.on && A.W.r == 4) launch_em_kernel(dmr::k_em<T, false, true, 4>, nb, pdl, A);
     else if (A.W.on) launch_em_kernel(dmr::k_em<T, false, true>, nb, pdl, A);
     else launch_em_kernel(dmr::k_em<T, false>, nb, pdl, A);
   }

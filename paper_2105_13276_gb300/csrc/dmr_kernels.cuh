@@ -344,7 +344,7 @@ __device__ __forceinline__ void em_cfb(const EmArgs<T>& A, int blk) {
   else A.dEy[q * p + nfx] = v;
 }
 
-template <class T, bool PML, bool WR, bool CG>
+template <class T, bool PML, bool WR, bool CG, int RW = 0>
 __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk);
 
 // Blocks of one mesh's EM step: the coarse-fine side blocks first (the
@@ -353,14 +353,16 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk);
 // PML: compile the CPML terms in (coarse launches of CPML runs only)
 // WR: compile the producer-side fine->coarse transfer in (launches of the
 // last fine sub-step of a coarse step only)
-// CG: loads through L2 only (the persistent period kernel)
-template <class T, bool PML = false, bool WR = false, bool CG = false>
+// CG: loads through L2 only (the persistent period kernel).  RW: the
+// refinement factor of the fine->coarse transfer as a constant (0: read
+// from the arguments), so its group sums unroll and its divisions are shifts.
+template <class T, bool PML = false, bool WR = false, bool CG = false, int RW = 0>
 __device__ __forceinline__ void em_segment(const EmArgs<T>& A, int blk) {
   if (blk < A.ncfb) em_cfb<T, CG>(A, blk);
-  else em_strips<T, PML, WR, CG>(A, blk - A.ncfb);
+  else em_strips<T, PML, WR, CG, RW>(A, blk - A.ncfb);
 }
 
-template <class T, bool PML, bool WR, bool CG>
+template <class T, bool PML, bool WR, bool CG, int RW>
 __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
   const Mesh<T>& m = A.m;
   T* __restrict__ dEx = A.dEx;
@@ -446,7 +448,7 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
   // phase jq = j mod r and the coarse row Jc = J0 + j / r are set once and
   // advance with j, so the loop divides by nothing.  An Ex group's r columns
   // are consecutive lanes of one strip (strip width a multiple of r).
-  const int rw = WR ? A.W.r : 1;
+  const int rw = WR ? (RW > 0 ? RW : A.W.r) : 1;
   const bool hx = WR && own && i < nx && (i % rw) == 0;                  // head of an Ex group
   const int Ic = WR ? A.W.I0 + (i > 0 ? i / rw : 0) : 0;
   const bool hy = hx && i > 0 && Ic >= A.W.ilo && Ic <= A.W.ihi;        // restricted Ey column
@@ -641,10 +643,10 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
   }
 }
 
-template <class T, bool PML = false, bool WR = false>
+template <class T, bool PML = false, bool WR = false, int RW = 0>
 __global__ void __launch_bounds__(32 * EM_WARPS, kEmMinBlocks<T>) k_em(EmArgs<T> A) {
   pdl_enter();
-  em_segment<T, PML, WR>(A, blockIdx.x);
+  em_segment<T, PML, WR, false, RW>(A, blockIdx.x);
 }
 
 constexpr int kSegStage = 256;   // segment offsets staged in shared memory up to this many
