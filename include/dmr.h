@@ -239,10 +239,15 @@ int dmr_sync(const dmr_ctx* ctx);
  * changing the run -- 20 back-to-back copies of the launch are captured in a
  * CUDA graph and replayed, as the periods are; they write only next-level
  * buffers that the next step rewrites in full -- keeps the fastest; returns
- * the choice and the per-candidate mean launch times (ms).  With r >= 2 a
- * second pass times fine sub-step 2 alone (no E^2 sample) for the same
- * targets and keeps the fastest for the fine sub-steps that have launches of
- * their own. */
+ * the choice and the per-candidate mean launch times (ms).  With a fine
+ * rectangle the choice is then made on the two launches of a coarse step as
+ * they run: ten pairs of the merged launch and fine sub-step 2 (reading the
+ * present fine state, writing next-level buffers; its E^2 sample is kept
+ * aside and put back) per CUDA graph, programmatic dependent launches in FP32,
+ * for the 16 combinations of targets {16, 32, 48, 96} for the merged launch
+ * and for the fine sub-steps with launches of their own; times within 1 % of
+ * the fastest count as ties, which go to the higher targets (shorter
+ * strips).  *warps_per_sm returns the merged launch's choice. */
 int dmr_autotune(dmr_ctx* ctx, int32_t* warps_per_sm, double trial_ms[5]);
 
 /* Duration of one EM launch form of the present step (at a period boundary;

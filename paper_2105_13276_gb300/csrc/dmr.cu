@@ -2139,26 +2139,46 @@ struct Engine final : Base {
     }
     warps_per_sm = best_w;
     if (has_fine && cfg.r >= 2) {
-      // fine sub-step 2 alone, as it runs (reads the present fine state,
-      // writes the next-level buffers and adds its E^2 sample): the strip
-      // height of the later sub-steps.  The sample goes into S2, so S2 is
-      // kept in the idle fine set (rewritten at the next growth) and put back.
+      // The pair as it runs: the merged launch, then fine sub-step 2 (reading
+      // the present fine state, writing next-level buffers and adding its E^2
+      // sample), ten pairs per graph, programmatic dependent launches in FP32
+      // as in the periods, for each combination of the two strip heights.
+      // Timing one launch kind alone left near-ties that cost up to 25 % in
+      // the real sequence.  The sample goes into S2, so S2 is kept in the
+      // idle fine set (rewritten at the next growth) and put back.
       const size_t s2b = (size_t)(F[cur].ny + 1) * (size_t)F[cur].p * sizeof(double);
       if (int s_ = ck(cudaMemcpyAsync(fS2[cur ^ 1], fS2[cur], s2b, cudaMemcpyDeviceToDevice, st),
                       "autotune: keep S2")) return s_;
-      double best_f = 1e30;
-      int best_fw = warps_per_sm_fine;
-      for (int c = 0; c < 5; ++c) {
-        warps_per_sm_fine = cand[c];
-        dmr::EmArgs<T> Af;
-        em_args_for(2, m, cpar, fpar, true, nullptr, &Af);
-        auto launch = [&]() { go_em(Af.nblk + Af.ncfb, Af); };
-        float ms = 0.f;
-        if (int s_ = ck(graph_time(st, launch, kTrialLaunches, &ms), "autotune trial (fine)")) return s_;
-        launches += 4 * kTrialLaunches;
-        if (ms < best_f) { best_f = ms; best_fw = cand[c]; }
-      }
-      warps_per_sm_fine = best_fw;
+      const int pc[4] = {16, 32, 48, 96};
+      double best_p = 1e30;
+      int bc = best_w, bf = warps_per_sm_fine;
+      const bool pdl = sizeof(T) == 4;
+      for (int a_ = 0; a_ < 4; ++a_)
+        for (int f_ = 0; f_ < 4; ++f_) {
+          warps_per_sm = pc[a_];
+          warps_per_sm_fine = pc[f_];
+          dmr::EmArgs<T> Ac, A1, A2;
+          em_args_for(1, m, cpar, fpar, true, &Ac, &A1);
+          em_args_for(2, m, cpar, fpar, true, nullptr, &A2);
+          auto launch = [&]() {
+            for (int q = 0; q < kTrialLaunches / 2; ++q) {
+              go_em2(Ac.nblk + Ac.ncfb + A1.nblk + A1.ncfb, Ac, A1, pdl && q > 0);
+              go_em(A2.nblk + A2.ncfb, A2, pdl);
+            }
+          };
+          float ms = 0.f;
+          if (int s_ = ck(graph_time(st, launch, 1, &ms), "autotune trial (pair)")) return s_;
+          launches += 4 * kTrialLaunches;
+          // ties (within 1 %) go to the shorter strips
+          if (ms < best_p * 0.99 || (ms <= best_p * 1.01 && (pc[a_] > bc || (pc[a_] == bc && pc[f_] > bf)))) {
+            if (ms < best_p) best_p = ms;
+            bc = pc[a_];
+            bf = pc[f_];
+          }
+        }
+      warps_per_sm = bc;
+      warps_per_sm_fine = bf;
+      best_w = bc;
       if (int s_ = ck(cudaMemcpyAsync(fS2[cur], fS2[cur ^ 1], s2b, cudaMemcpyDeviceToDevice, st),
                       "autotune: restore S2")) return s_;
     }
