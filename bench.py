@@ -166,16 +166,17 @@ def kernel_source_sha():
     return hashlib.sha256("\n".join(ln for ln in lines if ln).encode()).hexdigest()
 
 
-def recorded_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu counters of this kernel,
-    or None when the kernel source changed since that capture."""
+def recorded_traffic(kernel, workload_name):
+    """DRAM bytes per launch from the committed ncu counters of this kernel on
+    this workload, or None when there is no such capture or the kernel source
+    changed since it was taken."""
     root = os.path.dirname(os.path.abspath(__file__))
     try:
         rec = json.load(open(os.path.join(root, "profiles", "ncu_counters.json")))[kernel]
         sha = kernel_source_sha()
     except (OSError, ValueError, KeyError):
         return None
-    if sha != rec.get("kernels_sha256"):
+    if sha != rec.get("kernels_sha256") or rec.get("workload") != workload_name:
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -566,7 +567,7 @@ def run_ours(args):
     step_ach = em_bytes / (ms / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": "k_em2 (coarse step + first fine sub-step), mid-period form",
             "achieved": mid["achieved"], "peak": peak, "peak_source": src + " (burst copy)",
-            "unit": "GB/s", "frac": mid["frac"], "traffic": recorded_traffic("k_em2"),
+            "unit": "GB/s", "frac": mid["frac"], "traffic": recorded_traffic("k_em2", args.workload),
             "avg_launch_us": mid["avg_launch_us"],
             "algorithmic_bytes_per_launch": mid["algorithmic_bytes_per_launch"],
             "timed_region": "CUDA-graph replays of 20 back-to-back copies of the launch on the "
