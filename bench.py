@@ -138,6 +138,25 @@ def cpu_oracle_rate(w, budget_s=12.0, per_step_cap=None):
     return steps * per_step / dt, steps, dt
 
 
+def _oracle_worker(job):
+    w, budget = job
+    os.environ["OMP_NUM_THREADS"] = "1"
+    return cpu_oracle_rate(w, budget_s=budget)
+
+
+def cpu_oracle_rate_all_cores(w, budget_s=6.0):
+    """The same oracle sample run as one independent process per host core at
+    once (spawned, so no process inherits a CUDA context): their summed rate,
+    the process count and the slowest process's seconds."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    n = os.cpu_count() or 1
+    with ProcessPoolExecutor(max_workers=n, mp_context=mp.get_context("spawn")) as ex:
+        futs = [ex.submit(_oracle_worker, (w, budget_s)) for _ in range(n)]
+        res = [f.result(timeout=600) for f in futs]
+    return sum(x[0] for x in res), n, max(x[2] for x in res)
+
+
 def period_em_bytes(cfg, rect, es):
     """Algorithmic bytes of all EM launches of one period with the fine
     rectangle rect: every E, H, v component and n read once and E, H, v
@@ -652,6 +671,11 @@ def run_ours(args):
                "sample": "first %d coarse steps (%.2f periods) of the same run, FP64 numpy oracle on "
                          "one of the host's %d cores (the oracle is one sequential run), %.1f s"
                          % (csteps, csteps / NT, os.cpu_count() or 0, csec)}
+        if not args.no_cpu_all:
+            ar, an, asec = cpu_oracle_rate_all_cores(w, budget_s=args.cpu_seconds / 2)
+            cpu["all_cores"] = {"value": ar, "unit": UNIT, "cores": an,
+                                "sample": "the same sample as %d independent oracle processes at once "
+                                          "(one per host core), %.1f s each; summed rate" % (an, asec)}
 
     if rank == 0:
         c = config_of(w, args)
@@ -689,6 +713,7 @@ def main():
     ap.add_argument("--no-uniform", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu-all", action="store_true", help="skip the all-cores oracle figure")
     ap.add_argument("--batch-runs", type=int, default=64, help="runs of the batch64 workload")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
