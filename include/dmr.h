@@ -240,14 +240,18 @@ int dmr_sync(const dmr_ctx* ctx);
  * CUDA graph and replayed, as the periods are; they write only next-level
  * buffers that the next step rewrites in full -- keeps the fastest; returns
  * the choice and the per-candidate mean launch times (ms).  With a fine
- * rectangle the choice is then made on the two launches of a coarse step as
- * they run: ten pairs of the merged launch and fine sub-step 2 (reading the
- * present fine state, writing next-level buffers; its E^2 sample is kept
- * aside and put back) per CUDA graph, programmatic dependent launches in FP32,
- * for the 16 combinations of targets {16, 32, 48, 96} for the merged launch
- * and for the fine sub-steps with launches of their own; times within 1 % of
- * the fastest count as ties, which go to the higher targets (shorter
- * strips).  *warps_per_sm returns the merged launch's choice. */
+ * rectangle the choice is then made on the launches of a coarse step as
+ * they run: ten coarse steps of the merged launch and fine sub-steps 2..r
+ * (each reading the present fine state and writing next-level buffers; their
+ * E^2 samples are kept aside and put back) per CUDA graph, programmatic
+ * dependent launches in FP32, for the 16 combinations of targets {16, 32, 48,
+ * 96} for the merged launch and for the fine sub-steps with launches of
+ * their own; times within 1 % of the fastest count as ties, which go to the
+ * higher targets (shorter strips).  In FP32 runs without CPML each
+ * combination is also timed with two node columns per lane in sub-steps
+ * 2..r (dmr_set_strip_columns); two must be more than 1 % faster to be
+ * chosen.  *warps_per_sm returns the merged launch's choice
+ * (dmr_get_launch_shape gives the whole shape). */
 int dmr_autotune(dmr_ctx* ctx, int32_t* warps_per_sm, double trial_ms[5]);
 
 /* Duration of one EM launch form of the present step (at a period boundary;
@@ -268,6 +272,21 @@ int dmr_time_launch(dmr_ctx* ctx, int form, int reps, double* ms_per_launch, dou
  * in [1, 1024] (e.g. the choice dmr_autotune made on an earlier run of the
  * same size).  Results do not depend on it.  DMR_EINVAL otherwise. */
 int dmr_set_launch_shape(dmr_ctx* ctx, int32_t warps_per_sm);
+
+/* Node columns each lane of the EM strip kernel advances in the fine
+ * sub-steps 2..r of a coarse step (the ones with launches of their own): 1
+ * (default) or 2.  With 2, a warp covers 60 columns and each row's loads and
+ * stores are 8-byte vector accesses (16-byte for the FP64 E^2 sums).  It
+ * applies to FP32 runs without CPML, not in a persistent period; the last
+ * sub-step (which writes the fine->coarse means) takes it at r = 2 or 4
+ * only.  Results do not depend on it, bit for bit.  dmr_autotune may change
+ * it.  Errors: DMR_EINVAL (not 1 or 2), DMR_ESTATE (a run of a batch). */
+int dmr_set_strip_columns(dmr_ctx* ctx, int32_t columns_per_lane);
+
+/* The present launch shape: shape[0] the warps-per-SM target of the coarse
+ * step's launch, shape[1] that of the fine sub-steps with launches of their
+ * own, shape[2] the node columns per lane. */
+int dmr_get_launch_shape(const dmr_ctx* ctx, int32_t shape[3]);
 
 /* Persistent period (enable = 1; default 0): every full period that starts
  * at a period boundary runs its N_T coarse steps with their r fine sub-steps

@@ -367,6 +367,8 @@ struct Base {
   virtual int stats(double* out) = 0;
   virtual int autotune(int32_t* wps, double* trial_ms) = 0;
   virtual void set_shape(int wps) = 0;
+  virtual void set_cols(int cols) = 0;
+  virtual void get_shape(int32_t* out) const = 0;
   virtual int adj_record(int64_t n, int64_t K, void* ckpt, size_t bytes) = 0;
   virtual size_t adj_ckpt_bytes(int64_t n, int64_t K) const = 0;
   virtual size_t adj_bytes() const = 0;
@@ -723,10 +725,11 @@ struct Engine final : Base {
   // about one memory latency, large ones up to 64 (the warm-up row is 1/rows)
   int warps_per_sm = 48;     // strip-height policy (the batch autotuner may change it)
   int warps_per_sm_fine = 48;   // the same for the fine sub-steps after the first (own launches)
+  int lanecols = 1;             // node columns per lane of the EM strips (2: em_strips2, FP32)
   // rows per warp of an EM launch over an nx x ny mesh with sw-column strips;
   // a multiple of rr, or 1 (the last fine sub-step sums Ey over the r rows of
   // a coarse row)
-  int em_rows(int nx, int ny, int sw, int rr, int wps) const {
+  int em_rows(int nx, int ny, int sw, int rr, int wps, bool cross_ok = true) const {
     const long long sx = (nx + 1 + sw - 1) / sw;
     const long long target = (long long)num_sms * wps;
     long long rows = (sx * (ny + 1) + target - 1) / target;
@@ -735,7 +738,7 @@ struct Engine final : Base {
     // (the block's warps then sum Ey in groups of r, em_strips); not in a
     // batch, whose blocks each stage their segment's arguments first, so
     // halving the rows there doubles that work
-    if (rr > 1 && rows == 1 && dmr::EM_WARPS % rr == 0 && !in_batch) return 1;
+    if (rr > 1 && rows == 1 && dmr::EM_WARPS % rr == 0 && !in_batch && cross_ok) return 1;
     rows = (rows + rr - 1) / rr * rr;
     return (int)std::min<long long>(rows, 64 - 64 % rr);
   }
@@ -857,6 +860,14 @@ struct Engine final : Base {
   }
   // coarse EM launches compile the CPML terms in only for CPML runs
   void go_em(int nb, const dmr::EmArgs<T>& A, bool pdl = false) const {
+    if constexpr (sizeof(T) == 4) {
+      if (A.lw == 2) {
+        if (A.W.on && A.W.r == 2) launch_em_kernel(dmr::k_em_w2<true, 2>, nb, pdl, A);
+        else if (A.W.on) launch_em_kernel(dmr::k_em_w2<true, 4>, nb, pdl, A);
+        else launch_em_kernel(dmr::k_em_w2<false, 0>, nb, pdl, A);
+        return;
+      }
+    }
     if (A.pml.on) launch_em_kernel(dmr::k_em<T, true>, nb, pdl, A);
     else if (A.W.on && A.W.r == 2) launch_em_kernel(dmr::k_em<T, false, true, 2>, nb, pdl, A);
     else if (A.W.on && A.W.r == 4) launch_em_kernel(dmr::k_em<T, false, true, 4>, nb, pdl, A);
@@ -872,15 +883,22 @@ struct Engine final : Base {
   // (the last fine sub-step of a coarse step, which writes the a8 means); 1
   // otherwise
   dmr::EmArgs<T> em_args(const dmr::Mesh<T>& src, T* const* dst, const dmr::Step<T>& c,
-                         const dmr::Bnd<T>& b, int rr = 1, int wps = 0) const {
+                         const dmr::Bnd<T>& b, int rr = 1, int wps = 0, bool w2_ok = false) const {
     dmr::EmArgs<T> A;
     A.m = src;
     A.dEx = dst[0]; A.dEy = dst[1]; A.dHz = dst[2]; A.dvx = dst[3]; A.dvy = dst[4];
     A.c = c; A.b = b;
     A.pml = dmr::Pml<T>{};
     A.W = dmr::RestrW<T>{};
-    A.sw = dmr::STRIP_W - dmr::STRIP_W % rr;
-    A.rows = em_rows(src.nx, src.ny, A.sw, rr, wps > 0 ? wps : warps_per_sm);
+    // two node columns per lane where the run asks for them: the fine
+    // sub-steps with launches of their own (w2_ok) in FP32 runs without CPML,
+    // not in a batch or a persistent period; the last one at r = 2 or 4 only,
+    // with rows per warp a multiple of r
+    const bool w2 = w2_ok && lanecols == 2 && sizeof(T) == 4 && !in_batch && !persist_on() &&
+                    d.boundary != 1 && (rr == 1 || rr == 2 || rr == 4);
+    A.lw = w2 ? 2 : 1;
+    A.sw = w2 ? dmr::STRIP_W2 - dmr::STRIP_W2 % rr : dmr::STRIP_W - dmr::STRIP_W % rr;
+    A.rows = em_rows(src.nx, src.ny, A.sw, rr, wps > 0 ? wps : warps_per_sm, !w2);
     A.gx = (src.nx + 1 + A.sw - 1) / A.sw;
     const int sy = (src.ny + 1 + A.rows - 1) / A.rows;
     A.nblk = A.gx * ((sy + dmr::EM_WARPS - 1) / dmr::EM_WARPS);
@@ -959,7 +977,7 @@ struct Engine final : Base {
                   fineE(cur, fp ^ 1, 3), fineE(cur, fp ^ 1, 4)};
     // the last sub-step's strips align with the coarse cells (a8 column groups and row sums)
     // sub-steps after the first run alone, with their own strip height
-    *Af = em_args(fsrc, fdst, sf, bf, k == r ? r : 1, k > 1 ? warps_per_sm_fine : warps_per_sm);
+    *Af = em_args(fsrc, fdst, sf, bf, k == r ? r : 1, k > 1 ? warps_per_sm_fine : warps_per_sm, k > 1);
     Af->kind = 1; Af->N = r * NT; Af->r = r; Af->ps = ph[2]; Af->pc = ph[3];
     if (k == r) {
       // a8: the last sub-step writes the mean of r collinear fine edges into
@@ -2112,10 +2130,22 @@ struct Engine final : Base {
     warps_per_sm_fine = wps;
     drop_graph();
   }
+  void set_cols(int cols) override {
+    lanecols = cols;
+    drop_graph();
+  }
+  void get_shape(int32_t* out) const override {
+    out[0] = warps_per_sm;
+    out[1] = warps_per_sm_fine;
+    out[2] = lanecols;
+  }
 
   int autotune(int32_t* wps_out, double* trial_ms) override {
     if (m % cfg.steps_per_period != 0) return fail(DMR_ESTATE, "autotune at a period boundary");
     const int cand[5] = {8, 16, 32, 48, 96};
+    // node columns per lane of the later fine sub-steps tried: 1, and 2
+    // where the run can use them; two must be more than 1 % faster
+    const int ncols = (sizeof(T) == 4 && d.boundary != 1 && !in_batch && !persist_on()) ? 2 : 1;
     double best = 1e30;
     int best_w = warps_per_sm;
     for (int c = 0; c < 5; ++c) {
@@ -2139,45 +2169,54 @@ struct Engine final : Base {
     }
     warps_per_sm = best_w;
     if (has_fine && cfg.r >= 2) {
-      // The pair as it runs: the merged launch, then fine sub-step 2 (reading
-      // the present fine state, writing next-level buffers and adding its E^2
-      // sample), ten pairs per graph, programmatic dependent launches in FP32
-      // as in the periods, for each combination of the two strip heights.
+      // The coarse step's launches as they run: the merged launch, then fine
+      // sub-steps 2..r (each reading the present fine state, writing
+      // next-level buffers and adding its E^2 sample; the last one writing
+      // the fine->coarse means), ten coarse steps per graph, programmatic
+      // dependent launches in FP32 as in the periods, for each combination of
+      // the two strip heights (and node columns per lane of sub-steps 2..r).
       // Timing one launch kind alone left near-ties that cost up to 25 % in
-      // the real sequence.  The sample goes into S2, so S2 is kept in the
+      // the real sequence.  The samples go into S2, so S2 is kept in the
       // idle fine set (rewritten at the next growth) and put back.
       const size_t s2b = (size_t)(F[cur].ny + 1) * (size_t)F[cur].p * sizeof(double);
       if (int s_ = ck(cudaMemcpyAsync(fS2[cur ^ 1], fS2[cur], s2b, cudaMemcpyDeviceToDevice, st),
                       "autotune: keep S2")) return s_;
       const int pc[4] = {16, 32, 48, 96};
       double best_p = 1e30;
-      int bc = best_w, bf = warps_per_sm_fine;
+      int bc = best_w, bf = warps_per_sm_fine, blc = lanecols;
       const bool pdl = sizeof(T) == 4;
+      for (int lc = 1; lc <= ncols; ++lc)
       for (int a_ = 0; a_ < 4; ++a_)
         for (int f_ = 0; f_ < 4; ++f_) {
+          lanecols = lc;
           warps_per_sm = pc[a_];
           warps_per_sm_fine = pc[f_];
-          dmr::EmArgs<T> Ac, A1, A2;
+          dmr::EmArgs<T> Ac, A1;
+          std::vector<dmr::EmArgs<T>> Ak(cfg.r + 1);
           em_args_for(1, m, cpar, fpar, true, &Ac, &A1);
-          em_args_for(2, m, cpar, fpar, true, nullptr, &A2);
+          for (int k = 2; k <= cfg.r; ++k) em_args_for(k, m, cpar, fpar, true, nullptr, &Ak[k]);
           auto launch = [&]() {
             for (int q = 0; q < kTrialLaunches / 2; ++q) {
               go_em2(Ac.nblk + Ac.ncfb + A1.nblk + A1.ncfb, Ac, A1, pdl && q > 0);
-              go_em(A2.nblk + A2.ncfb, A2, pdl);
+              for (int k = 2; k <= cfg.r; ++k) go_em(Ak[k].nblk + Ak[k].ncfb, Ak[k], pdl);
             }
           };
           float ms = 0.f;
-          if (int s_ = ck(graph_time(st, launch, 1, &ms), "autotune trial (pair)")) return s_;
-          launches += 4 * kTrialLaunches;
-          // ties (within 1 %) go to the shorter strips
-          if (ms < best_p * 0.99 || (ms <= best_p * 1.01 && (pc[a_] > bc || (pc[a_] == bc && pc[f_] > bf)))) {
+          if (int s_ = ck(graph_time(st, launch, 1, &ms), "autotune trial (coarse step)")) return s_;
+          launches += 4 * (int64_t)(kTrialLaunches / 2) * cfg.r;
+          // ties (within 1 %) go to the shorter strips, and to one column per
+          // lane
+          if (ms < best_p * 0.99 ||
+              (ms <= best_p * 1.01 && lc == blc && (pc[a_] > bc || (pc[a_] == bc && pc[f_] > bf)))) {
             if (ms < best_p) best_p = ms;
             bc = pc[a_];
             bf = pc[f_];
+            blc = lc;
           }
         }
       warps_per_sm = bc;
       warps_per_sm_fine = bf;
+      lanecols = blc;
       best_w = bc;
       if (int s_ = ck(cudaMemcpyAsync(fS2[cur], fS2[cur ^ 1], s2b, cudaMemcpyDeviceToDevice, st),
                       "autotune: restore S2")) return s_;
@@ -2880,6 +2919,21 @@ int dmr_set_launch_shape(dmr_ctx* ctx, int32_t warps_per_sm) {
   CTX_OR_FAIL(ctx);
   if (warps_per_sm < 1 || warps_per_sm > 1024) return ctx->e->fail(DMR_EINVAL, "warps_per_sm outside [1, 1024]");
   ctx->e->set_shape(warps_per_sm);
+  return DMR_OK;
+}
+
+int dmr_set_strip_columns(dmr_ctx* ctx, int32_t columns_per_lane) {
+  CTX_OR_FAIL(ctx);
+  if (columns_per_lane < 1 || columns_per_lane > 2) return ctx->e->fail(DMR_EINVAL, "columns_per_lane must be 1 or 2");
+  if (ctx->e->in_batch) return ctx->e->fail(DMR_ESTATE, "runs of a batch step in the batch's launches");
+  ctx->e->set_cols(columns_per_lane);
+  return DMR_OK;
+}
+
+int dmr_get_launch_shape(const dmr_ctx* ctx, int32_t shape[3]) {
+  CTX_OR_FAIL(ctx);
+  if (!shape) return ctx->e->fail(DMR_EINVAL, "null output pointer");
+  ctx->e->get_shape(shape);
   return DMR_OK;
 }
 

@@ -272,6 +272,7 @@ struct EmArgs {
   int sw;               // owned columns per strip (STRIP_W; a multiple of r on the fine mesh)
   int rows, gx, nblk;   // strips: rows per warp, strips across x, blocks
   int ncfb;             // blocks that write the coarse-fine boundary E (Eq. 5b)
+  int lw;               // node columns per lane of the strips: 1 (em_strips) or 2 (em_strips2)
   // batched launches: the level-dependent fields (phase, E^2 sample, Eq. 5b
   // time weight) are filled in the kernel from the step index
   int kind;             // 0 coarse step, 1 fine sub-step
@@ -642,6 +643,275 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
     nc = nn;
   }
 }
+
+// ---- two node columns per lane (FP32) ---------------------------------------
+// The same EM step as em_strips (Eqs. 1-3, Mur, the E^2 sample of the level
+// being left, the producer-side a8 transfer) with each lane holding two
+// adjacent node columns, so each row's loads and stores are 8-byte vector
+// accesses (16-byte for the FP64 E^2 sums) and one lane shuffle serves two
+// nodes: a warp covers 64 columns, lanes 1..STRIP_W2/2 own 60 of them, lane 0
+// and lane 31 hold the halo columns.  Every element is computed by the same
+// operations in the same order as em_strips, so results are the same bits.
+// Used for Mur/coarse-fine/PEC sides without CPML, outside the persistent
+// period; the last fine sub-step (WR) takes r = 2 or 4 with rows per warp a
+// multiple of r.  The v of every edge is stored by the owner of its column
+// and row (on a Mur side that is the value em_strips' neighbour stores).
+constexpr int STRIP_W2 = 60;
+
+__device__ __forceinline__ float2 ld_f2(const float* q, bool both, bool first) {
+  float2 v = make_float2(0.f, 0.f);
+  if (both) v = *reinterpret_cast<const float2*>(q);
+  else if (first) v.x = *q;
+  return v;
+}
+__device__ __forceinline__ double2 ld_d2(const double* q, bool both, bool first) {
+  double2 v = make_double2(0.0, 0.0);
+  if (both) v = *reinterpret_cast<const double2*>(q);
+  else if (first) v.x = *q;
+  return v;
+}
+__device__ __forceinline__ void st_f2(float* q, float a, float b, bool sa, bool sb) {
+  if (sa && sb) {
+    *reinterpret_cast<float2*>(q) = make_float2(a, b);
+  } else {
+    if (sa) q[0] = a;
+    if (sb) q[1] = b;
+  }
+}
+__device__ __forceinline__ void st_d2(double* q, double a, double b, bool sa, bool sb) {
+  if (sa && sb) {
+    *reinterpret_cast<double2*>(q) = make_double2(a, b);
+  } else {
+    if (sa) q[0] = a;
+    if (sb) q[1] = b;
+  }
+}
+
+// |E^n|^2 at node (i, j) from the x edges left/right and the y edges
+// below/above (incident added), as em_strips takes it
+__device__ __forceinline__ float node_e2_sample(int i, int j, int nx, int ny, float exl, float exc,
+                                                float eyp, float eyc, float inc) {
+  float sx, sy;
+  if (i > 0 && i < nx) sx = 0.5f * (exl * exl + exc * exc);
+  else if (i > 0) sx = exl * exl;
+  else sx = exc * exc;
+  const float e = eyp + inc, f = eyc + inc;
+  if (j > 0 && j < ny) sy = 0.5f * (e * e + f * f);
+  else if (j > 0) sy = e * e;
+  else sy = f * f;
+  return sx + sy;
+}
+
+// One node column of a row of em_strips2: the x and y edge updates of node
+// (i, j) from its loaded and neighbouring values (the operations of em_strips)
+struct Col2 {
+  float en_x, en_y;   // E^{n+1} of the node's x / y edge (interior edges)
+  float exw0, exwN;   // Mur bottom / top: the boundary row's new Ex
+  float eywL, eywR;   // Mur left / right: the boundary column's new Ey
+};
+
+__device__ __forceinline__ Col2 col2_update(const Step<float>& c, const Bnd<float>& b, int i, int j,
+                                            int nx, int ny, float hz, float hzp, float hzl,
+                                            float exc, float exp_, float exn, float eyc, float eyl,
+                                            float eyr, float vxo, float vyo, float nc, float ncr,
+                                            float nn, float inc) {
+  Col2 o;
+  o.en_x = o.en_y = o.exw0 = o.exwN = o.eywL = o.eywR = 0.f;
+  if (i < nx && j > 0 && j < ny) {
+    const float v = c.va * vxo - c.vb * exc;
+    const float en = exc + c.ce * (hz - hzp) + c.cj * (nc + ncr) * v;
+    o.en_x = en;
+    if (j == 1 && b.mode[SIDE_BOTTOM] == BC_MUR) o.exw0 = exc + c.mur * (en - exp_);
+    if (j == ny - 1 && b.mode[SIDE_TOP] == BC_MUR) o.exwN = exc + c.mur * (en - exn);
+  }
+  if (j < ny && i > 0 && i < nx) {
+    const float v = c.va * vyo - c.vb * (eyc + inc);
+    const float en = eyc - c.ce * (hz - hzl) + c.cj * (nc + nn) * v;
+    o.en_y = en;
+    if (i == 1 && b.mode[SIDE_LEFT] == BC_MUR) o.eywL = eyc + c.mur * (en - eyl);
+    if (i == nx - 1 && b.mode[SIDE_RIGHT] == BC_MUR) o.eywR = eyc + c.mur * (en - eyr);
+  }
+  return o;
+}
+
+template <bool WR, int RW>
+__device__ __forceinline__ void em_strips2(const EmArgs<float>& A, int blk) {
+  const Mesh<float>& m = A.m;
+  float* __restrict__ dEx = A.dEx;
+  float* __restrict__ dEy = A.dEy;
+  float* __restrict__ dHz = A.dHz;
+  float* __restrict__ dvx = A.dvx;
+  float* __restrict__ dvy = A.dvy;
+  const Step<float>& c = A.c;
+  const Bnd<float>& b = A.b;
+  const int rows = A.rows;
+  const int lane = threadIdx.x & 31;
+  const int bx = blk % A.gx, byb = blk / A.gx;
+  const int sy = byb * EM_WARPS + (threadIdx.x >> 5);
+  const int p = m.p, nx = m.nx, ny = m.ny;
+  const int sw = A.sw;                       // owned columns per strip (even)
+  const int ia = bx * sw - 2 + 2 * lane, ib = ia + 1;
+  const int j0 = sy * rows;
+  if (j0 > ny) return;                       // whole warp leaves together
+  const int j1 = min(j0 + rows, ny + 1);
+  const bool lo = lane >= 1 && 2 * lane <= sw;
+  const bool own_a = lo && ia <= nx, own_b = lo && ib <= nx;
+  const bool live = 2 * lane <= sw + 2;
+  const bool xa = live && ia >= 0 && ia < nx, xb = live && ib >= 0 && ib < nx;
+  const bool ya = live && ia >= 0 && ia <= nx, yb = live && ib >= 0 && ib <= nx;
+  const float inc_a = ya ? incident(c, ia) : 0.f, inc_b = yb ? incident(c, ib) : 0.f;
+  const bool pec_b = b.mode[SIDE_BOTTOM] == BC_PEC, pec_t = b.mode[SIDE_TOP] == BC_PEC;
+  const bool pec_l = b.mode[SIDE_LEFT] == BC_PEC, pec_r = b.mode[SIDE_RIGHT] == BC_PEC;
+  // carried state for row j: Ex^n(j), Ex^n(j-1), Ey^n(j-1), Hz^{n+1/2}(j-1), n(j)
+  float2 exc = ld_f2(m.Ex + j0 * p + ia, xb, xa);
+  float2 nc = ld_f2(m.n + j0 * p + ia, yb, ya);
+  float2 exp_ = make_float2(0.f, 0.f), eyp = make_float2(0.f, 0.f), hzp = make_float2(0.f, 0.f);
+  if (j0 > 0) {
+    const int jm = j0 - 1;
+    const float2 exm = ld_f2(m.Ex + jm * p + ia, xb, xa);
+    const float2 eym = ld_f2(m.Ey + jm * p + ia, yb, ya);
+    const float2 hzo = ld_f2(m.Hz + jm * p + ia, xb, xa);
+    const float eyr_b = __shfl_down_sync(0xffffffffu, eym.x, 1);
+    if (xa) hzp.x = hzo.x - c.ch * ((eym.y - eym.x) - (exc.x - exm.x));
+    if (xb) hzp.y = hzo.y - c.ch * ((eyr_b - eym.y) - (exc.y - exm.y));
+    exp_ = exm;
+    eyp = eym;
+  }
+  struct Row2 { float2 exn, eyc, hzo, vxo, vyo, nn; double2 s2; };
+  auto load_row = [&](int j) {
+    Row2 q;
+    const int id = j * p + ia;
+    const bool in = j < ny;
+    const float2 z = make_float2(0.f, 0.f);
+    q.exn = in ? ld_f2(m.Ex + id + p, xb, xa) : z;
+    q.eyc = in ? ld_f2(m.Ey + id, yb, ya) : z;
+    q.hzo = in ? ld_f2(m.Hz + id, xb, xa) : z;
+    q.vxo = ld_f2(m.vx + id, xb, xa);
+    q.vyo = in ? ld_f2(m.vy + id, yb, ya) : z;
+    q.nn = in ? ld_f2(m.n + id + p, yb, ya) : z;
+    q.s2 = c.accum ? ld_d2(m.S2 + id, own_b, own_a) : make_double2(0.0, 0.0);
+    return q;
+  };
+  Row2 nxt = load_row(j0);
+  // a8 on the producer side (r = 2 or 4, rows a multiple of r): an Ex group
+  // of r columns is one lane (r = 2) or two (r = 4, heads on odd lanes)
+  constexpr int rw = WR ? RW : 1;
+  static_assert(!WR || RW == 2 || RW == 4, "two columns per lane: r = 2 or 4");
+  const bool hx = WR && own_a && ia < nx && (ia % rw) == 0;         // head of an Ex group
+  const int Ic = WR ? A.W.I0 + (ia > 0 ? ia / rw : 0) : 0;
+  const bool hy = hx && ia > 0 && Ic >= A.W.ilo && Ic <= A.W.ihi;   // restricted Ey column
+  int jq = 0, Jc = WR ? A.W.J0 + j0 / rw : 0;
+  float eacc_a = 0.f, eaccL = 0.f, eaccR = 0.f;
+  for (int j = j0; j < j1; ++j) {
+    const int id = j * p + ia;
+    const Row2 cur = nxt;
+    if (j + 1 < j1) nxt = load_row(j + 1);
+    // ---- H (Eq. 2)
+    const float eyr_b = __shfl_down_sync(0xffffffffu, cur.eyc.x, 1);
+    float2 hz = make_float2(0.f, 0.f);
+    if (j < ny) {
+      if (xa) hz.x = cur.hzo.x - c.ch * ((cur.eyc.y - cur.eyc.x) - (cur.exn.x - exc.x));
+      if (xb) hz.y = cur.hzo.y - c.ch * ((eyr_b - cur.eyc.y) - (cur.exn.y - exc.y));
+    }
+    const float hzl_a = __shfl_up_sync(0xffffffffu, hz.y, 1);
+    const float exl_a = __shfl_up_sync(0xffffffffu, exc.y, 1);
+    const float ncr_b = __shfl_down_sync(0xffffffffu, nc.x, 1);
+    const float vyr_b = __shfl_down_sync(0xffffffffu, cur.vyo.x, 1);
+    const Col2 oa = col2_update(c, b, ia, j, nx, ny, hz.x, hzp.x, hzl_a, exc.x, exp_.x, cur.exn.x,
+                                cur.eyc.x, 0.f, cur.eyc.y, cur.vxo.x, cur.vyo.x, nc.x, nc.y,
+                                cur.nn.x, inc_a);
+    const Col2 ob = col2_update(c, b, ib, j, nx, ny, hz.y, hzp.y, hz.x, exc.y, exp_.y, cur.exn.y,
+                                cur.eyc.y, cur.eyc.x, eyr_b, cur.vxo.y, cur.vyo.y, nc.y, ncr_b,
+                                cur.nn.y, inc_b);
+    const bool ax = own_a && ia < nx, bxx = own_b && ib < nx;   // columns with an x edge
+    // ---- stores: H, the E^2 sample of level n, v, interior and PEC E
+    st_f2(dHz + id, hz.x, hz.y, ax && j < ny, bxx && j < ny);
+    if (c.accum) {
+      const float e2a = node_e2_sample(ia, j, nx, ny, exl_a, exc.x, eyp.x, cur.eyc.x, inc_a);
+      const float e2b = node_e2_sample(ib, j, nx, ny, exc.x, exc.y, eyp.y, cur.eyc.y, inc_b);
+      st_d2(m.S2 + id, cur.s2.x + (double)e2a, cur.s2.y + (double)e2b, own_a, own_b);
+    }
+    st_f2(dvx + id, c.va * cur.vxo.x - c.vb * exc.x, c.va * cur.vxo.y - c.vb * exc.y, ax, bxx);
+    {
+      const bool xin = j > 0 && j < ny;
+      const bool xpec = (j == 0 && pec_b) || (j == ny && pec_t);
+      st_f2(dEx + id, oa.en_x, ob.en_x, ax && (xin || xpec), bxx && (xin || xpec));
+      if (j == 1 && b.mode[SIDE_BOTTOM] == BC_MUR) st_f2(dEx + ia, oa.exw0, ob.exw0, ax && j < ny, bxx && j < ny);
+      if (j == ny - 1 && b.mode[SIDE_TOP] == BC_MUR) st_f2(dEx + ny * p + ia, oa.exwN, ob.exwN, ax && j > 0, bxx && j > 0);
+    }
+    if (j < ny) {
+      st_f2(dvy + id, c.va * cur.vyo.x - c.vb * (cur.eyc.x + inc_a),
+            c.va * cur.vyo.y - c.vb * (cur.eyc.y + inc_b), own_a, own_b);
+      const bool ia_in = ia > 0 && ia < nx, ib_in = ib > 0 && ib < nx;
+      const bool ia_pec = (ia == 0 && pec_l) || (ia == nx && pec_r);
+      const bool ib_pec = (ib == 0 && pec_l) || (ib == nx && pec_r);
+      st_f2(dEy + id, oa.en_y, ob.en_y, own_a && (ia_in || ia_pec), own_b && (ib_in || ib_pec));
+      // Mur left / right: the boundary column's Ey by the owner of column 1 / nx - 1
+      if (own_b && ib == 1 && b.mode[SIDE_LEFT] == BC_MUR) dEy[j * p] = ob.eywL;
+      if (own_a && ia == nx - 1 && b.mode[SIDE_RIGHT] == BC_MUR) dEy[j * p + nx] = oa.eywR;
+      if (own_b && ib == nx - 1 && b.mode[SIDE_RIGHT] == BC_MUR) dEy[j * p + nx] = ob.eywR;
+    }
+    if (WR && A.W.on) {
+      // a8 on the producer side, sums in the order of em_strips
+      const RestrW<float>& Wr = A.W;
+      auto gsum = [&](float va_, float vb_) {
+        float acc = va_ + vb_;
+        if (rw == 4) {
+          acc = acc + __shfl_down_sync(0xffffffffu, va_, 1);
+          acc = acc + __shfl_down_sync(0xffffffffu, vb_, 1);
+        }
+        return acc;
+      };
+      if (j > 0 && j < ny && jq == 0) {
+        const float acc = gsum(oa.en_x, ob.en_x);
+        if (hx && Jc >= Wr.jlo && Jc <= Wr.jhi) Wr.cEx[Jc * Wr.cp + Ic] = acc * Wr.rinv;
+      }
+      if (j == 1 && b.mode[SIDE_BOTTOM] == BC_MUR) {     // fine row 0 (Mur), coarse row J0
+        const float acc = gsum(oa.exw0, ob.exw0);
+        if (hx) Wr.cEx[Wr.J0 * Wr.cp + Ic] = acc * Wr.rinv;
+      }
+      if (j == ny - 1 && b.mode[SIDE_TOP] == BC_MUR) {   // fine row ny (Mur), coarse row J1
+        const float acc = gsum(oa.exwN, ob.exwN);
+        if (hx) Wr.cEx[Wr.J1 * Wr.cp + Ic] = acc * Wr.rinv;
+      }
+      if (j < ny) {
+        const float eR = ia == nx - 1 ? oa.eywR : ob.eywR;
+        eacc_a = jq == 0 ? oa.en_y : eacc_a + oa.en_y;
+        eaccL = jq == 0 ? ob.eywL : eaccL + ob.eywL;
+        eaccR = jq == 0 ? eR : eaccR + eR;
+        if (jq == rw - 1) {
+          if (hy) Wr.cEy[Jc * Wr.cp + Ic] = eacc_a * Wr.rinv;
+          if (own_b && ib == 1 && b.mode[SIDE_LEFT] == BC_MUR) Wr.cEy[Jc * Wr.cp + Wr.I0] = eaccL * Wr.rinv;
+          if (((own_a && ia == nx - 1) || (own_b && ib == nx - 1)) && b.mode[SIDE_RIGHT] == BC_MUR)
+            Wr.cEy[Jc * Wr.cp + Wr.I1] = eaccR * Wr.rinv;
+        }
+      }
+      if (++jq == rw) { jq = 0; ++Jc; }
+    }
+    exp_ = exc;
+    exc = cur.exn;
+    eyp = cur.eyc;
+    hzp = hz;
+    nc = cur.nn;
+  }
+}
+
+// resident blocks per SM the two-column kernels' registers allow
+constexpr int kEm2MinBlocks = 6;
+
+template <bool WR = false, int RW = 0>
+__device__ __forceinline__ void em_segment2(const EmArgs<float>& A, int blk) {
+  if (blk < A.ncfb) em_cfb<float>(A, blk);
+  else em_strips2<WR, RW>(A, blk - A.ncfb);
+}
+
+// k_em with two node columns per lane (FP32, no CPML)
+template <bool WR = false, int RW = 0>
+__global__ void __launch_bounds__(32 * EM_WARPS, kEm2MinBlocks) k_em_w2(EmArgs<float> A) {
+  pdl_enter();
+  em_segment2<WR, RW>(A, blockIdx.x);
+}
+
 
 template <class T, bool PML = false, bool WR = false, int RW = 0>
 __global__ void __launch_bounds__(32 * EM_WARPS, kEmMinBlocks<T>) k_em(EmArgs<T> A) {

@@ -77,6 +77,8 @@ def load():
         "dmr_stats": (c_int, [P, POINTER(c_double)]),
         "dmr_set_graphs": (c_int, [P, c_int]),
         "dmr_set_launch_shape": (c_int, [P, c_int32]),
+        "dmr_set_strip_columns": (c_int, [P, c_int32]),
+        "dmr_get_launch_shape": (c_int, [P, POINTER(c_int32)]),
         "dmr_set_persistent": (c_int, [P, c_int, c_int32, c_int32]),
         "dmr_test_stall": (c_int, [P, c_int, c_int64]),
         "dmr_set_timing": (c_int, [P, c_int]),
@@ -237,6 +239,17 @@ class Run:
     def set_launch_shape(self, warps_per_sm):
         """Strip height of the EM launches as a warps-per-SM target."""
         self._check(self.lib.dmr_set_launch_shape(self.ctx, int(warps_per_sm)))
+
+    def set_strip_columns(self, columns_per_lane):
+        """Node columns per lane of the EM strips (1 or 2; same results)."""
+        self._check(self.lib.dmr_set_strip_columns(self.ctx, int(columns_per_lane)))
+
+    def launch_shape(self):
+        """(warps per SM of the coarse step's launch, of the later fine
+        sub-steps, node columns per lane)."""
+        s = (c_int32 * 3)()
+        self._check(self.lib.dmr_get_launch_shape(self.ctx, s))
+        return tuple(s)
 
     def set_timing(self, on=True, classes=None):
         """Time every kernel class (on=True), none (on=False) or the named
