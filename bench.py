@@ -552,6 +552,9 @@ def run_ours(args):
     # (dmr_time_launch), at the start and at the end of the timed run.
     run = D.run_from_workload(w, device=dev)
     wps, trial = run.autotune()
+    if args.strip_columns:
+        run.set_strip_columns(args.strip_columns)
+    shape = run.launch_shape()
     forms0 = [run.time_launch(f, 20) for f in ((0, 1, 2) if cfg.get("r", 1) > 1 else (0, 1))]
     run.set_graphs(True)
     # one untimed period on the timed run: its first graph capture and
@@ -601,6 +604,8 @@ def run_ours(args):
                          "launch gaps included) / peak"}
     if len(forms0) > 2:
         roof["fine_substep"] = form_roof(2)
+        roof["fine_substep"]["kernel"] = ("k_em_w2 (two node columns per lane)" if shape[2] == 2
+                                          else "k_em (one node column per lane)")
 
     # uniform fine mesh on the same GPU: the comparison the metric names
     uni_rate = None
@@ -680,6 +685,9 @@ def run_ours(args):
     if rank == 0:
         c = config_of(w, args)
         c.update({"autotuned_warps_per_sm": wps, "autotune_trial_ms": [round(t, 5) for t in trial],
+                  "launch_shape": {"warps_per_sm_coarse_step": shape[0],
+                                   "warps_per_sm_fine_substeps": shape[1],
+                                   "node_columns_per_lane_fine_substeps": shape[2]},
                   "periods_timed": K, "simulated_ns": K / cfg["freq"] * 1e9,
                   "l2": "flushed (256 MB write) between timed periods",
                   "final_rect": final_rect,
@@ -715,6 +723,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cpu-all", action="store_true", help="skip the all-cores oracle figure")
     ap.add_argument("--batch-runs", type=int, default=64, help="runs of the batch64 workload")
+    ap.add_argument("--strip-columns", type=int, default=0, choices=[0, 1, 2],
+                    help="node columns per lane of the fine sub-steps of the timed run "
+                         "(0: the autotuner's choice); for profiling one kernel form")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         raise SystemExit("--steps >= 1 and --warmup >= 0")
