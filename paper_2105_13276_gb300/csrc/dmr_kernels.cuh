@@ -363,6 +363,90 @@ __device__ __forceinline__ void em_segment(const EmArgs<T>& A, int blk) {
   else em_strips<T, PML, WR, CG, RW>(A, blk - A.ncfb);
 }
 
+// em_strips for a block whose strips lie away from every side of the mesh:
+// node columns c0 - 1 .. c0 + STRIP_W within [1, nx - 2] and node rows within
+// [2, ny - 2] (so rows j0 - 1 .. j1 exist, no Mur, coarse-fine or PEC edge is
+// near, every lane holds a column and every node's E^2 sample takes both
+// neighbours).  The same operations as em_strips in the same order, without
+// the edge tests.
+template <class T>
+__device__ __forceinline__ void em_strips_interior(const EmArgs<T>& A, int bx, int sy) {
+  const Mesh<T>& m = A.m;
+  T* __restrict__ dEx = A.dEx;
+  T* __restrict__ dEy = A.dEy;
+  T* __restrict__ dHz = A.dHz;
+  T* __restrict__ dvx = A.dvx;
+  T* __restrict__ dvy = A.dvy;
+  const Step<T>& c = A.c;
+  const int rows = A.rows;
+  const int lane = threadIdx.x & 31;
+  const int p = m.p;
+  const int i = bx * STRIP_W - 1 + lane;
+  const int j0 = sy * rows, j1 = j0 + rows;
+  const bool own = lane >= 1 && lane <= STRIP_W;
+  const T inc = incident(c, i);
+  T exc = m.Ex[j0 * p + i], nc = m.n[j0 * p + i];
+  T exp_, eyp, hzp;
+  {
+    const int q = (j0 - 1) * p + i;
+    const T exm = m.Ex[q], eym = m.Ey[q], hzo = m.Hz[q];
+    const T eyr = __shfl_down_sync(0xffffffffu, eym, 1);
+    hzp = hzo - c.ch * ((eyr - eym) - (exc - exm));
+    exp_ = exm;
+    eyp = eym;
+  }
+  struct Row { T exn, eyc, hzo, vxo, vyo, nn; double s2; };
+  auto load_row = [&](int j) {
+    Row q;
+    const int id = j * p + i;
+    q.exn = m.Ex[id + p];
+    q.eyc = m.Ey[id];
+    q.hzo = m.Hz[id];
+    q.vxo = m.vx[id];
+    q.vyo = m.vy[id];
+    q.nn = m.n[id + p];
+    q.s2 = (c.accum && own) ? m.S2[id] : 0.0;
+    return q;
+  };
+  Row nxt = load_row(j0);
+  for (int j = j0; j < j1; ++j) {
+    const int id = j * p + i;
+    const Row cur = nxt;
+    if (j + 1 < j1) nxt = load_row(j + 1);
+    const T exn = cur.exn, eyc = cur.eyc, hzo = cur.hzo, vxo = cur.vxo, vyo = cur.vyo, nn = cur.nn;
+    const T eyr = __shfl_down_sync(0xffffffffu, eyc, 1);
+    const T hz = hzo - c.ch * ((eyr - eyc) - (exn - exc));
+    const T hzl = __shfl_up_sync(0xffffffffu, hz, 1);
+    const T exl = __shfl_up_sync(0xffffffffu, exc, 1);
+    const T ncr = __shfl_down_sync(0xffffffffu, nc, 1);
+    if (own) {
+      dHz[id] = hz;
+      if (c.accum) {
+        const T sx = T(0.5) * (exl * exl + exc * exc);
+        const T e = eyp + inc, f = eyc + inc;
+        const T sy2 = T(0.5) * (e * e + f * f);
+        m.S2[id] = cur.s2 + (double)(sx + sy2);
+      }
+      {
+        const T v = c.va * vxo - c.vb * exc;
+        dvx[id] = v;
+        dEx[id] = exc + c.ce * (hz - hzp) + c.cj * (nc + ncr) * v;
+      }
+      {
+        const T v = c.va * vyo - c.vb * (eyc + inc);
+        dvy[id] = v;
+        dEy[id] = eyc - c.ce * (hz - hzl) + c.cj * (nc + nn) * v;
+      }
+    }
+    exp_ = exc;
+    exc = exn;
+    eyp = eyc;
+    hzp = hz;
+    nc = nn;
+  }
+  (void)exp_;
+}
+
 template <class T, bool PML, bool WR, bool CG, int RW>
 __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
   const Mesh<T>& m = A.m;
@@ -379,6 +463,14 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
   const int sy = byb * EM_WARPS + (threadIdx.x >> 5);
   const int p = m.p, nx = m.nx, ny = m.ny;
   const int sw = A.sw;
+  if constexpr (!PML && !WR && !CG) {
+    // a block away from every side takes the path without edge tests
+    const int bj0 = byb * EM_WARPS * rows, bj1 = bj0 + EM_WARPS * rows;
+    if (sw == STRIP_W && bx * sw >= 2 && bx * sw + sw <= nx - 2 && bj0 >= 2 && bj1 <= ny - 1) {
+      em_strips_interior<T>(A, bx, sy);
+      return;
+    }
+  }
   const int i = bx * sw - 1 + lane;
   const int j0 = sy * rows;
   if (j0 > ny) return;                       // whole warp leaves together
@@ -734,6 +826,115 @@ __device__ __forceinline__ Col2 col2_update(const Step<float>& c, const Bnd<floa
   return o;
 }
 
+// em_strips2 for a block away from every side of the mesh: node columns
+// c0 - 2 .. c0 + 61 within [1, nx - 2] and node rows within [2, ny - 2], so
+// every lane holds two valid columns and no Mur, coarse-fine or PEC edge is
+// near.  The same operations in the same order, without the edge tests.
+template <bool WR, int RW>
+__device__ __forceinline__ void em_strips2_interior(const EmArgs<float>& A, int bx, int sy) {
+  const Mesh<float>& m = A.m;
+  float* __restrict__ dEx = A.dEx;
+  float* __restrict__ dEy = A.dEy;
+  float* __restrict__ dHz = A.dHz;
+  float* __restrict__ dvx = A.dvx;
+  float* __restrict__ dvy = A.dvy;
+  const Step<float>& c = A.c;
+  const int rows = A.rows;
+  const int lane = threadIdx.x & 31;
+  const int p = m.p;
+  const int ia = bx * STRIP_W2 - 2 + 2 * lane;
+  const int j0 = sy * rows, j1 = j0 + rows;
+  const bool lo = lane >= 1 && lane <= STRIP_W2 / 2;
+  const float inc_a = incident(c, ia), inc_b = incident(c, ia + 1);
+  float2 exc = *reinterpret_cast<const float2*>(m.Ex + j0 * p + ia);
+  float2 nc = *reinterpret_cast<const float2*>(m.n + j0 * p + ia);
+  float2 eyp, hzp;
+  {
+    const int q = (j0 - 1) * p + ia;
+    const float2 exm = *reinterpret_cast<const float2*>(m.Ex + q);
+    const float2 eym = *reinterpret_cast<const float2*>(m.Ey + q);
+    const float2 hzo = *reinterpret_cast<const float2*>(m.Hz + q);
+    const float eyr_b = __shfl_down_sync(0xffffffffu, eym.x, 1);
+    hzp.x = hzo.x - c.ch * ((eym.y - eym.x) - (exc.x - exm.x));
+    hzp.y = hzo.y - c.ch * ((eyr_b - eym.y) - (exc.y - exm.y));
+    eyp = eym;
+  }
+  struct Row2 { float2 exn, eyc, hzo, vxo, vyo, nn; double2 s2; };
+  auto load_row = [&](int j) {
+    Row2 q;
+    const int id = j * p + ia;
+    q.exn = *reinterpret_cast<const float2*>(m.Ex + id + p);
+    q.eyc = *reinterpret_cast<const float2*>(m.Ey + id);
+    q.hzo = *reinterpret_cast<const float2*>(m.Hz + id);
+    q.vxo = *reinterpret_cast<const float2*>(m.vx + id);
+    q.vyo = *reinterpret_cast<const float2*>(m.vy + id);
+    q.nn = *reinterpret_cast<const float2*>(m.n + id + p);
+    q.s2 = (c.accum && lo) ? *reinterpret_cast<const double2*>(m.S2 + id) : make_double2(0.0, 0.0);
+    return q;
+  };
+  Row2 nxt = load_row(j0);
+  constexpr int rw = WR ? RW : 1;
+  const bool hx = WR && lo && (ia % rw) == 0;
+  const int Ic = WR ? A.W.I0 + ia / rw : 0;
+  const bool hy = hx && Ic >= A.W.ilo && Ic <= A.W.ihi;
+  int jq = 0, Jc = WR ? A.W.J0 + j0 / rw : 0;
+  float eacc_a = 0.f;
+  for (int j = j0; j < j1; ++j) {
+    const int id = j * p + ia;
+    const Row2 cur = nxt;
+    if (j + 1 < j1) nxt = load_row(j + 1);
+    const float eyr_b = __shfl_down_sync(0xffffffffu, cur.eyc.x, 1);
+    float2 hz;
+    hz.x = cur.hzo.x - c.ch * ((cur.eyc.y - cur.eyc.x) - (cur.exn.x - exc.x));
+    hz.y = cur.hzo.y - c.ch * ((eyr_b - cur.eyc.y) - (cur.exn.y - exc.y));
+    const float hzl_a = __shfl_up_sync(0xffffffffu, hz.y, 1);
+    const float exl_a = __shfl_up_sync(0xffffffffu, exc.y, 1);
+    const float ncr_b = __shfl_down_sync(0xffffffffu, nc.x, 1);
+    const float vxa = c.va * cur.vxo.x - c.vb * exc.x, vxb = c.va * cur.vxo.y - c.vb * exc.y;
+    const float enxa = exc.x + c.ce * (hz.x - hzp.x) + c.cj * (nc.x + nc.y) * vxa;
+    const float enxb = exc.y + c.ce * (hz.y - hzp.y) + c.cj * (nc.y + ncr_b) * vxb;
+    const float vya = c.va * cur.vyo.x - c.vb * (cur.eyc.x + inc_a);
+    const float vyb = c.va * cur.vyo.y - c.vb * (cur.eyc.y + inc_b);
+    const float enya = cur.eyc.x - c.ce * (hz.x - hzl_a) + c.cj * (nc.x + cur.nn.x) * vya;
+    const float enyb = cur.eyc.y - c.ce * (hz.y - hz.x) + c.cj * (nc.y + cur.nn.y) * vyb;
+    if (lo) {
+      *reinterpret_cast<float2*>(dHz + id) = hz;
+      if (c.accum) {
+        float sx = 0.5f * (exl_a * exl_a + exc.x * exc.x);
+        float e = eyp.x + inc_a, f = cur.eyc.x + inc_a;
+        const float e2a = sx + 0.5f * (e * e + f * f);
+        sx = 0.5f * (exc.x * exc.x + exc.y * exc.y);
+        e = eyp.y + inc_b;
+        f = cur.eyc.y + inc_b;
+        const float e2b = sx + 0.5f * (e * e + f * f);
+        *reinterpret_cast<double2*>(m.S2 + id) = make_double2(cur.s2.x + (double)e2a, cur.s2.y + (double)e2b);
+      }
+      *reinterpret_cast<float2*>(dvx + id) = make_float2(vxa, vxb);
+      *reinterpret_cast<float2*>(dEx + id) = make_float2(enxa, enxb);
+      *reinterpret_cast<float2*>(dvy + id) = make_float2(vya, vyb);
+      *reinterpret_cast<float2*>(dEy + id) = make_float2(enya, enyb);
+    }
+    if (WR && A.W.on) {
+      const RestrW<float>& Wr = A.W;
+      if (jq == 0) {
+        float acc = enxa + enxb;
+        if (rw == 4) {
+          acc = acc + __shfl_down_sync(0xffffffffu, enxa, 1);
+          acc = acc + __shfl_down_sync(0xffffffffu, enxb, 1);
+        }
+        if (hx && Jc >= Wr.jlo && Jc <= Wr.jhi) Wr.cEx[Jc * Wr.cp + Ic] = acc * Wr.rinv;
+      }
+      eacc_a = jq == 0 ? enya : eacc_a + enya;
+      if (jq == rw - 1 && hy) Wr.cEy[Jc * Wr.cp + Ic] = eacc_a * Wr.rinv;
+      if (++jq == rw) { jq = 0; ++Jc; }
+    }
+    exc = cur.exn;
+    eyp = cur.eyc;
+    hzp = hz;
+    nc = cur.nn;
+  }
+}
+
 template <bool WR, int RW>
 __device__ __forceinline__ void em_strips2(const EmArgs<float>& A, int blk) {
   const Mesh<float>& m = A.m;
@@ -750,6 +951,14 @@ __device__ __forceinline__ void em_strips2(const EmArgs<float>& A, int blk) {
   const int sy = byb * EM_WARPS + (threadIdx.x >> 5);
   const int p = m.p, nx = m.nx, ny = m.ny;
   const int sw = A.sw;                       // owned columns per strip (even)
+  {
+    // a block away from every side takes the path without edge tests
+    const int bj0 = byb * EM_WARPS * rows, bj1 = bj0 + EM_WARPS * rows;
+    if (sw == STRIP_W2 && bx * sw >= 3 && bx * sw + 63 <= nx && bj0 >= 2 && bj1 <= ny - 1) {
+      em_strips2_interior<WR, RW>(A, bx, sy);
+      return;
+    }
+  }
   const int ia = bx * sw - 2 + 2 * lane, ib = ia + 1;
   const int j0 = sy * rows;
   if (j0 > ny) return;                       // whole warp leaves together
