@@ -323,6 +323,29 @@ def test_launch_shapes_give_identical_results(precision):
     assert e.value.code == D.EINVAL
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_launch_shapes_identical_with_interior_blocks(precision):
+    """Meshes several strips wide and tall: blocks away from every side take
+    the strip path without edge tests, the others the full one, and which
+    blocks do depends on the strip height.  Every height gives the same bits,
+    so the two paths agree node for node."""
+    w = W.small_dmr(nx=130, ny=100, rect=(40, 30, 90, 70), precision=precision)
+    NT = w["cfg"]["steps_per_period"]
+    ref = D.run_from_workload(w)
+    ref.set_graphs(True)
+    ref.set_launch_shape(1)
+    ref.advance(2 * NT + 5)
+    for wps in (16, 96, 1024):
+        run = D.run_from_workload(w)
+        run.set_graphs(True)
+        run.set_launch_shape(wps)
+        run.advance(2 * NT + 5)
+        assert run.get_patch() == ref.get_patch()
+        for level in (0, 1):
+            for name in FIELDS + ("S2",):
+                assert np.array_equal(run.read(name, level), ref.read(name, level)), (wps, level, name)
+
+
 def test_vacuum_stays_exactly_zero():
     w = W.small_dmr()
     w = dict(w, seeds=[(0.0, 0.5, 0.5, 0.1, 0.1)])

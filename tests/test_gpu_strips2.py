@@ -8,9 +8,10 @@ sums, the rectangle log and the FP64 totals, with growth, CUDA graphs and
 programmatic launches, for r = 2 and 4 (two columns in the last fine
 sub-step, which writes the fine->coarse means), r = 3 (sub-step 2 with two
 columns, the last one with one), rectangles on the domain edges (fine Mur
-sides), the threshold-line growth, several strips with a ragged last one and
-odd and even mesh widths (a Mur column at either lane slot).  One case is
-also checked against the FP64 oracle directly.
+sides), the threshold-line growth, several strips with a ragged last one,
+odd and even mesh widths (a Mur column at either lane slot) and rectangles
+wide enough for strips away from every side (the path without edge tests).
+One case is also checked against the FP64 oracle directly.
 """
 import numpy as np
 import pytest
@@ -55,6 +56,10 @@ def _case(name):
         return W.small_dmr(precision=1, growth=2, n_th=3e16)
     if name == "r2_many_strips":
         return W.small_dmr(nx=131, ny=70, rect=(40, 30, 101, 52), precision=1)
+    if name == "r2_wide":      # fine strips away from every side (the path without edge tests)
+        return W.small_dmr(nx=160, ny=64, rect=(20, 10, 100, 54), precision=1)
+    if name == "r4_wide":
+        return W.small_dmr(nx=100, ny=64, r=4, rect=(20, 10, 60, 40), precision=1)
     raise KeyError(name)
 
 
@@ -81,7 +86,8 @@ def _same(a, b, w, tag):
 
 
 @pytest.mark.parametrize("name", ["r2", "r2_edges_low", "r2_edges_high", "r2_odd_nx", "r4",
-                                  "r4_edges", "r3", "r2_lines", "r2_many_strips"])
+                                  "r4_edges", "r3", "r2_lines", "r2_many_strips", "r2_wide",
+                                  "r4_wide"])
 def test_two_columns_per_lane_give_the_same_bits(name):
     w = _case(name)
     ref = _run(w, 1)
