@@ -1118,10 +1118,19 @@ struct Engine final : Base {
 
   // host side of the period end: read the control block, stability guard,
   // growth policy (or replay), expansion
+  // pinned host copy of the control block (a copy into pageable memory is
+  // staged through a driver buffer); host memory, allocated at first use
+  dmr::Ctl* hctl = nullptr;
+  ~Engine() override {
+    if (hctl) cudaFreeHost(hctl);
+  }
   int period_end_host(bool graph_ran = false) {
-    dmr::Ctl hc;
-    if (int s = ck(cudaMemcpyAsync(&hc, ctl, sizeof hc, cudaMemcpyDeviceToHost, st), "read control block")) return s;
+    if (!hctl)
+      if (int s = ck(cudaHostAlloc(reinterpret_cast<void**>(&hctl), sizeof(dmr::Ctl), cudaHostAllocDefault),
+                     "pinned control block")) { hctl = nullptr; return s; }
+    if (int s = ck(cudaMemcpyAsync(hctl, ctl, sizeof(dmr::Ctl), cudaMemcpyDeviceToHost, st), "read control block")) return s;
     if (int s = ck(cudaStreamSynchronize(st), "period sync")) return s;
+    const dmr::Ctl hc = *hctl;
     harvest_period(graph_ran);
     return period_decide(hc);
   }
