@@ -90,7 +90,13 @@ typedef enum {
  */
 typedef struct dmr_config {
   int32_t nx, ny;            /* coarse cells along x and y (>= 4 each) */
-  int32_t r;                 /* refinement factor (Sec. III.C); 1 = uniform mesh, no patch */
+  int32_t r;                 /* refinement factor (Sec. III.C); 1 = uniform mesh, no patch.
+                                Note: the coarse-fine coupling (Eq. 5b into the fine
+                                sides, the fine mean back into the coarse E) has a
+                                slowly growing mode (spectral radius 1.0005-1.0045 per
+                                coarse step in vacuum, more at r = 4 than r = 2 on some
+                                shapes).  Collisional plasma damps it in the benchmark
+                                runs; long r = 4 runs can end in DMR_EUNSTABLE. */
   int32_t n_lambda;          /* coarse cells per wavelength: dx_c = lambda / n_lambda */
   int32_t steps_per_period;  /* N_T coarse EM steps per period: dt_c = 1/(f N_T);
                                 Courant c dt/dx = n_lambda/N_T must be <= 1/sqrt(2) */
