@@ -29,8 +29,7 @@ E lives on integer time levels, H and v on half levels.
 All arithmetic is written so that it also runs on complex128 arrays
 (complex-step derivatives): comparisons use the real part.
 
-Readings of passages the paper leaves open are stated where they are used;
-each is listed again in the design notes of the repository.
+Readings of passages the paper leaves open are stated where they are used.
 Parity unpinned: the spatio-temporal physics magnitudes (filament spacing,
 front speed), whose figures are missing from the paper.
 """

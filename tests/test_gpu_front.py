@@ -9,8 +9,8 @@ n = 1e19 m^-3 crossing on the central x line) is tracked every 50 periods
 and its velocity fitted where it lies 1.0 to 0.3 wavelengths from the left
 edge; the velocities agree within 2 %.  (The absolute velocity follows
 the ionization and diffusion readings, which the paper leaves to cited
-works; r = 4 runs into the coupling instability recorded in the design notes
-and is not asserted.)"""
+works; at r = 4 a slowly growing mode of the coarse-fine coupling drives the
+density up near the interface, so r = 4 is not asserted.)"""
 import numpy as np
 import pytest
 
