@@ -303,6 +303,32 @@ def run_batch(args):
     ms = sum(x.elapsed_time(y) for x, y in evs)
     launches = b.launch_count() - l0
     fine = [b.runs[q].stats()["fine_cells"] for q in range(len(ws))]
+    # roofline of the dominant launch: the autotuner's trials time the
+    # phase-1 launch (every run's coarse step and first fine sub-step) at
+    # the start, a period boundary: 44 B per node (no E^2 sample) over the
+    # coarse nodes and the starting rectangles' fine nodes
+    peak, src = measured_peak()
+    def nodes(w):
+        c = w["cfg"]
+        n = (c["nx"] + 1) * (c["ny"] + 1)
+        if c.get("r", 1) > 1 and w.get("rect") is not None:
+            i0, j0, i1, j1 = w["rect"]
+            n += (c["r"] * (i1 - i0) + 1) * (c["r"] * (j1 - j0) + 1)
+        return n
+    ph1_bytes = 44.0 * sum(nodes(w) for w in ws)
+    ph1_ms = min(trial)
+    step_bytes = sum(period_em_bytes(w["cfg"], w.get("rect"), 4) for w in ws)
+    roof = {"bound": "hbm", "kernel": "k_em_batch phase 1 (every run's coarse step and first fine "
+                                      "sub-step), period-boundary form, at the start",
+            "achieved": ph1_bytes / (ph1_ms / 1e3) / 1e9, "peak": peak,
+            "peak_source": src + " (burst copy)", "unit": "GB/s",
+            "frac": ph1_bytes / (ph1_ms / 1e3) / 1e9 / peak, "traffic": None,
+            "avg_launch_us": 1e3 * ph1_ms, "algorithmic_bytes_per_launch": ph1_bytes,
+            "timed_region": "the batch autotuner's trial: CUDA-graph replays of 5 back-to-back "
+                            "copies of the launch at the chosen strip height",
+            "frac_step": step_bytes / (ms / K / 1e3) / 1e9 / peak,
+            "step_note": "frac_step: algorithmic bytes of all EM launches of a period (every run at "
+                         "its starting rectangle) / the mean timed period / peak"}
     line = {"metric": METRIC, "value": K * upp / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": K, "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -312,7 +338,7 @@ def run_batch(args):
                        "autotuned_warps_per_sm": wps, "autotune_trial_ms": trial,
                        "fine_cells_end_total": sum(fine),
                        "l2": "flushed (256 MB write) between timed periods"},
-            "gpu_launches": launches, "clocks": clocks}
+            "roofline": roof, "gpu_launches": launches, "clocks": clocks}
     print(json.dumps(line))
     return 0
 
