@@ -409,6 +409,30 @@ def test_full_size_dmr_512_fp32_with_growth():
         assert rel_l2(run.read("erms", level).T, sim.erms(level)) <= TOL32
 
 
+@pytest.mark.parametrize("r", [2, 4])
+def test_full_size_large_fp32_in_the_bench_launch_shape(r):
+    """The 2048x1024 workloads (eight seeds, the rectangle at 15 % of the
+    domain) in the launch shape the benchmark times: the autotuner's strip
+    heights and lane width (two node columns per lane in the fine sub-steps
+    there), blocks away from every side on the path without edge tests,
+    CUDA graphs.  Against the FP64 oracle: at r = 2 one period and three
+    steps (the oracle's rectangle log replayed), at r = 4 nine coarse steps
+    (36 fine sub-steps), read mid-period."""
+    w = W.large_dmr(r=r)
+    NT = w["cfg"]["steps_per_period"]
+    steps = NT + 3 if r == 2 else 9
+    sim = O.sim_from_workload(w)
+    sim.advance(steps)
+    run = D.run_from_workload(w)
+    run.autotune()
+    run.set_graphs(True)
+    if sim.log:
+        run.replay_log(sim.log)
+    run.advance(steps)
+    assert run.get_patch() == tuple(sim.rect)
+    compare(run, sim, TOL32, verbose=True)
+
+
 def test_capacity_error_and_state_errors():
     w = W.small_dmr()
     cfg = dict(w["cfg"], patch_cap_cells=4 * 12 * 10)
