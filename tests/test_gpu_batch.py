@@ -85,6 +85,35 @@ def test_batched_run_matches_oracle():
                 assert rel < 1e-12, (q, level, name, rel)
 
 
+def test_full_size_batch_sampled_runs_match_oracle():
+    """The 64-run batch the benchmark times (coarse 128^2 to 1024^2, r = 2,
+    FP32), autotuned and in CUDA graphs, over one period and five steps; one
+    run of each size (the first in the batch) against the FP64 oracle."""
+    ws = W.batch_runs(64)
+    steps = 64 + 5
+    b = D.batch_from_workloads(ws)
+    b.autotune()
+    b.set_graphs(True)
+    b.advance(steps)
+    picks = {}
+    for q, w in enumerate(ws):
+        picks.setdefault(w["cfg"]["nx"], q)
+    assert sorted(picks) == [128, 256, 512, 1024]
+    for nx, q in sorted(picks.items()):
+        sim = O.sim_from_workload(ws[q])
+        sim.advance(steps)
+        run = b.runs[q]
+        assert run.get_patch() == tuple(sim.rect)
+        for level, mesh in ((0, sim.coarse), (1, sim.fine)):
+            for name in FIELDS + ("S2",):
+                g = run.read(name, level).T.astype(np.float64)
+                o = getattr(mesh, name)
+                rel = np.linalg.norm(g - o) / max(np.linalg.norm(o), 1e-300)
+                assert rel < 1e-4, (nx, q, level, name, rel)
+        st = run.stats()
+        assert abs(st["N_e"] / sim.N_e - 1) < 1e-4, (nx, q)
+
+
 @pytest.mark.parametrize("graphs", [False, True])
 def test_batch_with_threshold_line_growth(graphs):
     """Runs with both growth policies in one batch (Sec. III.D threshold lines

@@ -356,6 +356,45 @@ def test_vacuum_stays_exactly_zero():
             assert not np.any(run.read(name, level)), (level, name)
 
 
+def test_full_size_uniform_256_fp64_in_the_bench_launch_shape():
+    """The uniform workload (256^2 at lambda/64, FP64) in the launch shape the
+    benchmark times (autotuned strip height, CUDA graphs) against the FP64
+    oracle over two periods and seven steps, with the period totals."""
+    w = W.uniform_256(precision=0)
+    NT = w["cfg"]["steps_per_period"]
+    steps = 2 * NT + 7
+    sim = O.sim_from_workload(w)
+    sim.advance(steps)
+    run = D.run_from_workload(w)
+    run.autotune()
+    run.set_graphs(True)
+    run.advance(steps)
+    compare(run, sim, TOL64, levels=(0,), verbose=True)
+    st = run.stats()
+    for key, ref in (("N_e", sim.N_e), ("P_abs", sim.P_abs), ("W_abs", sim.W_abs)):
+        assert abs(st[key] / ref - 1) < TOL64, key
+
+
+def test_full_size_dmr_512_fp64_in_the_bench_launch_shape():
+    """The DMR benchmark geometry (coarse 512^2 at lambda/32, r = 2) in FP64,
+    autotuned and in CUDA graphs, free-running (its own period-end decisions)
+    against the FP64 oracle over two periods and seven steps."""
+    w = W.dmr_512_r2(precision=0)
+    NT = w["cfg"]["steps_per_period"]
+    steps = 2 * NT + 7
+    sim = O.sim_from_workload(w)
+    sim.advance(steps)
+    run = D.run_from_workload(w)
+    run.autotune()
+    run.set_graphs(True)
+    run.advance(steps)
+    assert run.get_patch() == tuple(sim.rect)
+    compare(run, sim, TOL64, verbose=True)
+    st = run.stats()
+    for key, ref in (("N_e", sim.N_e), ("P_abs", sim.P_abs), ("W_abs", sim.W_abs)):
+        assert abs(st[key] / ref - 1) < TOL64, key
+
+
 @pytest.mark.parametrize("periods", [10, 100])
 def test_full_size_dmr_512_fp32_graphs(periods):
     """The benchmark workload (coarse 512^2 at lambda/32, r = 2, FP32, CUDA
