@@ -34,6 +34,15 @@ sys.path.insert(0, ROOT)
 METRIC = "fine-equiv cell-updates/s, DMR vs uniform fine mesh, % of HBM BW roofline"
 UNIT = "fine-equiv cell-updates/s"
 FALLBACK_HBM_GBS = 6800.0
+# FP64 arithmetic: 1.25 TFLOP/s dense (an FMA counted as two flops) at 2070 MHz
+# over 152 SMs is 2 FP64 FMAs per clock per SM.  The kernels are compiled
+# without contraction, so each FP64 add or multiply is one instruction at that
+# rate: at most 152 x 2.07 GHz x 2 = 0.629 T FP64 operations per second.
+FP64_OPS_PEAK_T = 152 * 2.07e9 * 2 / 1e12
+# FP64 operations per node of an EM step (the fused H, v, E updates: 26; the
+# E^2 sample adds 11), counted from the update formulas with the total field
+# Ey + E_inc formed once
+FP64_OPS_PER_NODE = (26.0, 37.0)
 
 
 def dist_env():
@@ -613,7 +622,9 @@ def run_ours(args):
 
     mid = form_roof(1)
     step_ach = em_bytes / (ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": "k_em2 (coarse step + first fine sub-step), mid-period form",
+    first = ("k_em2 (coarse step + first fine sub-step)" if cfg.get("r", 1) > 1
+             else "k_em (coarse step)")
+    roof = {"bound": "hbm", "kernel": first + ", mid-period form",
             "achieved": mid["achieved"], "peak": peak, "peak_source": src + " (burst copy)",
             "unit": "GB/s", "frac": mid["frac"], "traffic": recorded_traffic("k_em2", args.workload),
             "avg_launch_us": mid["avg_launch_us"],
@@ -632,6 +643,30 @@ def run_ours(args):
         roof["fine_substep"] = form_roof(2)
         roof["fine_substep"]["kernel"] = ("k_em_w2 (two node columns per lane)" if shape[2] == 2
                                           else "k_em (one node column per lane)")
+    if es == 8:
+        # FP64 runs are bound by the FP64 pipe, not by HBM: the same launches
+        # against the FP64 operation rate (the HBM view is kept under "hbm")
+        def alu_roof(q):
+            t_ms = 0.5 * (forms0[q][0] + forms1[q][0])
+            nodes = 0.5 * (forms0[q][1] + forms1[q][1]) / (11.0 * es + (16.0 if q == 1 else 0.0))
+            ops = FP64_OPS_PER_NODE[q] * nodes
+            ach = ops / (t_ms / 1e3) / 1e12
+            return {"achieved": ach, "frac": ach / FP64_OPS_PEAK_T, "avg_launch_us": 1e3 * t_ms,
+                    "fp64_ops_per_launch": ops, "nodes_per_launch": nodes}
+        hbm = dict(roof)
+        a_mid = alu_roof(1)
+        roof = {"bound": "alu", "kernel": first + ", mid-period form", "achieved": a_mid["achieved"],
+                "peak": FP64_OPS_PEAK_T, "unit": "TFLOP/s",
+                "peak_source": "derived: FP64 1.25 TFLOP/s dense at 2070 MHz over 152 SMs = 2 FP64 "
+                               "FMAs per clock per SM; the kernels issue FP64 adds and multiplies "
+                               "unfused, one operation each at that rate",
+                "frac": a_mid["frac"], "traffic": hbm["traffic"],
+                "avg_launch_us": a_mid["avg_launch_us"],
+                "fp64_ops_per_launch": a_mid["fp64_ops_per_launch"],
+                "ops_note": "37 FP64 operations per node with the E^2 sample, 26 without; nodes "
+                            "from the launch's algorithmic bytes (11 words per node, + 16 B of "
+                            "the E^2 sum)",
+                "boundary_form": alu_roof(0), "timed_region": hbm["timed_region"], "hbm": hbm}
 
     # uniform fine mesh on the same GPU: the comparison the metric names
     uni_rate = None
