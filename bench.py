@@ -34,15 +34,17 @@ sys.path.insert(0, ROOT)
 METRIC = "fine-equiv cell-updates/s, DMR vs uniform fine mesh, % of HBM BW roofline"
 UNIT = "fine-equiv cell-updates/s"
 FALLBACK_HBM_GBS = 6800.0
-# FP64 arithmetic: 1.25 TFLOP/s dense (an FMA counted as two flops) at 2070 MHz
-# over 152 SMs is 2 FP64 FMAs per clock per SM.  The kernels are compiled
-# without contraction, so each FP64 add or multiply is one instruction at that
-# rate: at most 152 x 2.07 GHz x 2 = 0.629 T FP64 operations per second.
-FP64_OPS_PEAK_T = 152 * 2.07e9 * 2 / 1e12
-# FP64 operations per node of an EM step (the fused H, v, E updates: 26; the
-# E^2 sample adds 11), counted from the update formulas with the total field
-# Ey + E_inc formed once
-FP64_OPS_PER_NODE = (26.0, 37.0)
+# FP64 arithmetic: 1.25 TFLOP/s dense (an FMA counted as two flops); at
+# 2070 MHz over 152 SMs that is 2 FP64 instructions (FMA, add or multiply)
+# per clock per SM, 0.629 T FP64 instructions per second.
+FP64_TFLOPS_PEAK = 1.25
+FP64_INSTR_PEAK_T = 152 * 2.07e9 * 2 / 1e12
+# per node of an EM step without / with the E^2 sample: FP64 flops of the
+# update formulas (H 5, v and E along x 10, along y 11 with the total field
+# Ey + E_inc formed once; the E^2 sample 11), and the FP64 instructions the
+# kernels issue for them (each a * b + c one fused multiply-add)
+FP64_FLOPS_PER_NODE = (26.0, 37.0)
+FP64_INSTR_PER_NODE = (19.0, 28.0)
 
 
 def dist_env():
@@ -645,27 +647,31 @@ def run_ours(args):
                                           else "k_em (one node column per lane)")
     if es == 8:
         # FP64 runs are bound by the FP64 pipe, not by HBM: the same launches
-        # against the FP64 operation rate (the HBM view is kept under "hbm")
+        # against the FP64 rate (the HBM view is kept under "hbm")
         def alu_roof(q):
             t_ms = 0.5 * (forms0[q][0] + forms1[q][0])
             nodes = 0.5 * (forms0[q][1] + forms1[q][1]) / (11.0 * es + (16.0 if q == 1 else 0.0))
-            ops = FP64_OPS_PER_NODE[q] * nodes
-            ach = ops / (t_ms / 1e3) / 1e12
-            return {"achieved": ach, "frac": ach / FP64_OPS_PEAK_T, "avg_launch_us": 1e3 * t_ms,
-                    "fp64_ops_per_launch": ops, "nodes_per_launch": nodes}
+            flops = FP64_FLOPS_PER_NODE[q] * nodes
+            ach = flops / (t_ms / 1e3) / 1e12
+            ins = FP64_INSTR_PER_NODE[q] * nodes / (t_ms / 1e3) / 1e12
+            return {"achieved": ach, "frac": ach / FP64_TFLOPS_PEAK, "avg_launch_us": 1e3 * t_ms,
+                    "fp64_flops_per_launch": flops, "nodes_per_launch": nodes,
+                    "fp64_pipe": {"instructions_per_s_T": ins, "peak_T": FP64_INSTR_PEAK_T,
+                                  "frac": ins / FP64_INSTR_PEAK_T}}
         hbm = dict(roof)
         a_mid = alu_roof(1)
         roof = {"bound": "alu", "kernel": first + ", mid-period form", "achieved": a_mid["achieved"],
-                "peak": FP64_OPS_PEAK_T, "unit": "TFLOP/s",
-                "peak_source": "derived: FP64 1.25 TFLOP/s dense at 2070 MHz over 152 SMs = 2 FP64 "
-                               "FMAs per clock per SM; the kernels issue FP64 adds and multiplies "
-                               "unfused, one operation each at that rate",
+                "peak": FP64_TFLOPS_PEAK, "unit": "TFLOP/s",
+                "peak_source": "nominal FP64 1.25 TFLOP/s dense (FMA = 2 flops) = 2 FP64 "
+                               "instructions per clock per SM at 2070 MHz over 152 SMs",
                 "frac": a_mid["frac"], "traffic": hbm["traffic"],
                 "avg_launch_us": a_mid["avg_launch_us"],
-                "fp64_ops_per_launch": a_mid["fp64_ops_per_launch"],
-                "ops_note": "37 FP64 operations per node with the E^2 sample, 26 without; nodes "
-                            "from the launch's algorithmic bytes (11 words per node, + 16 B of "
-                            "the E^2 sum)",
+                "fp64_flops_per_launch": a_mid["fp64_flops_per_launch"],
+                "fp64_pipe": a_mid["fp64_pipe"],
+                "ops_note": "37 FP64 flops per node with the E^2 sample, 26 without, issued as 28 / "
+                            "19 FP64 instructions (fused multiply-adds); fp64_pipe: those "
+                            "instructions against 2 per clock per SM; nodes from the launch's "
+                            "algorithmic bytes (11 words per node, + 16 B of the E^2 sum)",
                 "boundary_form": alu_roof(0), "timed_region": hbm["timed_region"], "hbm": hbm}
 
     # uniform fine mesh on the same GPU: the comparison the metric names

@@ -1,9 +1,9 @@
 """Build ``libdmr.so`` in-tree with nvcc for sm_103a (GB300).
 
 One translation unit, one -gencode, no cmake: a few seconds on x86 and on
-the Arm GPU hosts.  ``-fmad=false`` keeps the FP64 path free of FMA
-contraction (it repeats the rounding of a plain unfused evaluation); the
-kernels are memory-bound, so this costs nothing measurable.
+the Arm GPU hosts.  ``-fmad=false``: nothing is contracted behind the
+source's back; the fused multiply-adds of the FP64 update formulas are
+written out in the kernels, the same in every code path.
 """
 from __future__ import annotations
 

@@ -7,8 +7,11 @@
 // Threads map x to threadIdx.x so each warp reads 32 consecutive elements.
 //
 // The stencils are HBM-bound (~0.7 flop/byte): no tensor cores.  Arithmetic
-// is compiled without FMA contraction so that the FP64 path repeats the
-// rounding of a plain unfused evaluation.
+// is compiled without FMA contraction.  The update formulas of Eqs. 1-3 go
+// through the helpers below, which every code path calls, so that the paths
+// give identical bits: in FP32 they evaluate a * b + c with the product
+// rounded first, in FP64 as one fused multiply-add (FP64 arithmetic, not
+// HBM, bounds the FP64 launches on this part).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -87,6 +90,30 @@ __device__ __forceinline__ T incident(const Step<T>& c, int i) {
   return c.E0 * (c.sphi * c.ckx[i] - c.cphi * c.skx[i]);
 }
 
+// a * b + c: FP32 with the product rounded first, FP64 fused
+__device__ __forceinline__ float mad_(float a, float b, float c) { return a * b + c; }
+__device__ __forceinline__ double mad_(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Eq. 2: Hz^{n+1/2} = Hz^{n-1/2} - ch curl, curl = dEy/dx - dEx/dy in cell units
+template <class T>
+__device__ __forceinline__ T upd_h(const Step<T>& c, T hzo, T curl) { return mad_(-c.ch, curl, hzo); }
+// Eq. 3 (Crank-Nicolson momentum): v' = va v - vb E
+template <class T>
+__device__ __forceinline__ T upd_v(const Step<T>& c, T vo, T e) { return mad_(c.va, vo, -(c.vb * e)); }
+// Eq. 1 at an x edge: Ex' = Ex + ce dH + cj (n_a + n_b) v'
+template <class T>
+__device__ __forceinline__ T upd_ex(const Step<T>& c, T exc, T dh, T ns, T v) {
+  return mad_(c.cj * ns, v, mad_(c.ce, dh, exc));
+}
+// Eq. 1 at a y edge: Ey' = Ey - ce dH + cj (n_a + n_b) v'
+template <class T>
+__device__ __forceinline__ T upd_ey(const Step<T>& c, T eyc, T dh, T ns, T v) {
+  return mad_(c.cj * ns, v, mad_(-c.ce, dh, eyc));
+}
+// mean of two squares, (a^2 + b^2) / 2
+template <class T>
+__device__ __forceinline__ T sq_mean(T a, T b) { return T(0.5) * mad_(a, a, b * b); }
+
 // Squared total field at node (i, j): mean of the existing Ex^2 edges along x
 // plus mean of the existing Ey^2 edges along y (incident added to Ey).
 template <class T>
@@ -95,7 +122,7 @@ __device__ __forceinline__ T node_e2(const Mesh<T>& m, const Step<T>& c, int i, 
   T sx, sy;
   if (i > 0 && i < m.nx) {
     T a = m.Ex[j * p + i - 1], b = m.Ex[j * p + i];
-    sx = T(0.5) * (a * a + b * b);
+    sx = sq_mean(a, b);
   } else if (i > 0) {
     T a = m.Ex[j * p + i - 1];
     sx = a * a;
@@ -106,7 +133,7 @@ __device__ __forceinline__ T node_e2(const Mesh<T>& m, const Step<T>& c, int i, 
   T inc = incident(c, i);
   if (j > 0 && j < m.ny) {
     T e = m.Ey[(j - 1) * p + i] + inc, f = m.Ey[j * p + i] + inc;
-    sy = T(0.5) * (e * e + f * f);
+    sy = sq_mean(e, f);
   } else if (j > 0) {
     T e = m.Ey[(j - 1) * p + i] + inc;
     sy = e * e;
@@ -152,10 +179,10 @@ __device__ __forceinline__ T coarse_new_ex(const Bnd<T>& b, int i, int J) {
   const T exm = load_ex<T, CG>(m, i, J - 1), exc = load_ex<T, CG>(m, i, J), exn = load_ex<T, CG>(m, i, J + 1);
   const T eym = load_ey<T, CG>(m, i, J - 1), eyc = load_ey<T, CG>(m, i, J);
   const T eymr = load_ey<T, CG>(m, i + 1, J - 1), eyr = load_ey<T, CG>(m, i + 1, J);
-  const T hzp = ldv<CG>(m.Hz + (J - 1) * p + i) - c.ch * ((eymr - eym) - (exc - exm));
-  const T hz = ldv<CG>(m.Hz + J * p + i) - c.ch * ((eyr - eyc) - (exn - exc));
-  const T v = c.va * ldv<CG>(m.vx + J * p + i) - c.vb * exc;
-  return exc + c.ce * (hz - hzp) + c.cj * (m.n[J * p + i] + m.n[J * p + i + 1]) * v;
+  const T hzp = upd_h(c, ldv<CG>(m.Hz + (J - 1) * p + i), (eymr - eym) - (exc - exm));
+  const T hz = upd_h(c, ldv<CG>(m.Hz + J * p + i), (eyr - eyc) - (exn - exc));
+  const T v = upd_v(c, ldv<CG>(m.vx + J * p + i), exc);
+  return upd_ex(c, exc, hz - hzp, m.n[J * p + i] + m.n[J * p + i + 1], v);
 }
 
 template <class T, bool CG = false>
@@ -166,10 +193,10 @@ __device__ __forceinline__ T coarse_new_ey(const Bnd<T>& b, int I, int j) {
   const T eyl = load_ey<T, CG>(m, I - 1, j), eyc = load_ey<T, CG>(m, I, j), eyr = load_ey<T, CG>(m, I + 1, j);
   const T exl = load_ex<T, CG>(m, I - 1, j), exln = load_ex<T, CG>(m, I - 1, j + 1);
   const T exc = load_ex<T, CG>(m, I, j), exn = load_ex<T, CG>(m, I, j + 1);
-  const T hzl = ldv<CG>(m.Hz + j * p + I - 1) - c.ch * ((eyc - eyl) - (exln - exl));
-  const T hz = ldv<CG>(m.Hz + j * p + I) - c.ch * ((eyr - eyc) - (exn - exc));
-  const T v = c.va * ldv<CG>(m.vy + j * p + I) - c.vb * (eyc + incident(c, I));
-  return eyc - c.ce * (hz - hzl) + c.cj * (m.n[j * p + I] + m.n[(j + 1) * p + I]) * v;
+  const T hzl = upd_h(c, ldv<CG>(m.Hz + j * p + I - 1), (eyc - eyl) - (exln - exl));
+  const T hz = upd_h(c, ldv<CG>(m.Hz + j * p + I), (eyr - eyc) - (exn - exc));
+  const T v = upd_v(c, ldv<CG>(m.vy + j * p + I), eyc + incident(c, I));
+  return upd_ey(c, eyc, hz - hzl, m.n[j * p + I] + m.n[(j + 1) * p + I], v);
 }
 
 template <class T, bool CG = false>
@@ -391,7 +418,7 @@ __device__ __forceinline__ void em_strips_interior(const EmArgs<T>& A, int bx, i
     const int q = (j0 - 1) * p + i;
     const T exm = m.Ex[q], eym = m.Ey[q], hzo = m.Hz[q];
     const T eyr = __shfl_down_sync(0xffffffffu, eym, 1);
-    hzp = hzo - c.ch * ((eyr - eym) - (exc - exm));
+    hzp = upd_h(c, hzo, (eyr - eym) - (exc - exm));
     exp_ = exm;
     eyp = eym;
   }
@@ -415,27 +442,27 @@ __device__ __forceinline__ void em_strips_interior(const EmArgs<T>& A, int bx, i
     if (j + 1 < j1) nxt = load_row(j + 1);
     const T exn = cur.exn, eyc = cur.eyc, hzo = cur.hzo, vxo = cur.vxo, vyo = cur.vyo, nn = cur.nn;
     const T eyr = __shfl_down_sync(0xffffffffu, eyc, 1);
-    const T hz = hzo - c.ch * ((eyr - eyc) - (exn - exc));
+    const T hz = upd_h(c, hzo, (eyr - eyc) - (exn - exc));
     const T hzl = __shfl_up_sync(0xffffffffu, hz, 1);
     const T exl = __shfl_up_sync(0xffffffffu, exc, 1);
     const T ncr = __shfl_down_sync(0xffffffffu, nc, 1);
     if (own) {
       dHz[id] = hz;
       if (c.accum) {
-        const T sx = T(0.5) * (exl * exl + exc * exc);
+        const T sx = sq_mean(exl, exc);
         const T e = eyp + inc, f = eyc + inc;
-        const T sy2 = T(0.5) * (e * e + f * f);
+        const T sy2 = sq_mean(e, f);
         m.S2[id] = cur.s2 + (double)(sx + sy2);
       }
       {
-        const T v = c.va * vxo - c.vb * exc;
+        const T v = upd_v(c, vxo, exc);
         dvx[id] = v;
-        dEx[id] = exc + c.ce * (hz - hzp) + c.cj * (nc + ncr) * v;
+        dEx[id] = upd_ex(c, exc, hz - hzp, nc + ncr, v);
       }
       {
-        const T v = c.va * vyo - c.vb * (eyc + inc);
+        const T v = upd_v(c, vyo, eyc + inc);
         dvy[id] = v;
-        dEy[id] = eyc - c.ce * (hz - hzl) + c.cj * (nc + nn) * v;
+        dEy[id] = upd_ey(c, eyc, hz - hzl, nc + nn, v);
       }
     }
     exp_ = exc;
@@ -513,9 +540,9 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
         const T dey = eyr - eym, dex = exc - exm;
         const T px = P.bxh[i] * ldv<CG>(P.hx + q) + P.cxh[i] * dey;
         const T py = P.byh[jm] * ldv<CG>(P.hy + q) + P.cyh[jm] * dex;
-        hzp = hzo - c.ch * ((dey + px) - (dex + py));
+        hzp = upd_h(c, hzo, (dey + px) - (dex + py));
       } else {
-        hzp = hzo - c.ch * ((eyr - eym) - (exc - exm));
+        hzp = upd_h(c, hzo, (eyr - eym) - (exc - exm));
       }
     }
     exp_ = exm;
@@ -568,9 +595,9 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
           P.dhx[id] = px;
           P.dhy[id] = py;
         }
-        hz = hzo - c.ch * ((dey + px) - (dex + py));
+        hz = upd_h(c, hzo, (dey + px) - (dex + py));
       } else {
-        hz = hzo - c.ch * ((eyr - eyc) - (exn - exc));
+        hz = upd_h(c, hzo, (eyr - eyc) - (exn - exc));
       }
     }
     const T hzl = __shfl_up_sync(0xffffffffu, hz, 1);
@@ -585,11 +612,11 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
       // ---- S2 += |E^n|^2 at node (i, j)
       if (c.accum) {
         T sx, sy;
-        if (i > 0 && i < nx) sx = T(0.5) * (exl * exl + exc * exc);
+        if (i > 0 && i < nx) sx = sq_mean(exl, exc);
         else if (i > 0) sx = exl * exl;
         else sx = exc * exc;
         const T e = eyp + inc, f = eyc + inc;
-        if (j > 0 && j < ny) sy = T(0.5) * (e * e + f * f);
+        if (j > 0 && j < ny) sy = sq_mean(e, f);
         else if (j > 0) sy = e * e;
         else sy = f * f;
         m.S2[id] = s2 + (double)(sx + sy);
@@ -597,35 +624,35 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
       // ---- x edge (i, j)
       if (i < nx) {
         if (j > 0 && j < ny) {
-          const T v = c.va * vxo - c.vb * exc;
+          const T v = upd_v(c, vxo, exc);
           dvx[id] = v;
           T en;
           if (pw) {
             const T dh = hz - hzp;
             const T pe = P.byn[j] * ldv<CG>(P.exy + id) + P.cyn[j] * dh;
             P.dexy[id] = pe;
-            en = exc + c.ce * (dh + pe) + c.cj * (nc + ncr) * v;
+            en = upd_ex(c, exc, dh + pe, nc + ncr, v);
           } else {
-            en = exc + c.ce * (hz - hzp) + c.cj * (nc + ncr) * v;
+            en = upd_ex(c, exc, hz - hzp, nc + ncr, v);
           }
           if (keep_ex(i, j)) dEx[id] = en;
           exw = en;
           if (j == 1 && b.mode[SIDE_BOTTOM] == BC_MUR) {
-            dvx[i] = c.va * ldv<CG>(m.vx + i) - c.vb * exp_;
+            dvx[i] = upd_v(c, ldv<CG>(m.vx + i), exp_);
             exw0 = exc + c.mur * (en - exp_);
             if (keep_ex(i, 0)) dEx[i] = exw0;
           }
           if (j == ny - 1 && b.mode[SIDE_TOP] == BC_MUR) {
             const int ib = ny * p + i;
-            dvx[ib] = c.va * ldv<CG>(m.vx + ib) - c.vb * exn;
+            dvx[ib] = upd_v(c, ldv<CG>(m.vx + ib), exn);
             exwN = exc + c.mur * (en - exn);
             if (keep_ex(i, ny)) dEx[ib] = exwN;
           }
         } else {
           const int sd = (j == 0) ? SIDE_BOTTOM : SIDE_TOP;
-          if (b.mode[sd] == BC_CFB) dvx[id] = c.va * vxo - c.vb * exc;  // E: em_cfb
+          if (b.mode[sd] == BC_CFB) dvx[id] = upd_v(c, vxo, exc);  // E: em_cfb
           if (b.mode[sd] == BC_PEC) {
-            dvx[id] = c.va * vxo - c.vb * exc;
+            dvx[id] = upd_v(c, vxo, exc);
             dEx[id] = T(0);
           }
         }
@@ -633,36 +660,36 @@ __device__ __forceinline__ void em_strips(const EmArgs<T>& A, int blk) {
       // ---- y edge (i, j)
       if (j < ny) {
         if (i > 0 && i < nx) {
-          const T v = c.va * vyo - c.vb * (eyc + inc);
+          const T v = upd_v(c, vyo, eyc + inc);
           dvy[id] = v;
           T en;
           if (pw) {
             const T dh = hz - hzl;
             const T pe = P.bxn[i] * ldv<CG>(P.eyx + id) + P.cxn[i] * dh;
             P.deyx[id] = pe;
-            en = eyc - c.ce * (dh + pe) + c.cj * (nc + nn) * v;
+            en = upd_ey(c, eyc, dh + pe, nc + nn, v);
           } else {
-            en = eyc - c.ce * (hz - hzl) + c.cj * (nc + nn) * v;
+            en = upd_ey(c, eyc, hz - hzl, nc + nn, v);
           }
           if (keep_ey(i, j)) dEy[id] = en;
           eyw = en;
           if (i == 1 && b.mode[SIDE_LEFT] == BC_MUR) {
             const int ib = j * p;
-            dvy[ib] = c.va * vyl - c.vb * (eyl + inc0);
+            dvy[ib] = upd_v(c, vyl, eyl + inc0);
             eywL = eyc + c.mur * (en - eyl);
             if (keep_ey(0, j)) dEy[ib] = eywL;
           }
           if (i == nx - 1 && b.mode[SIDE_RIGHT] == BC_MUR) {
             const int ib = j * p + nx;
-            dvy[ib] = c.va * vyr - c.vb * (eyr + incn);
+            dvy[ib] = upd_v(c, vyr, eyr + incn);
             eywR = eyc + c.mur * (en - eyr);
             if (keep_ey(nx, j)) dEy[ib] = eywR;
           }
         } else {
           const int sd = (i == 0) ? SIDE_LEFT : SIDE_RIGHT;
-          if (b.mode[sd] == BC_CFB) dvy[id] = c.va * vyo - c.vb * (eyc + inc);  // E: em_cfb
+          if (b.mode[sd] == BC_CFB) dvy[id] = upd_v(c, vyo, eyc + inc);  // E: em_cfb
           if (b.mode[sd] == BC_PEC) {
-            dvy[id] = c.va * vyo - c.vb * (eyc + inc);
+            dvy[id] = upd_v(c, vyo, eyc + inc);
             dEy[id] = T(0);
           }
         }
@@ -784,11 +811,11 @@ __device__ __forceinline__ void st_d2(double* q, double a, double b, bool sa, bo
 __device__ __forceinline__ float node_e2_sample(int i, int j, int nx, int ny, float exl, float exc,
                                                 float eyp, float eyc, float inc) {
   float sx, sy;
-  if (i > 0 && i < nx) sx = 0.5f * (exl * exl + exc * exc);
+  if (i > 0 && i < nx) sx = sq_mean(exl, exc);
   else if (i > 0) sx = exl * exl;
   else sx = exc * exc;
   const float e = eyp + inc, f = eyc + inc;
-  if (j > 0 && j < ny) sy = 0.5f * (e * e + f * f);
+  if (j > 0 && j < ny) sy = sq_mean(e, f);
   else if (j > 0) sy = e * e;
   else sy = f * f;
   return sx + sy;
@@ -810,15 +837,15 @@ __device__ __forceinline__ Col2 col2_update(const Step<float>& c, const Bnd<floa
   Col2 o;
   o.en_x = o.en_y = o.exw0 = o.exwN = o.eywL = o.eywR = 0.f;
   if (i < nx && j > 0 && j < ny) {
-    const float v = c.va * vxo - c.vb * exc;
-    const float en = exc + c.ce * (hz - hzp) + c.cj * (nc + ncr) * v;
+    const float v = upd_v(c, vxo, exc);
+    const float en = upd_ex(c, exc, hz - hzp, nc + ncr, v);
     o.en_x = en;
     if (j == 1 && b.mode[SIDE_BOTTOM] == BC_MUR) o.exw0 = exc + c.mur * (en - exp_);
     if (j == ny - 1 && b.mode[SIDE_TOP] == BC_MUR) o.exwN = exc + c.mur * (en - exn);
   }
   if (j < ny && i > 0 && i < nx) {
-    const float v = c.va * vyo - c.vb * (eyc + inc);
-    const float en = eyc - c.ce * (hz - hzl) + c.cj * (nc + nn) * v;
+    const float v = upd_v(c, vyo, eyc + inc);
+    const float en = upd_ey(c, eyc, hz - hzl, nc + nn, v);
     o.en_y = en;
     if (i == 1 && b.mode[SIDE_LEFT] == BC_MUR) o.eywL = eyc + c.mur * (en - eyl);
     if (i == nx - 1 && b.mode[SIDE_RIGHT] == BC_MUR) o.eywR = eyc + c.mur * (en - eyr);
@@ -855,8 +882,8 @@ __device__ __forceinline__ void em_strips2_interior(const EmArgs<float>& A, int 
     const float2 eym = *reinterpret_cast<const float2*>(m.Ey + q);
     const float2 hzo = *reinterpret_cast<const float2*>(m.Hz + q);
     const float eyr_b = __shfl_down_sync(0xffffffffu, eym.x, 1);
-    hzp.x = hzo.x - c.ch * ((eym.y - eym.x) - (exc.x - exm.x));
-    hzp.y = hzo.y - c.ch * ((eyr_b - eym.y) - (exc.y - exm.y));
+    hzp.x = upd_h(c, hzo.x, (eym.y - eym.x) - (exc.x - exm.x));
+    hzp.y = upd_h(c, hzo.y, (eyr_b - eym.y) - (exc.y - exm.y));
     eyp = eym;
   }
   struct Row2 { float2 exn, eyc, hzo, vxo, vyo, nn; double2 s2; };
@@ -885,28 +912,28 @@ __device__ __forceinline__ void em_strips2_interior(const EmArgs<float>& A, int 
     if (j + 1 < j1) nxt = load_row(j + 1);
     const float eyr_b = __shfl_down_sync(0xffffffffu, cur.eyc.x, 1);
     float2 hz;
-    hz.x = cur.hzo.x - c.ch * ((cur.eyc.y - cur.eyc.x) - (cur.exn.x - exc.x));
-    hz.y = cur.hzo.y - c.ch * ((eyr_b - cur.eyc.y) - (cur.exn.y - exc.y));
+    hz.x = upd_h(c, cur.hzo.x, (cur.eyc.y - cur.eyc.x) - (cur.exn.x - exc.x));
+    hz.y = upd_h(c, cur.hzo.y, (eyr_b - cur.eyc.y) - (cur.exn.y - exc.y));
     const float hzl_a = __shfl_up_sync(0xffffffffu, hz.y, 1);
     const float exl_a = __shfl_up_sync(0xffffffffu, exc.y, 1);
     const float ncr_b = __shfl_down_sync(0xffffffffu, nc.x, 1);
-    const float vxa = c.va * cur.vxo.x - c.vb * exc.x, vxb = c.va * cur.vxo.y - c.vb * exc.y;
-    const float enxa = exc.x + c.ce * (hz.x - hzp.x) + c.cj * (nc.x + nc.y) * vxa;
-    const float enxb = exc.y + c.ce * (hz.y - hzp.y) + c.cj * (nc.y + ncr_b) * vxb;
-    const float vya = c.va * cur.vyo.x - c.vb * (cur.eyc.x + inc_a);
-    const float vyb = c.va * cur.vyo.y - c.vb * (cur.eyc.y + inc_b);
-    const float enya = cur.eyc.x - c.ce * (hz.x - hzl_a) + c.cj * (nc.x + cur.nn.x) * vya;
-    const float enyb = cur.eyc.y - c.ce * (hz.y - hz.x) + c.cj * (nc.y + cur.nn.y) * vyb;
+    const float vxa = upd_v(c, cur.vxo.x, exc.x), vxb = upd_v(c, cur.vxo.y, exc.y);
+    const float enxa = upd_ex(c, exc.x, hz.x - hzp.x, nc.x + nc.y, vxa);
+    const float enxb = upd_ex(c, exc.y, hz.y - hzp.y, nc.y + ncr_b, vxb);
+    const float vya = upd_v(c, cur.vyo.x, cur.eyc.x + inc_a);
+    const float vyb = upd_v(c, cur.vyo.y, cur.eyc.y + inc_b);
+    const float enya = upd_ey(c, cur.eyc.x, hz.x - hzl_a, nc.x + cur.nn.x, vya);
+    const float enyb = upd_ey(c, cur.eyc.y, hz.y - hz.x, nc.y + cur.nn.y, vyb);
     if (lo) {
       *reinterpret_cast<float2*>(dHz + id) = hz;
       if (c.accum) {
-        float sx = 0.5f * (exl_a * exl_a + exc.x * exc.x);
+        float sx = sq_mean(exl_a, exc.x);
         float e = eyp.x + inc_a, f = cur.eyc.x + inc_a;
-        const float e2a = sx + 0.5f * (e * e + f * f);
-        sx = 0.5f * (exc.x * exc.x + exc.y * exc.y);
+        const float e2a = sx + sq_mean(e, f);
+        sx = sq_mean(exc.x, exc.y);
         e = eyp.y + inc_b;
         f = cur.eyc.y + inc_b;
-        const float e2b = sx + 0.5f * (e * e + f * f);
+        const float e2b = sx + sq_mean(e, f);
         *reinterpret_cast<double2*>(m.S2 + id) = make_double2(cur.s2.x + (double)e2a, cur.s2.y + (double)e2b);
       }
       *reinterpret_cast<float2*>(dvx + id) = make_float2(vxa, vxb);
@@ -981,8 +1008,8 @@ __device__ __forceinline__ void em_strips2(const EmArgs<float>& A, int blk) {
     const float2 eym = ld_f2(m.Ey + jm * p + ia, yb, ya);
     const float2 hzo = ld_f2(m.Hz + jm * p + ia, xb, xa);
     const float eyr_b = __shfl_down_sync(0xffffffffu, eym.x, 1);
-    if (xa) hzp.x = hzo.x - c.ch * ((eym.y - eym.x) - (exc.x - exm.x));
-    if (xb) hzp.y = hzo.y - c.ch * ((eyr_b - eym.y) - (exc.y - exm.y));
+    if (xa) hzp.x = upd_h(c, hzo.x, (eym.y - eym.x) - (exc.x - exm.x));
+    if (xb) hzp.y = upd_h(c, hzo.y, (eyr_b - eym.y) - (exc.y - exm.y));
     exp_ = exm;
     eyp = eym;
   }
@@ -1019,8 +1046,8 @@ __device__ __forceinline__ void em_strips2(const EmArgs<float>& A, int blk) {
     const float eyr_b = __shfl_down_sync(0xffffffffu, cur.eyc.x, 1);
     float2 hz = make_float2(0.f, 0.f);
     if (j < ny) {
-      if (xa) hz.x = cur.hzo.x - c.ch * ((cur.eyc.y - cur.eyc.x) - (cur.exn.x - exc.x));
-      if (xb) hz.y = cur.hzo.y - c.ch * ((eyr_b - cur.eyc.y) - (cur.exn.y - exc.y));
+      if (xa) hz.x = upd_h(c, cur.hzo.x, (cur.eyc.y - cur.eyc.x) - (cur.exn.x - exc.x));
+      if (xb) hz.y = upd_h(c, cur.hzo.y, (eyr_b - cur.eyc.y) - (cur.exn.y - exc.y));
     }
     const float hzl_a = __shfl_up_sync(0xffffffffu, hz.y, 1);
     const float exl_a = __shfl_up_sync(0xffffffffu, exc.y, 1);
@@ -1040,7 +1067,7 @@ __device__ __forceinline__ void em_strips2(const EmArgs<float>& A, int blk) {
       const float e2b = node_e2_sample(ib, j, nx, ny, exc.x, exc.y, eyp.y, cur.eyc.y, inc_b);
       st_d2(m.S2 + id, cur.s2.x + (double)e2a, cur.s2.y + (double)e2b, own_a, own_b);
     }
-    st_f2(dvx + id, c.va * cur.vxo.x - c.vb * exc.x, c.va * cur.vxo.y - c.vb * exc.y, ax, bxx);
+    st_f2(dvx + id, upd_v(c, cur.vxo.x, exc.x), upd_v(c, cur.vxo.y, exc.y), ax, bxx);
     {
       const bool xin = j > 0 && j < ny;
       const bool xpec = (j == 0 && pec_b) || (j == ny && pec_t);
@@ -1049,8 +1076,8 @@ __device__ __forceinline__ void em_strips2(const EmArgs<float>& A, int blk) {
       if (j == ny - 1 && b.mode[SIDE_TOP] == BC_MUR) st_f2(dEx + ny * p + ia, oa.exwN, ob.exwN, ax && j > 0, bxx && j > 0);
     }
     if (j < ny) {
-      st_f2(dvy + id, c.va * cur.vyo.x - c.vb * (cur.eyc.x + inc_a),
-            c.va * cur.vyo.y - c.vb * (cur.eyc.y + inc_b), own_a, own_b);
+      st_f2(dvy + id, upd_v(c, cur.vyo.x, cur.eyc.x + inc_a), upd_v(c, cur.vyo.y, cur.eyc.y + inc_b),
+            own_a, own_b);
       const bool ia_in = ia > 0 && ia < nx, ib_in = ib > 0 && ib < nx;
       const bool ia_pec = (ia == 0 && pec_l) || (ia == nx && pec_r);
       const bool ib_pec = (ib == 0 && pec_l) || (ib == nx && pec_r);
