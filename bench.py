@@ -628,7 +628,7 @@ def run_ours(args):
              else "k_em (coarse step)")
     roof = {"bound": "hbm", "kernel": first + ", mid-period form",
             "achieved": mid["achieved"], "peak": peak, "peak_source": src + " (burst copy)",
-            "unit": "GB/s", "frac": mid["frac"], "traffic": recorded_traffic("k_em2", args.workload),
+            "unit": "GB/s", "frac": mid["frac"], "traffic": recorded_traffic("k_em2_fp64" if es == 8 else "k_em2", args.workload),
             "avg_launch_us": mid["avg_launch_us"],
             "algorithmic_bytes_per_launch": mid["algorithmic_bytes_per_launch"],
             "timed_region": "CUDA-graph replays of 20 back-to-back copies of the launch on the "
