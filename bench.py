@@ -454,7 +454,8 @@ def front_x(run, cfg, lam):
 def run_front(args):
     """Front-velocity experiment of Sec. IV.C on a 1.5 x 1.5 wavelength domain:
     uniform meshes at lambda/128 and lambda/256 against DMR (coarse lambda/64)
-    at r = 2 with both growth policies and at r = 4.  The front is tracked
+    at r = 2 with both growth policies and at r = 4, with the two-way
+    coupling and with the density-only transfer back.  The front is tracked
     every 50 periods; its velocity is the slope of a line fitted where the
     front lies between 1.0 and 0.3 wavelengths from the left edge."""
     import numpy as np
@@ -470,6 +471,16 @@ def run_front(args):
              ("dmr64_r2_box", W.front_1p5(64, 2, growth=1)),
              ("dmr64_r2_lines", W.front_1p5(64, 2, growth=2)),
              ("dmr64_r4_box", W.front_1p5(64, 4, growth=1))]
+
+    def variant(w, **kw):
+        return dict(w, cfg=dict(w["cfg"], **kw))
+    # coupling = 1: the density alone goes back to the coarse mesh
+    cases += [("dmr64_r2_box_oneway", variant(W.front_1p5(64, 2, growth=1), coupling=1)),
+              ("dmr64_r2_lines32_oneway", variant(W.front_1p5(64, 2, growth=2), coupling=1,
+                                                  m_ex=32, m_ey=16)),
+              ("dmr64_r4_box_oneway", variant(W.front_1p5(64, 4, growth=1), coupling=1)),
+              ("dmr64_r4_lines32_oneway", variant(W.front_1p5(64, 4, growth=2), coupling=1,
+                                                  m_ex=32, m_ey=16))]
     lam = 299792458.0 / 110e9
     T = 1.0 / 110e9
     res = {}

@@ -96,7 +96,9 @@ typedef struct dmr_config {
                                 slowly growing mode (spectral radius 1.0005-1.0045 per
                                 coarse step in vacuum, more at r = 4 than r = 2 on some
                                 shapes).  Collisional plasma damps it in the benchmark
-                                runs; long r = 4 runs can end in DMR_EUNSTABLE. */
+                                runs; long r = 4 runs can end in DMR_EUNSTABLE.  With
+                                coupling = 1 (below) the coupled step has no growing
+                                mode. */
   int32_t n_lambda;          /* coarse cells per wavelength: dx_c = lambda / n_lambda */
   int32_t steps_per_period;  /* N_T coarse EM steps per period: dt_c = 1/(f N_T);
                                 Courant c dt/dx = n_lambda/N_T must be <= 1/sqrt(2) */
@@ -134,6 +136,15 @@ typedef struct dmr_config {
                                 inside the domain (set_patch: DMR_EINVAL; growth stops
                                 there); adjoint and batched runs need boundary = 0 */
   int32_t pml_cells;         /* CPML thickness in coarse cells [8] (values <= 0) */
+  int32_t coupling;          /* what the fine mesh gives back to the coarse mesh
+                                (Sec. III.C: "fine mesh updated quantities are
+                                transferred back"): 0 the fine E means into the
+                                coarse E under the rectangle every coarse step and
+                                the fine density into the coarse nodes every period
+                                (two-way, the default); 1 the density only (one-way
+                                for the fields: the coarse E under the rectangle
+                                stays the coarse mesh's own; the vacuum coupled step
+                                then has spectral radius 1, see the note on r) */
 } dmr_config;
 
 /* Bytes of device workspace a run of this configuration needs; 0 if the

@@ -60,7 +60,7 @@ class Params:
     ``cfg`` is a plain dict with keys nx, ny, r, n_lambda, steps_per_period,
     freq, E0, p_torr and optional De, Da, beta_rec, Te, nu_scale, nu_a, n_th,
     g_th, buffer_cells, growth, m_ex, m_ey, nu_model, town_A, town_B,
-    boundary, pml_cells, patch_cap_cells.  A value of None (or a
+    boundary, pml_cells, patch_cap_cells, coupling.  A value of None (or a
     missing key) selects the default reading.
     """
 
@@ -113,6 +113,13 @@ class Params:
         self.m_ey = int(g("m_ey") if g("m_ey") is not None else self.buffer)
         self.cap = int(g("patch_cap_cells") if g("patch_cap_cells") is not None
                        else (self.r * self.nx) * (self.r * self.ny))
+        # Sec. III.C: the fine mesh's updated quantities go back to the coarse
+        # mesh.  coupling 0 (default reading): the E means every coarse step and
+        # the density every period; 1: the density only (the coarse E under
+        # the rectangle stays the coarse mesh's own)
+        self.coupling = int(g("coupling") or 0)
+        if self.coupling not in (0, 1):
+            raise ValueError("coupling must be 0 or 1")
         # Sec. II.A: r_ei = beta 1e-13 (300/T_e)^(1/2), read in m^3/s.
         self.r_ei = self.beta_rec * 1e-13 * math.sqrt(300.0 / self.Te)
         # Plasma step: forward Euler over one EM period (Sec. III.C).
@@ -619,7 +626,8 @@ class Sim:
                     sides[side] = "mur" if on_edge[side] else linear_cfb(old[side], new[side], frac, pos)
                 em_step(P, f, sides)
                 accumulate_e2(P, f)
-            self._restrict_e()
+            if P.coupling == 0:
+                self._restrict_e()
             accumulate_e2(P, c)
         if c.m % P.N_T == 0:
             self._period_end()

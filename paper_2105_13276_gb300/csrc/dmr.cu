@@ -88,6 +88,7 @@ struct Derived {
   int boundary;     // 0 Mur, 1 CPML
   int pml;          // CPML thickness (coarse cells)
   int margin;       // the fine rectangle stays this many coarse cells inside
+  int coupling;     // 0 fine E means and density back to the coarse mesh, 1 density only
 };
 
 int derive(const dmr_config* c, Derived* d, std::string* err) {
@@ -107,6 +108,8 @@ int derive(const dmr_config* c, Derived* d, std::string* err) {
   d->town_B = c->town_B > 0 ? c->town_B : 36500.0;    // 365 V/(cm Torr)
   if (c->boundary != 0 && c->boundary != 1) { *err = "boundary must be 0 (Mur) or 1 (CPML)"; return DMR_EINVAL; }
   d->boundary = c->boundary;
+  if (c->coupling != 0 && c->coupling != 1) { *err = "coupling must be 0 (two-way) or 1 (density only)"; return DMR_EINVAL; }
+  d->coupling = c->coupling;
   d->pml = c->pml_cells > 0 ? c->pml_cells : 8;
   d->margin = c->boundary == 1 ? d->pml + 2 : 0;
   if (c->boundary == 1 && (2 * d->pml + 2 > c->nx || 2 * d->pml + 2 > c->ny)) {
@@ -408,7 +411,7 @@ bool same_config(const dmr_config& a, const dmr_config& b) {
          a.Te == b.Te && a.nu_scale == b.nu_scale && a.nu_a == b.nu_a && a.n_th == b.n_th &&
          a.g_th == b.g_th && a.m_ex == b.m_ex && a.m_ey == b.m_ey && a.nu_model == b.nu_model &&
          a.town_A == b.town_A && a.town_B == b.town_B && a.boundary == b.boundary &&
-         a.pml_cells == b.pml_cells;
+         a.pml_cells == b.pml_cells && a.coupling == b.coupling;
 }
 
 template <class T>
@@ -529,7 +532,7 @@ struct Engine final : Base {
       set_rows(&ptab_h[par * nph], rc, 1);
       for (int k = 1; k < nph; ++k) set_rows(&ptab_h[par * nph + k], rf, k == r ? r : 1);
     }
-    if (fine) {
+    if (fine && d.coupling == 0) {
       // the coarse step leaves the edges the last fine sub-step restricts (a8)
       for (int par = 0; par < 2; ++par) {
         dmr::RestrW<T>& Wc = ptab_h[par * nph].W;
@@ -979,7 +982,7 @@ struct Engine final : Base {
     // sub-steps after the first run alone, with their own strip height
     *Af = em_args(fsrc, fdst, sf, bf, k == r ? r : 1, k > 1 ? warps_per_sm_fine : warps_per_sm, k > 1);
     Af->kind = 1; Af->N = r * NT; Af->r = r; Af->ps = ph[2]; Af->pc = ph[3];
-    if (k == r) {
+    if (k == r && d.coupling == 0) {
       // a8: the last sub-step writes the mean of r collinear fine edges into
       // the coarse E^{n+1} (the coarse step's output buffer)
       dmr::RestrW<T>& W = Af->W;
@@ -2002,7 +2005,7 @@ struct Engine final : Base {
       dmr::Step<T> s_ = make_step_at(r, (int64_t)r * P.L, true, P.rect_b[0]);
       dmr::ka_s2<T><<<nodes_grid(fnx, fny), blk, 0, st>>>(A.E[fin][0], A.E[fin][1], P.fEx, P.fEy, A.S2,
                                                           s_, fnx, fny, fp, sums);
-      if (P.rvalid) restrict_t(ca, cin, A, fin, P.rect_b);
+      if (P.rvalid && d.coupling == 0) restrict_t(ca, cin, A, fin, P.rect_b);
     }
     return launched("adjoint period end");
   }
@@ -2113,7 +2116,7 @@ struct Engine final : Base {
       std::swap(A.H, A.H2);
       fin ^= 1;
     }
-    if (R.rvalid) {
+    if (R.rvalid && d.coupling == 0) {
       // a8^T of the previous step's transfer, into the fine E^n adjoint
       ct.restr = 1;
       ct.I0 = R.rect[0]; ct.J0 = R.rect[1]; ct.I1 = R.rect[2]; ct.J1 = R.rect[3]; ct.r = r;

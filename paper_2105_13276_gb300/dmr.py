@@ -40,7 +40,8 @@ class DmrConfig(ctypes.Structure):
                 ("nu_scale", c_double), ("nu_a", c_double), ("n_th", c_double),
                 ("g_th", c_double), ("m_ex", c_int32), ("m_ey", c_int32),
                 ("nu_model", c_int32), ("town_A", c_double), ("town_B", c_double),
-                ("boundary", c_int32), ("pml_cells", c_int32)]
+                ("boundary", c_int32), ("pml_cells", c_int32),
+                ("coupling", c_int32)]
 
 
 class DMRError(RuntimeError):
@@ -136,6 +137,7 @@ def make_config(cfg: dict) -> DmrConfig:
     c.town_A, c.town_B = d("town_A"), d("town_B")
     c.boundary = int(cfg.get("boundary") or 0)
     c.pml_cells = int(cfg.get("pml_cells") or -1)
+    c.coupling = int(cfg.get("coupling") or 0)
     c.patch_cap_cells = int(-1 if cfg.get("patch_cap_cells") is None else cfg["patch_cap_cells"])
     c.freq, c.E0, c.p_torr = float(cfg["freq"]), float(cfg["E0"]), float(cfg["p_torr"])
     c.De, c.Da = d("De"), d("Da")

@@ -52,6 +52,9 @@ def test_config_validation_host_only(lib):
     with pytest.raises(D.DMRError, match="nu_model"):
         D.workspace_bytes(W.base_cfg(nu_model=2))
     assert D.workspace_bytes(W.base_cfg(nu_model=1, town_A=1e3, town_B=3e4)) > 0
+    with pytest.raises(D.DMRError, match="coupling"):
+        D.workspace_bytes(W.base_cfg(coupling=2))
+    assert D.workspace_bytes(W.base_cfg(coupling=1)) == D.workspace_bytes(W.base_cfg())
 
 
 def test_workspace_grows_with_capacity_and_precision(lib):

@@ -131,6 +131,25 @@ def test_fp64_adjoint_townsend_matches_complex_step():
     assert max(errs) <= TOL_ADJ64, errs
 
 
+def test_fp64_adjoint_one_way_coupling_matches_complex_step():
+    """The adjoint with the density-only transfer back (coupling = 1: no
+    fine->coarse E means, so no transposed means either)."""
+    w = W.small_dmr(coupling=1)
+    seed = O.sim_from_workload(w).fine.n.copy()
+    NT = w["cfg"]["steps_per_period"]
+    steps, K = 2 * NT, NT
+    ref = oracle_run(w, w["cfg"]["E0"], 1.0, seed, steps)
+    rng = np.random.default_rng(6)
+    target = ref.coarse.n * (1 + 0.05 * rng.standard_normal(ref.coarse.n.shape))
+    u = rng.standard_normal(seed.shape)
+    n_end, gE0, gnu, gseed = gpu_grads(w, seed, steps, K, target)
+    assert np.linalg.norm(n_end - ref.coarse.n) / np.linalg.norm(ref.coarse.n) < 1e-12
+    cE0, cnu, cseed = cs_grads(w, seed, steps, ref.log, target, u)
+    errs = (abs(gE0 / cE0 - 1), abs(gnu / cnu - 1), abs(float(np.sum(gseed * u)) / cseed - 1))
+    print("FP64 adjoint vs complex step, one-way coupling (E0, s_nu, seed dir):", errs)
+    assert max(errs) <= TOL_ADJ64, errs
+
+
 def test_fp64_adjoint_matches_central_differences():
     w, seed = case(2)
     NT = w["cfg"]["steps_per_period"]

@@ -153,6 +153,50 @@ def test_dmr_fp64_threshold_lines_match_oracle(rect, nth, mex, mey):
         assert sim.log[0][0] == 0 and sim.log[0][2] == w["cfg"]["nx"]
 
 
+@pytest.mark.parametrize("r,precision", [(2, 0), (4, 0), (2, 1)])
+def test_one_way_coupling_matches_oracle(r, precision):
+    """coupling = 1 (the density alone goes back to the coarse mesh):
+    free-running growth in FP64 (rectangles and masks exact, fields 1e-12),
+    FP32 with the oracle's rectangle log replayed (1e-4)."""
+    w = W.small_dmr(r=r, precision=precision, coupling=1)
+    sim = O.sim_from_workload(w)
+    NT = w["cfg"]["steps_per_period"]
+    steps = 3 * NT + 5
+    sim.advance(steps)
+    run = D.run_from_workload(w)
+    if precision == 1:
+        run.replay_log(sim.log)
+    run.advance(steps)
+    assert run.get_patch() == tuple(sim.rect)
+    assert sim.log[-1] != tuple(w["rect"]), "the rectangle should grow"
+    compare(run, sim, TOL64 if precision == 0 else TOL32)
+    st = run.stats()
+    assert abs(st["N_e"] / sim.N_e - 1) < (TOL64 if precision == 0 else TOL32)
+
+
+def test_one_way_coupling_launch_forms_identical():
+    """coupling = 1 in every launch form: direct launches, CUDA graphs, the
+    persistent period and a batch give the same bits (FP32, growth)."""
+    w = W.small_dmr(precision=1, coupling=1)
+    steps = 3 * w["cfg"]["steps_per_period"] + 7
+    runs = []
+    for form in ("direct", "graphs", "persistent"):
+        run = D.run_from_workload(w)
+        if form == "graphs":
+            run.set_graphs(True)
+        if form == "persistent":
+            run.set_persistent(True)
+        run.advance(steps)
+        runs.append(run)
+    b = D.batch_from_workloads([w, W.small_dmr(precision=1)])
+    b.advance(steps)
+    for other in runs[1:] + [b.runs[0]]:
+        assert other.get_patch() == runs[0].get_patch()
+        for level in (0, 1):
+            for name in FIELDS + ("S2",):
+                assert np.array_equal(other.read(name, level), runs[0].read(name, level)), (level, name)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_townsend_ionization_matches_oracle(precision):
     """The Townsend coefficient set (nu_model = 1, Sec. II.A) on the GPU
