@@ -61,6 +61,7 @@ class Naive:
         self.mode = 1 if cfg.get("growth") is None else int(cfg["growth"])
         self.mex = 2 * self.buf if cfg.get("m_ex") is None else cfg["m_ex"]
         self.mey = self.buf if cfg.get("m_ey") is None else cfg["m_ey"]
+        self.coupling = int(cfg.get("coupling") or 0)   # 1: no fine -> coarse E
         self.nl = nl
         self.c = NMesh(self.nx, self.ny, lam / nl, 1.0 / (self.f * self.NT), self.NT, 0, 0)
         self.rect = tuple(rect)
@@ -188,7 +189,7 @@ class Naive:
             self.step_mesh(fm, bnd)
             self.acc(fm)
         # fine -> coarse
-        for i in range(i0, i1):
+        for i in (range(i0, i1) if self.coupling == 0 else ()):
             for j in range(j0, j1 + 1):
                 if (j == j0 and not edge["bottom"]) or (j == j1 and not edge["top"]):
                     continue
@@ -196,7 +197,7 @@ class Naive:
                 for q in range(r):
                     s = s + fm.Ex[r * (i - i0) + q][r * (j - j0)]
                 c.Ex[i][j] = s / r
-        for i in range(i0, i1 + 1):
+        for i in (range(i0, i1 + 1) if self.coupling == 0 else ()):
             if (i == i0 and not edge["left"]) or (i == i1 and not edge["right"]):
                 continue
             for j in range(j0, j1):

@@ -159,13 +159,15 @@ def test_threshold_line_policy():
     assert O.grow_lines(rect, (False,) * 4, 8, 4, 20, 20) == rect
 
 
-@pytest.mark.parametrize("rect,growth", [((3, 3, 7, 6), 1), ((0, 2, 5, 8), 1), ((4, 0, 10, 8), 1),
-                                         ((4, 3, 6, 5), 2), ((5, 3, 8, 5), 2)])
-def test_p11_naive_per_element_implementation_agrees(rect, growth):
+@pytest.mark.parametrize("rect,growth,coupling", [((3, 3, 7, 6), 1, 0), ((0, 2, 5, 8), 1, 0),
+                                                  ((4, 0, 10, 8), 1, 0), ((4, 3, 6, 5), 2, 0),
+                                                  ((5, 3, 8, 5), 2, 0), ((3, 3, 7, 6), 1, 1)])
+def test_p11_naive_per_element_implementation_agrees(rect, growth, coupling):
     """P11: a 10x8 coarse r=2 DMR run, a dense seed so that flags fire and the
-    rectangle grows, against an independent per-element implementation."""
+    rectangle grows, against an independent per-element implementation (also
+    with the density-only transfer back, coupling = 1)."""
     cfg = W.base_cfg(nx=10, ny=8, r=2, n_lambda=8, steps_per_period=16, E0=6e6, p_torr=300.0,
-                     n_th=1e16, buffer_cells=1, growth=growth)
+                     n_th=1e16, buffer_cells=1, growth=growth, coupling=coupling)
     sim = O.Sim(cfg, rect=rect)
     nv = Naive(cfg, rect)
     P = sim.P
