@@ -33,7 +33,7 @@ def base_cfg(**kw):
                E0=5e6, p_torr=700.0, De=None, Da=None, beta_rec=None, Te=None,
                nu_scale=None, nu_a=None, n_th=None, g_th=None, buffer_cells=4,
                growth=True, m_ex=None, m_ey=None, nu_model=None, town_A=None, town_B=None,
-               boundary=None, pml_cells=None,
+               boundary=None, pml_cells=None, coupling=None,
                patch_cap_cells=None, precision=0)
     cfg.update(kw)
     return cfg
