@@ -1,4 +1,5 @@
-"""Slab decomposition of the uniform-mesh time step over several ranks.
+"""Slab decomposition of the time step over several ranks: the uniform mesh
+(SlabSim, local arrays) and the DMR step (DmrSlabSim, ghost zones).
 
 TEST INFRASTRUCTURE ONLY (like dmr_oracle.py): the CPU reference of how the
 method shards over processes, checked against the unsplit oracle.  Nothing on
@@ -256,3 +257,200 @@ class SlabSim:
         if name in ("Ex", "vx", "Hz"):
             return arr[self.c(a):self.c(min(b, self.P.nx))]
         return arr[self.c(a):self.c(b)]
+
+
+# ----------------------------------------------------------------------------
+# The DMR step (coarse mesh and fine rectangle) over the same slabs
+# ----------------------------------------------------------------------------
+_CELL = ("Ex", "vx", "Hz")
+_ARRAYS = ("Ex", "vx", "Hz", "Ey", "vy", "n", "S2", "erms_last")
+
+
+class DmrSlabSim(O.Sim):
+    """One rank's share of a DMR run (Sec. III.C-III.D): the coarse mesh and the
+    fine rectangle are cut at the same x positions (rank k owns coarse node
+    columns [a_k, b_k) and the fine node columns at x in [a_k, b_k) dx_c;
+    cell columns go with their left node).
+
+    Ghost-zone form: the rank keeps arrays of the full size, but only its own
+    columns and a halo of HALO coarse columns (r HALO fine columns) on each
+    side hold data; everything beyond is set to NaN before every coarse step,
+    so a read outside the halo would reach an owned value and show.  Before
+    each coarse step every array of both meshes exchanges HALO columns with
+    the neighbouring ranks; the step itself (Eqs. 1-3 on both meshes, Eq. 5b
+    on the rectangle's sides, the fine->coarse transfer) is the oracle's own
+    code.  At a period end (Eq. 4) the FP64 totals are all-reduced from the
+    owned nodes' partial sums (SUM), the flags' bounding box (MIN / MAX) and
+    the threshold-line hits (MAX) likewise, so every rank takes the same
+    growth decision; the expansion (Eq. 5a) is again the oracle's own code.
+    One coarse step with its period end reads at most 4 coarse columns
+    beyond a slab (a halo of 3 lets NaN reach owned values in the tests);
+    HALO keeps a margin."""
+
+    HALO = 6
+
+    def __init__(self, cfg: dict, rect, rank: int, world: int):
+        super().__init__(cfg, rect=rect)
+        if self.P.boundary != 0 or self.P.r < 2:
+            raise ValueError("the DMR slab reference covers DMR runs with the Mur boundary")
+        self.rank, self.world = rank, world
+        self.bounds = slab_bounds(self.P.nx, world)
+        if min(hi - lo for lo, hi in self.bounds) < self.HALO + 1:
+            raise ValueError("slabs narrower than the halo")
+        self.a, self.b = self.bounds[rank]
+
+    def cols(self, k, level, name):
+        """[lo, hi) of the columns rank k owns in array `name` of a level."""
+        a, b = self.bounds[k]
+        P = self.P
+        if level == 0:
+            lo, hi, ncell = a, b, P.nx
+        else:
+            r, i0, fnx = P.r, self.rect[0], self.fine.nx
+            lo = min(max(r * (a - i0), 0), fnx + 1)
+            hi = min(max(r * (b - i0), 0), fnx + 1)
+            ncell = fnx
+        if name in _CELL:
+            lo, hi = min(lo, ncell), min(hi, ncell)
+        return lo, hi
+
+    def exchange(self):
+        """Halo exchange of every array of both meshes, then the NaN fill."""
+        import torch
+        import torch.distributed as dist
+        ops, into, fills = [], [], []
+        meshes = [(0, self.coarse)] + ([(1, self.fine)] if self.fine is not None else [])
+        for level, mesh in meshes:
+            w = self.HALO * (1 if level == 0 else self.P.r)
+            for name in _ARRAYS:
+                arr = getattr(mesh, name)
+                lo, hi = self.cols(self.rank, level, name)
+                got_l = got_r = 0
+                for nb in (self.rank - 1, self.rank + 1):
+                    if nb < 0 or nb >= self.world:
+                        continue
+                    nlo, nhi = self.cols(nb, level, name)
+                    ws, wr = min(w, hi - lo), min(w, nhi - nlo)
+                    if ws > 0:
+                        part = arr[lo:lo + ws] if nb < self.rank else arr[hi - ws:hi]
+                        ops.append(dist.P2POp(dist.isend, torch.from_numpy(np.ascontiguousarray(part)), nb))
+                    if wr > 0:
+                        t = torch.empty((wr,) + arr.shape[1:], dtype=torch.float64)
+                        ops.append(dist.P2POp(dist.irecv, t, nb))
+                        at = lo - wr if nb < self.rank else hi
+                        into.append((arr, at, t))
+                        if nb < self.rank:
+                            got_l = wr
+                        else:
+                            got_r = wr
+                fills.append((arr, lo - got_l, hi + got_r))
+        if ops:
+            for req in dist.batch_isend_irecv(ops):
+                req.wait()
+        for arr, at, t in into:
+            arr[at:at + t.shape[0]] = t.numpy()
+        for arr, keep_lo, keep_hi in fills:
+            arr[:max(keep_lo, 0)] = np.nan
+            arr[keep_hi:] = np.nan
+
+    def advance(self, n_steps):
+        with np.errstate(all="ignore"):
+            for _ in range(int(n_steps)):
+                self.exchange()
+                self.coarse_step()
+
+    def _owned_sum(self, level, values):
+        lo, hi = self.cols(self.rank, level, "n")
+        return float(np.sum(values[lo:hi]))
+
+    def _period_end(self):
+        """The oracle's period end with its sums, flags and hits taken over the
+        owned nodes and all-reduced."""
+        import torch
+        import torch.distributed as dist
+        P = self.P
+        c, f = self.coarse, self.fine
+        wc, wf = self._weights()
+        heat = O.QE * O.QE / (O.ME * P.nu_m)
+        c.erms_last = np.sqrt(c.S2 / c.N)
+        f.erms_last = np.sqrt(f.S2 / f.N)
+        eeff_c, nu_c, D_c = O.density_rates(P, c, c.n)
+        pc = self._owned_sum(0, wc * c.n * heat * eeff_c * eeff_c)
+        n_c_new = O.continuity_update(P, c.n, D_c, nu_c, c.dx)
+        c.S2[...] = 0.0
+        c.n = n_c_new
+        eeff_f, nu_f, D_f = O.density_rates(P, f, f.n)
+        pf = self._owned_sum(1, wf * f.n * heat * eeff_f * eeff_f)
+        n_f_new = O.continuity_update(P, f.n, D_f, nu_f, f.dx)
+        r = P.r
+        i0, j0, i1, j1 = self.rect
+        on_edge = self._sides()
+        pa = i0 + np.arange(f.nx + 1) / r
+        pb = j0 + np.arange(f.ny + 1) / r
+        if not on_edge["bottom"]:
+            n_f_new[:, 0] = O.linear_cfb(n_c_new[:, j0], n_c_new[:, j0], 1.0, pa)
+        if not on_edge["top"]:
+            n_f_new[:, -1] = O.linear_cfb(n_c_new[:, j1], n_c_new[:, j1], 1.0, pa)
+        if not on_edge["left"]:
+            n_f_new[0, :] = O.linear_cfb(n_c_new[i0, :], n_c_new[i0, :], 1.0, pb)
+        if not on_edge["right"]:
+            n_f_new[-1, :] = O.linear_cfb(n_c_new[i1, :], n_c_new[i1, :], 1.0, pb)
+        f.S2[...] = 0.0
+        f.n = n_f_new
+        self._inject()
+        parts = torch.tensor([pc, pf, self._owned_sum(0, wc * c.n), self._owned_sum(1, wf * f.n)],
+                             dtype=torch.float64)
+        dist.all_reduce(parts, op=dist.ReduceOp.SUM)
+        p_abs = c.dx * c.dx * float(parts[0]) + f.dx * f.dx * float(parts[1])
+        self.N_e = c.dx * c.dx * float(parts[2]) + f.dx * f.dx * float(parts[3])
+        self.P_abs = p_abs
+        self.W_abs = self.W_abs + p_abs * P.T
+        self.period += 1
+        # flags and growth (Sec. III.D) from the owned coarse nodes
+        lo, hi = self.cols(self.rank, 0, "n")
+        mask = O.flag_mask(c.n, P.n_th, P.g_th, c.dx)
+        own = np.zeros_like(mask)
+        own[lo:hi] = mask[lo:hi]
+        self.masks.append(own)
+        if self.replay is not None:
+            new_rect = tuple(self.replay[self.period - 1])
+        elif P.growth == 2:
+            n_own = np.full(c.n.shape, -np.inf)
+            n_own[lo:hi] = c.n[lo:hi]
+            hits = torch.tensor([int(h) for h in O.line_hits(n_own, self.rect, P.n_th)],
+                                dtype=torch.int64)
+            dist.all_reduce(hits, op=dist.ReduceOp.MAX)
+            new_rect = O.grow_lines(self.rect, tuple(bool(h) for h in hits.tolist()),
+                                    P.m_ex, P.m_ey, P.nx, P.ny, P.rect_margin)
+        elif P.growth:
+            bb = O.mask_bbox(own)
+            big = 1 << 30
+            box = torch.tensor([big] * 4 if bb is None else [bb[0], bb[1], -bb[2], -bb[3]],
+                               dtype=torch.int64)
+            dist.all_reduce(box, op=dist.ReduceOp.MIN)
+            bbox = None if int(box[0]) == big else (int(box[0]), int(box[1]), -int(box[2]), -int(box[3]))
+            new_rect = O.grow_rect(self.rect, bbox, P.buffer, P.nx, P.ny, P.rect_margin)
+        else:
+            new_rect = self.rect
+        if new_rect != self.rect:
+            self._expand(new_rect)
+        self.log.append(self.rect)
+        self.stats_hist.append(self.stats())
+
+    def owned(self, level, name):
+        """The owned columns of a field of a level (x-major)."""
+        mesh = self.coarse if level == 0 else self.fine
+        lo, hi = self.cols(self.rank, level, name)
+        return getattr(mesh, name)[lo:hi]
+
+
+def dmr_slab_from_workload(w, rank, world):
+    """A rank's DmrSlabSim seeded as the oracle seeds a workload (every rank
+    evaluates the seed over the whole domain; the first exchange keeps its
+    own columns and halo)."""
+    sim = DmrSlabSim(w["cfg"], w["rect"], rank, world)
+    P = sim.P
+    Lx, Ly = P.nx * P.dxc, P.ny * P.dxc
+    for q, (n0, fx, fy, sxl, syl) in enumerate(w["seeds"]):
+        sim.seed_gaussian(n0, fx * Lx, fy * Ly, sxl * P.lam, syl * P.lam, add=q > 0)
+    return sim
