@@ -422,7 +422,7 @@ def run_adjoint(args):
 
 def front_x(run, cfg, lam):
     """Position (m) of the plasma front along the central x line: the
-    leftmost crossing of n = 1e19 m^-3 coming from the seed side (Sec. IV.C),
+    leftmost crossing of n = 1e19 m^-3 coming from the seed side (Sec. IV.B),
     log-linear between nodes; the fine rectangle's row where it covers the
     line, the coarse row elsewhere.  None before the density reaches it."""
     import numpy as np
@@ -452,7 +452,7 @@ def front_x(run, cfg, lam):
 
 
 def run_front(args):
-    """Front-velocity experiment of Sec. IV.C on a 1.5 x 1.5 wavelength domain:
+    """Front-velocity experiment of Sec. IV.B on a 1.5 x 1.5 wavelength domain:
     uniform meshes at lambda/128 and lambda/256 against DMR (coarse lambda/64)
     at r = 2 with both growth policies and at r = 4, with the two-way
     coupling and with the density-only transfer back.  The front is tracked

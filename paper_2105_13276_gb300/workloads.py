@@ -129,7 +129,7 @@ def small_dmr(nx=40, ny=32, r=2, rect=(12, 10, 24, 20), precision=0, **kw):
 
 
 def front_1p5(n_lambda, r, growth=1, precision=1):
-    """Front-velocity set-up of Sec. IV.C: a 1.5 x 1.5 wavelength domain,
+    """Front-velocity set-up of Sec. IV.B: a 1.5 x 1.5 wavelength domain,
     air at 760 Torr, E0 = 5.5 MV/m at 110 GHz, Gaussian n0 = 1e16 m^-3 at
     (0.85 Lx, 0.5 Ly) (sigma = lambda/8 here; the paper does not give it).
     n_lambda is the coarse resolution, r the refinement factor (1: uniform);

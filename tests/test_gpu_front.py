@@ -1,4 +1,4 @@
-"""Front-velocity experiment of Sec. IV.C on the GPU: a 1.5 x 1.5 wavelength
+"""Front-velocity experiment of Sec. IV.B on the GPU: a 1.5 x 1.5 wavelength
 domain in air at 760 Torr, E0 = 5.5 MV/m at 110 GHz, a Gaussian seed of
 1e16 m^-3 at (0.85 Lx, 0.5 Ly).  The paper reports the plasma front moving
 towards the source with the uniform fine mesh and DMR at r = 2 within 1-2 %
