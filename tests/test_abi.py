@@ -79,3 +79,39 @@ def test_create_rejects_bad_arguments_without_gpu(lib):
     assert st == D.ECAPACITY
     assert lib.dmr_kernel_class_name(0) == b"em_step"
     assert lib.dmr_kernel_class_name(99) is None
+
+
+def test_config_struct_layout_matches_the_header(tmp_path):
+    """The binding's dmr_config mirror has the header's field offsets and size
+    (compiled with the host C compiler)."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    import ctypes
+    import subprocess
+    from paper_2105_13276_gb300 import dmr as D
+    names = [f[0] for f in D.DmrConfig._fields_]
+    src = tmp_path / "layout.c"
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dmr.h"', "int main(void) {",
+             '  printf("size %zu\\n", sizeof(dmr_config));']
+    lines += ['  printf("%s %%zu\\n", offsetof(dmr_config, %s));' % (n, n) for n in names]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = dict(ln.split() for ln in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                    text=True).stdout.splitlines())
+    assert int(out["size"]) == ctypes.sizeof(D.DmrConfig)
+    for n in names:
+        assert int(out[n]) == getattr(D.DmrConfig, n).offset, n
+    # and no header field is missing from the mirror (one could hide in padding)
+    txt = open(os.path.join(ROOT, "include", "dmr.h")).read()
+    body = txt[txt.index("typedef struct dmr_config {"):txt.index("} dmr_config;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S).split("{", 1)[1]
+    declared = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            declared += [v.strip() for v in decl.split(None, 1)[1].split(",")]
+    assert declared == names
