@@ -115,3 +115,23 @@ def test_config_struct_layout_matches_the_header(tmp_path):
         if decl:
             declared += [v.strip() for v in decl.split(None, 1)[1].split(",")]
     assert declared == names
+
+
+def test_binding_constants_match_the_header():
+    """Status codes, field ids and statistics slots of the binding equal the
+    header's enumerations."""
+    from paper_2105_13276_gb300 import dmr as D
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "dmr.h")).read(), flags=re.S)
+    enum = {k: int(v) for k, v in re.findall(r"\b(DMR_[A-Z_0-9]+)\s*=\s*(-?\d+)", txt)}
+    for code, name in D.STATUS_NAMES.items():
+        assert enum[name] == code, name
+    field_ids = {"Ex": "EX", "Ey": "EY", "Hz": "HZ", "vx": "VX", "vy": "VY", "n": "NE", "S2": "S2",
+                 "mask": "MASK", "erms": "ERMS"}
+    for py, c in field_ids.items():
+        assert D.FIELDS[py] == enum["DMR_FIELD_" + c], py
+    stats = {"t": "T", "R": "R", "fine_cells": "FINE_CELLS", "N_e": "NE", "P_abs": "PABS",
+             "W_abs": "WABS", "periods": "PERIODS", "coarse_steps": "COARSE_STEPS", "n_max": "NMAX",
+             "flags": "FLAGS"}
+    assert len(D.STATS) == enum["DMR_NSTATS"]
+    for k, name in enumerate(D.STATS):
+        assert enum["DMR_STAT_" + stats[name]] == k, name
