@@ -195,8 +195,12 @@ int dmr_get_patch(const dmr_ctx* ctx, int32_t rect[4]);
 int dmr_advance(dmr_ctx* ctx, int64_t n_coarse_steps);
 
 /* Checked mode: from the next period end on, the rectangle after period k is
- * rects[4k .. 4k+3] instead of the growth policy (a recorded refinement log
- * is replayed).  n_periods = 0 switches replay off. */
+ * rects[4k .. 4k+3] instead of the growth policy of Sec. III.D (a recorded
+ * refinement log is replayed).  rects: host memory, 4 n_periods int32,
+ * copied by the call.  n_periods = 0 switches replay off.  Errors: DMR_EINVAL
+ * (NULL rects with n_periods > 0); a logged rectangle that does not contain
+ * the one before, or leaves the domain, stops dmr_advance at that period end
+ * with DMR_EINVAL, one beyond patch_cap_cells with DMR_ECAPACITY. */
 int dmr_replay_log(dmr_ctx* ctx, const int32_t* rects, int64_t n_periods);
 
 /* Shape (rows, cols) and element size of a field at level 0 (coarse) or 1
