@@ -171,7 +171,8 @@ const char* dmr_last_error(const dmr_ctx* ctx);
 /* Gaussian seed n0 exp(-((x-x0)^2/sx^2 + (y-y0)^2/sy^2)) on the nodes of the
  * coarse mesh and of the fine rectangle (Sec. IV), zero where the exponent is
  * below -60; add != 0 adds it to the present density.  The fine density is
- * then copied into the coinciding coarse nodes (Sec. III.C, direct copy). */
+ * then copied into the coinciding coarse nodes (Sec. III.C, direct copy).
+ * Queued on the stream.  Errors: DMR_EINVAL (sx or sy not > 0). */
 int dmr_seed_gaussian(dmr_ctx* ctx, double n0, double x0, double y0, double sx, double sy,
                       int add);
 
@@ -204,27 +205,39 @@ int dmr_advance(dmr_ctx* ctx, int64_t n_coarse_steps);
 int dmr_replay_log(dmr_ctx* ctx, const int32_t* rects, int64_t n_periods);
 
 /* Shape (rows, cols) and element size of a field at level 0 (coarse) or 1
- * (fine rectangle). */
+ * (fine rectangle), written to shape[2] and *elem_bytes (host memory;
+ * elem_bytes may be NULL).  Errors: DMR_EINVAL (unknown field, NULL shape),
+ * DMR_ESTATE (a level other than 0 and 1, level 1 without a rectangle, MASK
+ * at level 1 or of a uniform run, r = 1). */
 int dmr_field_shape(const dmr_ctx* ctx, int field, int level, int32_t shape[2],
                     int32_t* elem_bytes);
 
 /* Copy a field into dst (dense layout above).  dst_is_device != 0: dst is
  * device memory and the copy is queued on the stream; otherwise dst is host
  * memory and the call returns when the copy is done.  bytes must be at least
- * rows*cols*elem_bytes (DMR_ECAPACITY otherwise). */
+ * rows*cols*elem_bytes (DMR_ECAPACITY otherwise).  Errors also: DMR_EINVAL
+ * (NULL dst, unknown field), DMR_ESTATE (level as in dmr_field_shape),
+ * DMR_ECUDA. */
 int dmr_read(const dmr_ctx* ctx, int field, int level, void* dst, size_t bytes,
              int dst_is_device);
 
 /* Overwrite a field (EX..NE, S2) from src (same layout).  Used to start from
- * a given state or seed map.  src_is_device as in dmr_read. */
+ * a given state or seed map.  src_is_device as in dmr_read (a host src is
+ * copied before the call returns).  Errors: DMR_EINVAL (NULL src, unknown
+ * field, MASK or ERMS: derived quantities), DMR_ESTATE (level as in
+ * dmr_field_shape), DMR_ECAPACITY (bytes below rows*cols*elem_bytes),
+ * DMR_ECUDA. */
 int dmr_write(dmr_ctx* ctx, int field, int level, const void* src, size_t bytes,
               int src_is_device);
 
-/* Statistics (dmr_stat indices) after waiting for the stream. */
+/* Statistics (dmr_stat indices) into out[DMR_NSTATS] (host memory), after
+ * waiting for the stream.  Errors: DMR_ECUDA. */
 int dmr_stats(const dmr_ctx* ctx, double out[DMR_NSTATS]);
 
 /* Capture each full period (N_T coarse steps and the period-end kernels) in a
- * CUDA graph and replay it while the rectangle is unchanged (enable = 1). */
+ * CUDA graph and replay it while the rectangle is unchanged (enable = 1);
+ * 0 drops the graph and launches directly.  Results are the same either way.
+ * Never fails on a valid ctx. */
 int dmr_set_graphs(dmr_ctx* ctx, int enable);
 
 /* Per-kernel timing with CUDA events recorded on the run's stream around each
@@ -247,10 +260,11 @@ int dmr_kernel_time(const dmr_ctx* ctx, int kclass, double* ms, int64_t* launche
 const char* dmr_kernel_class_name(int kclass);
 
 /* Number of kernels the library has launched (graph replays count their
- * kernel nodes). */
+ * kernel nodes), into *launches (host memory). */
 int dmr_launch_count(const dmr_ctx* ctx, int64_t* launches);
 
-/* Wait for all work queued on the run's stream. */
+/* Wait for all work queued on the run's stream.  Errors: DMR_ECUDA (a
+ * failure of the queued work). */
 int dmr_sync(const dmr_ctx* ctx);
 
 /* Autotuner (at a period boundary): times the run's first EM launch of the

@@ -2879,6 +2879,7 @@ int dmr_replay_log(dmr_ctx* ctx, const int32_t* rects, int64_t n_periods) {
 
 int dmr_field_shape(const dmr_ctx* ctx, int field, int level, int32_t shape[2], int32_t* eb) {
   CTX_OR_FAIL(ctx);
+  if (!shape) return ctx->e->fail(DMR_EINVAL, "null output pointer");
   return ctx->e->shape(field, level, shape, eb);
 }
 
