@@ -2860,6 +2860,7 @@ int dmr_set_patch(dmr_ctx* ctx, const int32_t rect[4]) {
 
 int dmr_get_patch(const dmr_ctx* ctx, int32_t rect[4]) {
   CTX_OR_FAIL(ctx);
+  if (!rect) return ctx->e->fail(DMR_EINVAL, "null output pointer");
   for (int q = 0; q < 4; ++q) rect[q] = ctx->e->has_fine ? ctx->e->rect[q] : -1;
   return DMR_OK;
 }
@@ -2897,6 +2898,7 @@ int dmr_write(dmr_ctx* ctx, int field, int level, const void* src, size_t bytes,
 
 int dmr_stats(const dmr_ctx* ctx, double out[DMR_NSTATS]) {
   CTX_OR_FAIL(ctx);
+  if (!out) return ctx->e->fail(DMR_EINVAL, "null output pointer");
   return ctx->e->stats(out);
 }
 
@@ -2978,6 +2980,7 @@ const char* dmr_kernel_class_name(int kclass) {
 
 int dmr_launch_count(const dmr_ctx* ctx, int64_t* n) {
   CTX_OR_FAIL(ctx);
+  if (!n) return ctx->e->fail(DMR_EINVAL, "null output pointer");
   *n = ctx->e->launches;
   return DMR_OK;
 }
